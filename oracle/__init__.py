@@ -1,0 +1,428 @@
+"""FP64 CPU oracle of the VDS hot path (arXiv 2603.12550).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product package.  It
+shares no code with the CUDA library.
+
+Parts:
+  * ``vds_oracle.c`` (compiled here with gcc, FP64, OpenMP over particles):
+    density, entropy gradient, energy, explicit and implicit steps, stress,
+    median pair distance, pair counts, reduced-order refresh sums.
+  * this module (numpy, FP64): Silverman bandwidth, POD by the method of
+    snapshots, project/lift, the linearised reduced step, err_MOR, the batched
+    work-queue order.
+
+Pins (tests/test_oracle_*.py) tie every function to something other than
+itself: library densities, closed forms, invariants, finite differences,
+linear special cases solved by numpy, and brute force on tiny inputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vds_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_lock = threading.Lock()
+_lib = None
+
+OR_OK, OR_EARG, OR_EDOMAIN, OR_ENOCONV = 0, -1, -3, -4
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle status {code}")
+        self.code = code
+
+
+def _so_path():
+    with open(_SRC, "rb") as f:
+        tag = hashlib.sha1(f.read()).hexdigest()[:12]
+    return os.path.join(_BUILD, f"liboracle_{tag}.so")
+
+
+def build() -> str:
+    """Compile vds_oracle.c (gcc, -O2, OpenMP, strict IEEE FP64) if needed."""
+    path = _so_path()
+    if not os.path.exists(path):
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared",
+                               "-fno-fast-math", "-std=c11", "-D_GNU_SOURCE",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [("spring", ctypes.c_int), ("nb", ctypes.c_int), ("s", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("H", ctypes.c_double * 8),
+                ("b", ctypes.c_double), ("kBT", ctypes.c_double),
+                ("zeta", ctypes.c_double), ("h", ctypes.c_double),
+                ("dt", ctypes.c_double), ("kappa", ctypes.c_double * 9),
+                ("tol", ctypes.c_double), ("jfloor", ctypes.c_double)]
+
+
+def params(nb, s, H=1.0, kBT=1.0, zeta=4.0, h=0.3, dt=0.0, kappa=None,
+           spring=0, b=0.0, tol=1e-10, max_iter=50, jfloor=1e-14) -> OrParams:
+    p = OrParams()
+    p.spring, p.nb, p.s, p.max_iter = int(spring), int(nb), int(s), int(max_iter)
+    Hs = np.broadcast_to(np.asarray(H, dtype=np.float64), (nb,))
+    for j in range(nb):
+        p.H[j] = float(Hs[j])
+    p.b, p.kBT, p.zeta, p.h, p.dt, p.tol = float(b), float(kBT), float(zeta), float(h), float(dt), float(tol)
+    p.jfloor = float(jfloor)
+    k = np.zeros((s, s)) if kappa is None else np.asarray(kappa, dtype=np.float64).reshape(s, s)
+    for c in range(s * s):
+        p.kappa[c] = float(k.flat[c])
+    return p
+
+
+def _L():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            dp = ctypes.POINTER(ctypes.c_double)
+            fp = ctypes.POINTER(ctypes.c_float)
+            lp = ctypes.POINTER(ctypes.c_long)
+            ip = ctypes.POINTER(ctypes.c_int)
+            pp = ctypes.POINTER(OrParams)
+            L, I, D = ctypes.c_long, ctypes.c_int, ctypes.c_double
+            sig = {
+                "or_density": [dp, L, I, D, dp],
+                "or_entropy_grad": [dp, L, I, D, dp, dp],
+                "or_energy_grad": [dp, L, I, pp, dp, dp, dp],
+                "or_explicit_steps": [dp, L, I, pp, I],
+                "or_implicit_steps": [dp, L, I, pp, I, ip],
+                "or_stress": [dp, L, I, pp, dp, dp],
+                "or_median_pairdist": [dp, L, I, dp],
+                "or_count_pairs": [dp, L, I, D, lp, lp],
+                "or_count_pairs_f32": [fp, L, I, ctypes.c_float, lp, lp],
+                "or_refresh_sums": [dp, L, I, D, dp, dp, I, I, dp, dp, dp],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            lib.or_rouse.argtypes = [I, I]
+            lib.or_rouse.restype = D
+            lib.or_rouse_inv.argtypes = [I, I, I]
+            lib.or_rouse_inv.restype = D
+            _lib = lib
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(st):
+    if st != OR_OK:
+        raise OracleError(st)
+
+
+# ------------------------------------------------------------ C-backed parts
+
+def density(q, h):
+    """rho_I = sum_J exp(-|q_I - q_J|^2 / 2h^2), self term included."""
+    q, qp = _d(q)
+    N, D = q.shape
+    rho, rp = _d(np.empty(N))
+    _check(_L().or_density(qp, N, D, h, rp))
+    return rho
+
+
+def entropy_grad(q, h, rho=None):
+    """S_I = -(1/h^2) sum_J khat_IJ (q_I - q_J)(1/rho_I + 1/rho_J)."""
+    q, qp = _d(q)
+    N, D = q.shape
+    if rho is None:
+        rho = density(q, h)
+    rho, rp = _d(rho)
+    S, Sp = _d(np.empty((N, D)))
+    _check(_L().or_entropy_grad(qp, N, D, h, rp, Sp))
+    return S
+
+
+def energy_grad(q, p: OrParams, want_grad=True):
+    """Returns (E, g, rho): E = (1/N) sum [kBT ln f_h + Psi], g = N dE/dq."""
+    q, qp = _d(q)
+    N, D = q.shape
+    E = ctypes.c_double()
+    g, gp = _d(np.empty((N, D)))
+    rho, rp = _d(np.empty(N))
+    _check(_L().or_energy_grad(qp, N, D, ctypes.byref(p), ctypes.byref(E),
+                               gp if want_grad else None, rp))
+    return E.value, (g if want_grad else None), rho
+
+
+def energy(q, p: OrParams):
+    return energy_grad(q, p, want_grad=False)[0]
+
+
+def explicit_steps(q, p: OrParams, nsteps):
+    q = np.array(q, dtype=np.float64, copy=True)
+    _, qp = _d(q)
+    qp = q.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    N, D = q.shape
+    _check(_L().or_explicit_steps(qp, N, D, ctypes.byref(p), int(nsteps)))
+    return q
+
+
+def implicit_steps(q, p: OrParams, nsteps, raise_on_error=True):
+    """Returns (q_new, iters per step, status)."""
+    q = np.array(q, dtype=np.float64, copy=True)
+    qp = q.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    N, D = q.shape
+    it = (ctypes.c_int * max(1, int(nsteps)))()
+    st = _L().or_implicit_steps(qp, N, D, ctypes.byref(p), int(nsteps), it)
+    if raise_on_error:
+        _check(st)
+    return q, np.array(it[:nsteps]), st
+
+
+def stress(q, p: OrParams):
+    """Returns (tau s x s, qq D x D)."""
+    q, qp = _d(q)
+    N, D = q.shape
+    tau, tp = _d(np.empty((p.s, p.s)))
+    qq, qqp = _d(np.empty((D, D)))
+    _check(_L().or_stress(qp, N, D, ctypes.byref(p), tp, qqp))
+    return tau, qq
+
+
+def kramers(tau, p: OrParams):
+    """Kramers form tau - n (N-1) kBT Id with n = 1 (Eq. experiments_equilibriumStress)."""
+    return tau - p.nb * p.kBT * np.eye(p.s)
+
+
+def median_pairdist(q):
+    q, qp = _d(q)
+    N, D = q.shape
+    m = ctypes.c_double()
+    _check(_L().or_median_pairdist(qp, N, D, ctypes.byref(m)))
+    return m.value
+
+
+def median_bandwidth(q):
+    """h = med / sqrt(2 ln N) (Eq. model_bandwidth, natural log)."""
+    N = q.shape[0]
+    return median_pairdist(q) / np.sqrt(2.0 * np.log(N))
+
+
+def count_pairs(q, r2):
+    q, qp = _d(q)
+    N, D = q.shape
+    lt, le = ctypes.c_long(), ctypes.c_long()
+    _check(_L().or_count_pairs(qp, N, D, float(r2), ctypes.byref(lt), ctypes.byref(le)))
+    return lt.value, le.value
+
+
+def count_pairs_f32(q32, r2):
+    q32 = np.ascontiguousarray(q32, dtype=np.float32)
+    N, D = q32.shape
+    lt, le = ctypes.c_long(), ctypes.c_long()
+    _check(_L().or_count_pairs_f32(q32.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                   N, D, ctypes.c_float(r2), ctypes.byref(lt), ctypes.byref(le)))
+    return lt.value, le.value
+
+
+def rouse(nb):
+    L = _L()
+    return np.array([[L.or_rouse(j, k) for k in range(nb)] for j in range(nb)])
+
+
+def rouse_inv(nb):
+    L = _L()
+    return np.array([[L.or_rouse_inv(j, k, nb) for k in range(nb)] for j in range(nb)])
+
+
+def refresh_sums(q, h, rho, Phi, s):
+    """(W1, W2, c) of the frozen Brownian terms; Phi is (N*s) x r."""
+    q, qp = _d(q)
+    N, D = q.shape
+    Phi, up = _d(Phi)
+    r = Phi.shape[1]
+    rho, rp = _d(rho)
+    W1, w1 = _d(np.empty((N * s, r)))
+    W2, w2 = _d(np.empty((N * s, r)))
+    c, cp = _d(np.empty(N))
+    _check(_L().or_refresh_sums(qp, N, D, h, rp, up, s, r, w1, w2, cp))
+    return W1, W2, c
+
+
+# ------------------------------------------------------------ numpy parts
+
+def silverman_bandwidth(q):
+    """h = sigma (4 / ((D+2) N))^(1/(D+4)), sigma = mean per-coordinate sample
+    standard deviation (ddof = 1).  Not in the paper (a common KDE rule)."""
+    q = np.asarray(q, dtype=np.float64)
+    N, D = q.shape
+    sigma = np.mean(np.std(q, axis=0, ddof=1))
+    return sigma * (4.0 / ((D + 2) * N)) ** (1.0 / (D + 4))
+
+
+def snapshots_from_states(states, s, nb):
+    """Snapshot matrix X of Sec. 3.1: one column per (snapshot l, bond k), l
+    major; column = q_k(t_l) flattened as rows (I, alpha).  Shape (N s) x (L nb)."""
+    cols = []
+    for q in states:
+        q = np.asarray(q, dtype=np.float64)
+        N = q.shape[0]
+        for k in range(nb):
+            cols.append(q[:, s * k:s * k + s].reshape(N * s))
+    return np.stack(cols, axis=1)
+
+
+def pod_build(X, energy=0.9999, r_max=64, r_fixed=0):
+    """POD by the method of snapshots (Sec. 2.3, Sec. 3.1): the nonzero
+    eigenpairs of X X^T come from C = X^T X = V Lambda V^T as
+    U = X V Lambda^{-1/2}.  Rank: r_fixed if > 0, else the smallest r with
+    sum_{i<=r} lambda_i >= energy * sum_i lambda_i, capped at r_max.  Sign:
+    the largest-magnitude entry of every column is positive (ties: lowest
+    row).  Returns dict(Phi, lam (all, descending), r)."""
+    X = np.asarray(X, dtype=np.float64)
+    C = X.T @ X
+    lam, V = np.linalg.eigh(C)
+    order = np.argsort(-lam, kind="stable")
+    lam, V = lam[order], V[:, order]
+    r = int(r_fixed) if r_fixed > 0 else select_rank(lam, energy, r_max)
+    Phi = X @ V[:, :r] / np.sqrt(lam[:r])
+    for t in range(r):
+        i = int(np.argmax(np.abs(Phi[:, t])))
+        if Phi[i, t] < 0:
+            Phi[:, t] = -Phi[:, t]
+    return dict(Phi=Phi, lam=lam, r=r)
+
+
+def select_rank(lam, energy, r_max):
+    """Smallest r with cumulative energy fraction >= energy, capped at r_max."""
+    lam = np.asarray(lam, dtype=np.float64)
+    tot = lam.sum()
+    cum = 0.0
+    for i, l in enumerate(lam):
+        cum += l
+        if cum >= energy * tot:
+            return min(i + 1, r_max)
+    return min(len(lam), r_max)
+
+
+def project(Phi, q, s, nb):
+    """p_{k:} = U^T q_{k:} (Eq. model_pq); returns P (r x nb)."""
+    q = np.asarray(q, dtype=np.float64)
+    N = q.shape[0]
+    Q = np.stack([q[:, s * k:s * k + s].reshape(N * s) for k in range(nb)], axis=1)
+    return Phi.T @ Q
+
+
+def lift(Phi, P, s, nb):
+    """q~_{k:} = U p_{k:} (Eq. model_pq); returns N x (nb s)."""
+    Q = Phi @ P
+    N = Q.shape[0] // s
+    return np.concatenate([Q[:, k].reshape(N, s) for k in range(nb)], axis=1)
+
+
+def x_h(Phi, kappa, s):
+    """X^H_st = sum_I sum_{alpha beta} U_(I alpha)s G_{alpha beta} U_(I beta)t (Sec. 2.4)."""
+    N = Phi.shape[0] // s
+    r = Phi.shape[1]
+    U = Phi.reshape(N, s, r)
+    GU = np.einsum("ab,Ibt->Iat", np.asarray(kappa, dtype=np.float64).reshape(s, s), U)
+    return np.einsum("Ias,Iat->st", U, GU)
+
+
+def x_b(Phi, q, h, s):
+    """Frozen Brownian matrices of Sec. 2.4 at state q:
+      X^B1_st = -(1/h^2) sum_(I a) U_(Ia)s sum_K Z_IK (U_(Ia)t - U_(Ka)t) / rho_I
+      X^B2_st = -(1/h^2) sum_(I a) U_(Ia)s sum_K Z_IK (U_(Ia)t - U_(Ka)t) / rho_K
+    with Z_IK the kernel and rho_I = sum_J Z_IJ.  Returns (XB1, XB2, rho)."""
+    q = np.asarray(q, dtype=np.float64)
+    N = q.shape[0]
+    rho = density(q, h)
+    W1, W2, c = refresh_sums(q, h, rho, Phi, s)
+    r = Phi.shape[1]
+    U = Phi.reshape(N, s, r)
+    W1 = W1.reshape(N, s, r)
+    W2 = W2.reshape(N, s, r)
+    # sum_K Z_IK (U_(Ia)t - U_(Ka)t) = rho_I U_(Ia)t - W1_(Ia)t, since the row
+    # sum of Z is rho_I; divided by rho_I for X^B1.
+    inner1 = (rho[:, None, None] * U - W1) / rho[:, None, None]
+    # sum_K Z_IK (U_(Ia)t - U_(Ka)t) / rho_K = c_I U_(Ia)t - W2_(Ia)t.
+    inner2 = c[:, None, None] * U - W2
+    t1 = np.einsum("Ias,Iat->st", U, inner1)
+    t2 = np.einsum("Ias,Iat->st", U, inner2)
+    return -t1 / h ** 2, -t2 / h ** 2, rho
+
+
+def reduced_rhs(P, XH, XB, p: OrParams):
+    """Right-hand side of Eq. model_DymReduced in matrix form (P is r x nb):
+    Pdot = X^H P - (kBT/zeta) (X^B1 + X^B2) P A - (1/zeta) P diag(H) A."""
+    nb = p.nb
+    A = rouse(nb)
+    H = np.array([p.H[j] for j in range(nb)])
+    return XH @ P - (p.kBT / p.zeta) * (XB @ P @ A) - (1.0 / p.zeta) * (P * H[None, :]) @ A
+
+
+def velocity(q, p: OrParams):
+    """Full-order particle velocity of Eq. model_DymRepPar:
+    v_{k,I} = kappa q_{k,I} - (1/zeta) sum_j A_kj g_{I,j}."""
+    q = np.asarray(q, dtype=np.float64)
+    N, D = q.shape
+    s, nb = p.s, p.nb
+    _, g, _ = energy_grad(q, p)
+    A = rouse(nb)
+    kap = np.array(p.kappa[:s * s]).reshape(s, s)
+    qb = q.reshape(N, nb, s)
+    gb = g.reshape(N, nb, s)
+    v = np.einsum("ab,Ikb->Ika", kap, qb) - np.einsum("kj,Ija->Ika", A, gb) / p.zeta
+    return v.reshape(N, D)
+
+
+def galerkin_rhs(P, Phi, p: OrParams):
+    """Mode i: Pdot = U^T v(U P) (Eq. model_DymRepParPod at the lifted state)."""
+    q = lift(Phi, P, p.s, p.nb)
+    return project(Phi, velocity(q, p), p.s, p.nb)
+
+
+def reduced_run(P0, Phi, p: OrParams, nsteps, refresh_every):
+    """Explicit Euler on Eq. model_DymReduced with X^B1, X^B2 frozen and
+    rebuilt at the lifted state every ``refresh_every`` steps (Sec. 2.4,
+    Sec. 3.2)."""
+    s = p.s
+    kap = np.array(p.kappa[:s * s]).reshape(s, s)
+    XH = x_h(Phi, kap, s)
+    P = np.array(P0, dtype=np.float64)
+    XB = None
+    for n in range(nsteps):
+        if n % refresh_every == 0:
+            q = lift(Phi, P, s, p.nb)
+            B1, B2, _ = x_b(Phi, q, p.h, s)
+            XB = B1 + B2
+        P = P + p.dt * reduced_rhs(P, XH, XB, p)
+    return P
+
+
+def err_mor(q_mor, q_ref):
+    """Relative L2 MOR error (Sec. 3.1)."""
+    q_mor = np.asarray(q_mor, dtype=np.float64)
+    q_ref = np.asarray(q_ref, dtype=np.float64)
+    return np.linalg.norm(q_mor - q_ref) / np.linalg.norm(q_ref)
+
+
+def work_queue(sizes, tile):
+    """Batched work items (e, itile) in longest-processing-time order: cost
+    N_e descending, then ensemble index, then tile index ascending."""
+    items = []
+    for e, n in enumerate(sizes):
+        for t in range((int(n) + tile - 1) // tile):
+            items.append((-int(n), e, t))
+    items.sort()
+    return np.array([(e, t) for _, e, t in items], dtype=np.int32).reshape(-1, 2)
