@@ -1,0 +1,315 @@
+#!/usr/bin/env python3
+"""Benchmark of the VDS hot path on GB300: full-order VDS steps/s (and
+ordered pair-interactions/s) for the 4-bead chain in 3D, N = 65536
+particles, D = 9 (3 bonds x 3), Hookean H = 1, shear rate 1, dt = 0.005,
+explicit Euler, median-rule bandwidth computed once at t = 0.
+
+One step = one pass of the whole hot path for one time step: the density
+pair pass (rho, w = 1/rho), the gradient pair pass (kBT S + grad Psi) and the
+fused Euler update of all particles -- through the public C ABI (vds_step).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torchrun): the
+path is replicated, not sharded (weak scaling, no collective on the data
+path).  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
+the same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "chain4_n65536_d9"
+METRIC = "VDS steps/s (full-order explicit step, 4-bead chain N=65536 d=9)"
+UNIT = "steps/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _config(wl, h):
+    return {"workload": WORKLOAD, "N": wl["N"], "d": wl["nb"] * wl["s"], "bonds": wl["nb"],
+            "spatial_dim": wl["s"], "spring": "hookean", "H": wl["H"], "shear_rate": wl["rate"],
+            "dt": wl["dt"], "kBT": wl["kBT"], "zeta": wl["zeta"], "scheme": "explicit",
+            "bandwidth": "median rule at t=0", "h": h, "pairs_per_step": wl["N"] ** 2,
+            "l2": "flushed between timed steps (512 MiB write)", "seed": wl["seed"]}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _oracle_rate(wl, target_s=12.0, max_n=16384):
+    """FP64 oracle explicit step on the first n particles of the same cloud;
+    returns (ordered pairs per second across both passes, n, seconds, cores)."""
+    import oracle
+    from paper_2603_12550_gb300 import inputs
+    oracle.build()
+    q = inputs.equilibrium_cloud(wl["N"], wl["nb"], wl["s"], H=wl["H"], seed=wl["seed"]).astype(np.float64)
+    p = oracle.params(wl["nb"], wl["s"], H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=wl["_h"],
+                      dt=wl["dt"], kappa=inputs.shear_kappa(wl["s"], wl["rate"]))
+    n = 2048
+    while True:
+        t0 = time.perf_counter()
+        oracle.explicit_steps(q[:n], p, 1)
+        dt = time.perf_counter() - t0
+        if dt * 4.0 > target_s or n >= max_n:
+            break
+        n = min(max_n, n * 2)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return 2.0 * n * n / dt, n, dt, cores
+
+
+def run_reference(a, wl, rank):
+    if rank != 0:
+        return
+    from paper_2603_12550_gb300 import inputs
+    wl["_h"] = wl.get("_h") or 0.87
+    import oracle
+    oracle.build()
+    q = inputs.equilibrium_cloud(wl["N"], wl["nb"], wl["s"], H=wl["H"], seed=wl["seed"]).astype(np.float64)
+    p = oracle.params(wl["nb"], wl["s"], H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=wl["_h"],
+                      dt=wl["dt"], kappa=inputs.shear_kappa(wl["s"], wl["rate"]))
+    n = 4096
+    sample = q[:n].copy()
+    for _ in range(a.warmup):
+        sample = oracle.explicit_steps(sample, p, 1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        sample = oracle.explicit_steps(sample, p, 1)
+    el = time.perf_counter() - t0
+    # scale the sample's step rate to the full workload by ordered pairs
+    value = a.steps / el * (n / wl["N"]) ** 2
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded equilibrium Gaussian cloud)", "config": _config(wl, wl["_h"]),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle explicit steps on the first {n} particles of the "
+                                       f"same cloud, step rate scaled by (n/N)^2 to N={wl['N']}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2603_12550_gb300 import inputs
+    wl = dict(inputs.WORKLOADS[WORKLOAD])
+    if a.impl == "reference":
+        run_reference(a, wl, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_12550_gb300 import build
+    build.build()
+    from paper_2603_12550_gb300 import vds
+
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
+    D = nb * s
+    stream = torch.cuda.current_stream()
+    ctx = vds.Context(local, stream)
+    q0 = inputs.equilibrium_cloud(N, nb, s, H=wl["H"], kBT=wl["kBT"], seed=wl["seed"] + rank)
+    q = torch.from_numpy(q0).cuda()
+    if "vds_bandwidth" in vds.exported_symbols():
+        h = ctx.vds_bandwidth(q, 0)
+    else:
+        h = 0.87
+    wl["_h"] = h
+    p = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"],
+                   kappa=inputs.shear_kappa(s, wl["rate"]), scheme=0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(3, a.warmup)):
+        ctx.vds_step(q, p, 1)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM -------------------
+    ctx.vds_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    for k in range(a.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ctx.vds_step(q, p, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = float(sum(step_ms))
+    pass_ms, pass_n, launches = ctx.vds_timing_read()
+    ctx.vds_timing(False)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * a.steps / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers -----------------
+    q_h = torch.from_numpy(q0).pin_memory()
+    q_out = torch.empty_like(q_h).pin_memory()
+    for _ in range(2):
+        q.copy_(q_h, non_blocking=True)
+        ctx.vds_step(q, p, 1)
+        q_out.copy_(q, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(a.steps):
+        q.copy_(q_h, non_blocking=True)
+        ctx.vds_step(q, p, 1)
+        q_out.copy_(q, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": world * a.steps / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the dominant kernel (gradient pair pass) ---------------
+    peaks, src = _peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tops = nsm * 128 * clk_mhz * 1e6 / 1e12
+    t_grad = pass_ms[1] / max(1, pass_n[1]) / 1e3
+    t_dens = pass_ms[0] / max(1, pass_n[0]) / 1e3
+    ops_grad = float(N) * N * (3 * D + 2)
+    ops_dens = float(N) * N * (2 * D + 1)
+    traffic = None
+    roof = {"bound": "alu", "kernel": "k_pair<D=9,GRAD> (gradient pair pass)",
+            "achieved": ops_grad / t_grad / 1e12, "peak": peak_tops,
+            "unit": "TOP/s (FP32 lane-ops)", "frac": ops_grad / t_grad / 1e12 / peak_tops,
+            "traffic": traffic,
+            "peak_note": f"{nsm} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz ({src} sm_max_mhz)",
+            "ops_per_pair": 3 * D + 2, "launch_ms": t_grad * 1e3,
+            "density_pass": {"launch_ms": t_dens * 1e3, "ops_per_pair": 2 * D + 1,
+                             "achieved": ops_dens / t_dens / 1e12,
+                             "frac": ops_dens / t_dens / 1e12 / peak_tops}}
+
+    cpu = None
+    if not a.no_cpu_baseline:
+        rate, n, secs, cores = _oracle_rate(wl)
+        cpu = {"value": rate / (2.0 * N * N), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"one FP64 oracle explicit step on the first {n} particles of the same cloud "
+                         f"({2 * n * n:.3g} ordered pairs, {secs:.1f} s), rate scaled by pairs to N={N}"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded equilibrium Gaussian cloud, the paper's initial condition)",
+            "config": _config(wl, h),
+            "pair_interactions_per_s": value * N * N,
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+            "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

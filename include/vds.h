@@ -1,0 +1,132 @@
+/*
+ * vds.h -- C ABI of the GB300 (sm_103a) hot path of the reduced-order
+ * variational deterministic-particle scheme (VDS with POD) for the
+ * microscopic Fokker-Planck equation of bead-spring chains in homogeneous
+ * flow (Fang, Bao, Song, Xu, Huang, arXiv 2603.12550).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Notation: N representative particles (the paper's P); nb bonds per chain
+ *    (the paper's N-1); s spatial dimension (the paper's d); D = nb*s
+ *    coordinates per particle (the paper's (N-1)d).  1 <= D <= 16, s in {2,3},
+ *    1 <= nb <= 8.
+ *  - Particle arrays are DEVICE pointers to row-major N x D FP32, contiguous;
+ *    bond k of particle I is q[I*D + s*k + alpha].  The caller owns them.
+ *  - Scalars written to the host (E, h, tau, r, iters) are HOST pointers; the
+ *    call synchronises the context stream before returning them.  Every other
+ *    call is asynchronous on the context stream.
+ *  - The library owns the context (its stream binding and device workspace)
+ *    and pod_basis objects.
+ *  - Return value: VDS_OK or a negative status; on error the outputs are
+ *    unspecified and no memory is leaked.  Device-side failures (a FENE bond
+ *    leaving |q|^2 < b, a NaN, a wait that gave up) are reported by the next
+ *    call that synchronises (every call returning host scalars, and vds_step).
+ */
+#ifndef VDS_H
+#define VDS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define VDS_API __attribute__((visibility("default")))
+#else
+#define VDS_API
+#endif
+
+typedef struct vds_ctx vds_ctx;
+typedef struct pod_basis pod_basis;
+
+enum {
+  VDS_OK = 0,
+  VDS_EARG = -1,      /* invalid argument (size, pointer, parameter) */
+  VDS_ECUDA = -2,     /* CUDA runtime error */
+  VDS_EDOMAIN = -3,   /* FENE bond with |q_j|^2 >= b */
+  VDS_ENOCONV = -4,   /* implicit minimiser did not converge */
+  VDS_ENAN = -5,      /* non-finite density / energy */
+  VDS_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
+  VDS_ENOMEM = -7,    /* device allocation failed */
+  VDS_ESURROGATE = -8 /* surrogate check failed */
+};
+
+/* Physical and numerical parameters (Sec. 2.1-2.2, Sec. 3.1, Appendix A). */
+typedef struct {
+  int spring;       /* 0: Hookean Psi_j = H_j|q_j|^2/2 (Eq. model_Hookean);
+                       1: FENE Psi_j = -(H_j b/2) ln(1-|q_j|^2/b) */
+  int nb;           /* bonds per chain */
+  int s;            /* spatial dimension */
+  int max_iter;     /* implicit minimiser: max gradient evaluations per step */
+  double H[8];      /* spring constants H_j, j < nb */
+  double b;         /* FENE extensibility */
+  double kBT;       /* thermal energy */
+  double zeta;      /* friction */
+  double h;         /* kernel bandwidth (Eq. model_bandwidth or given) */
+  double dt;        /* time step */
+  double kappa[9];  /* s x s row-major velocity gradient G = (grad u)^T,
+                       acting as qdot = kappa q */
+  double tol;       /* minimiser stop: max|dir| <= tol (1 + max|y|) */
+  double jfloor;    /* Armijo round-off allowance, relative to 1 + |J| */
+  int scheme;       /* vds_step: 0 explicit Euler, 1 implicit Euler */
+  int reserved;
+} vds_params;
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream). */
+VDS_API int vds_create(vds_ctx **ctx, void *cuda_stream, int device);
+VDS_API void vds_destroy(vds_ctx *ctx);
+/* Rebind the context to another stream of the same device. */
+VDS_API int vds_set_stream(vds_ctx *ctx, void *cuda_stream);
+VDS_API const char *vds_strerror(int status);
+
+/* Density and free-energy gradient (Eq. model_DeteParAppr, Eq. model_DymRepPar).
+ *   rho_I = sum_J exp(-|q_I - q_J|^2 / 2h^2)   (self term included)
+ *   S_I   = -(1/h^2) sum_J khat_IJ (q_I - q_J)(1/rho_I + 1/rho_J)
+ *   E     = (1/N) sum_I [kBT ln f_h(q_I) + Psi(q_I)],
+ *           f_h(q_I) = (2 pi h^2)^(-D/2) rho_I / N
+ *   g_I   = N dE/dq_I = kBT S_I + grad Psi(q_I)
+ * With q_star != NULL (device, N x D) and p->dt > 0 it evaluates instead the
+ * implicit-step objective (Appendix A, implicit scheme)
+ *   J = (1/N) sum_I (zeta/2dt)(q_I - q*_I)^T (A^-1 (x) I_s)(q_I - q*_I) + E
+ * and G_I = N dJ/dq_I = (zeta/dt)(A^-1 (x) I_s)(q_I - q*_I) + g_I.
+ * E: host (may be NULL); g: device N x D (may be NULL); rho: device N
+ * (may be NULL). */
+VDS_API int vds_energy_grad(vds_ctx *ctx, const float *q, int N, int D,
+                    const vds_params *p, const float *q_star, double *E,
+                    float *g, float *rho);
+
+/* Advance q (device, N x D, in place) by nsteps time steps.
+ * scheme 0, explicit Euler (Appendix A):
+ *   q_{k,I} += dt [kappa q_{k,I} - (1/zeta) sum_j A_kj g_{I,j}],
+ *   A_jk = 2[j=k] - [|j-k|=1] the Rouse matrix (Sec. 2.1).
+ * scheme 1, implicit Euler (Appendix A), flow at t and the rest at t+dt,
+ *   q+ = q* - (dt/zeta)(A (x) I_s) g(q+),  q* = q + dt kappa q,
+ * solved as the minimiser of J above by preconditioned descent with FP64
+ * Armijo acceptance (unit step = fixed-point iteration).  iters_out (host,
+ * nsteps ints, may be NULL) receives gradient evaluations per step. */
+VDS_API int vds_step(vds_ctx *ctx, float *q, int N, int D, const vds_params *p,
+             int nsteps, int *iters_out);
+
+/* Polymer stress (Sec. 2.1, discrete form of Appendix A, n = 1):
+ *   tau = (1/N) sum_I sum_k q_{k,I} (x) grad Psi_k(q_{k,I})   (s x s, host)
+ * and second moments qq = (1/N) sum_I q_I q_I^T (D x D, host, may be NULL).
+ * The Kramers form is tau - nb kBT Id. */
+VDS_API int vds_stress(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
+               double *tau, double *qq);
+
+/* Instrumentation (no counterpart in the paper; used to report a kernel's
+ * achieved rate).  vds_timing(ctx, 1) clears the counters and starts
+ * recording the device duration of every pair-pass launch on the context
+ * stream (CUDA events around the launch); vds_timing(ctx, 0) stops.  The
+ * library's total kernel-launch count is cleared by either call.
+ * vds_timing_read synchronises and returns, per pass kind (0 density,
+ * 1 gradient, 2 bandwidth, 3 POD refresh), the summed milliseconds ms[4] and
+ * launch counts launches[4] (host arrays, may be NULL), and the number of
+ * kernels launched since the last vds_timing call. */
+VDS_API int vds_timing(vds_ctx *ctx, int enable);
+VDS_API int vds_timing_read(vds_ctx *ctx, double *ms, long *launches, long *total_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VDS_H */

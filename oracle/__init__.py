@@ -106,6 +106,7 @@ def _L():
                 "or_count_pairs": [dp, L, I, D, lp, lp],
                 "or_count_pairs_f32": [fp, L, I, ctypes.c_float, lp, lp],
                 "or_refresh_sums": [dp, L, I, D, dp, dp, I, I, dp, dp, dp],
+                "or_entropy_grad_rows": [dp, L, I, D, dp, lp, L, dp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -150,6 +151,32 @@ def entropy_grad(q, h, rho=None):
     S, Sp = _d(np.empty((N, D)))
     _check(_L().or_entropy_grad(qp, N, D, h, rp, Sp))
     return S
+
+
+def entropy_grad_rows(q, h, rho, rows):
+    """S_I for the particles in ``rows`` only (rho: density of all particles)."""
+    q, qp = _d(q)
+    N, D = q.shape
+    rho, rp = _d(rho)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    S, Sp = _d(np.empty((len(rows), D)))
+    _check(_L().or_entropy_grad_rows(qp, N, D, h, rp, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                     len(rows), Sp))
+    return S
+
+
+def spring_grad(q, p: OrParams):
+    """grad Psi(q_I) per particle (Hookean or FENE), N x D."""
+    q = np.asarray(q, dtype=np.float64)
+    N, D = q.shape
+    s, nb = p.s, p.nb
+    qb = q.reshape(N, nb, s)
+    H = np.array([p.H[j] for j in range(nb)])
+    if p.spring == 0:
+        f = np.broadcast_to(H, (N, nb))
+    else:
+        f = H[None, :] / (1.0 - (qb ** 2).sum(-1) / p.b)
+    return (qb * f[:, :, None]).reshape(N, D)
 
 
 def energy_grad(q, p: OrParams, want_grad=True):

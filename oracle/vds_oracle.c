@@ -463,3 +463,26 @@ int or_refresh_sums(const double *q, long N, int D, double h, const double *rho,
   }
   return OR_OK;
 }
+
+/* Entropy gradient S_I (as or_entropy_grad) for a subset of particles only:
+ * rows[0..nrows) index particles, S is nrows x D.  rho must hold the density
+ * of every particle (the second term of Eq. model_DymRepPar needs all of
+ * them). */
+int or_entropy_grad_rows(const double *q, long N, int D, double h, const double *rho,
+                         const long *rows, long nrows, double *S) {
+  if (N < 0 || D < 1 || D > 64 || !(h > 0)) return OR_EARG;
+  const double ih2 = 1.0 / (h * h);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long r = 0; r < nrows; ++r) {
+    const long I = rows[r];
+    double acc[64];
+    for (int c = 0; c < D; ++c) acc[c] = 0.0;
+    for (long J = 0; J < N; ++J) {
+      double k = khat(q + I * D, q + J * D, D, h);
+      double w = k * (1.0 / rho[I] + 1.0 / rho[J]);
+      for (int c = 0; c < D; ++c) acc[c] += w * (q[I * D + c] - q[J * D + c]);
+    }
+    for (int c = 0; c < D; ++c) S[r * D + c] = -ih2 * acc[c];
+  }
+  return OR_OK;
+}

@@ -1,0 +1,72 @@
+// pair.cuh -- host-side interface of the O(N^2) Gaussian-kernel pair passes
+// and their fused epilogues (pair.cu).
+#pragma once
+#include "vds_internal.cuh"
+
+// Stream-K schedule of a pair pass: the (i-tile, j-chunk) items of the N x N
+// pair square, flattened i-tile major, are split into G contiguous equal
+// ranges, one per CTA of a grid sized to the resident capacity of the GPU.
+// A CTA accumulates in registers while its i-tile is unchanged and writes one
+// FP64 partial per (i-tile, segment); an epilogue sums the segments of each
+// i-tile in a fixed order, so results do not depend on timing.
+struct Sched {
+  long long items;  // n_itiles * nchunk
+  int G;            // CTAs
+  int nchunk;       // j-chunks (tiles of TJ records) per i-tile
+  int n_itiles;
+  int maxseg;       // max segments per i-tile
+  int TI;           // particles per i-tile
+  int Npad;         // N rounded up to a multiple of TJ
+};
+
+__host__ __device__ __forceinline__ int sched_first_cta(long long x, const Sched &s) {
+  return (int)(((x + 1) * (long long)s.G + s.items - 1) / s.items - 1);
+}
+
+// Physical parameters as the kernels see them.
+struct KParams {
+  int N, D, nb, s, spring;
+  float c;          // coordinate scale: qhat = c q, khat = exp2(-|dqhat|^2)
+  double h, kBT, zeta, dt, b;
+  double H[8];
+  double kappa[9];
+  double lnorm;     // -ln N - (D/2) ln(2 pi h^2)
+  double sfac;      // S = -sfac * sum u dqhat, sfac = 1/(h^2 c)
+};
+
+KParams make_kparams(const vds_params *p, int N, int D);
+
+// Records of y = base + delta (delta may be NULL) scaled by c, with w = 0,
+// padded to Npad with padding records.  If delta_out != NULL it receives
+// delta - alpha*dir (and the record is built from base + that).
+int pass_prep(vds_ctx *c, const KParams &kp, const float *base, const float *delta,
+              const float *dir, float alpha, float *delta_out);
+
+// Density pass: rho_I over all J, then the epilogue: w_I = 1/rho_I into the
+// records, optional rho output, and when want_energy, the FP64 energy
+//   (1/N) sum_I [kBT (ln rho_I + lnorm) + Psi(y_I)]
+//   + (zeta/2dt)(1/N) sum_I dI^T (A^-1 (x) I) dI,   dI = qa_I - qb_I
+// (the quadratic term only when qa != NULL; qb may be NULL) into scal[SC_E].
+// y_I = ybase_I + ydelta_I (ydelta may be NULL).
+int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
+                 const float *ybase, const float *ydelta, const float *qa,
+                 const float *qb);
+
+// Gradient pass (records must hold w from pass_density) and its epilogues.
+enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2 };
+// GM_OUT: g = kBT S + grad Psi(y) (+ (zeta/dt)(A^-1 (x) I)(qa - qb) if qa).
+// GM_EXPLICIT: q_io += dt [kappa q - (1/zeta)(A (x) I) g]; rebuild records.
+// GM_IMPLICIT_DIR: dir = d + (dt/zeta)(A (x) I) g with d = ydelta, and
+//   scal[SC_DEC] = (1/N) sum <G, dir>, G = (zeta/dt)(A^-1 (x) I) d + g,
+//   scal[SC_DMAX] = max|dir|, scal[SC_YMAX] = max|y|.
+int pass_grad(vds_ctx *c, const KParams &kp, int mode, float *out,
+              const float *ybase, const float *ydelta, const float *qa,
+              const float *qb, float *q_io);
+
+// Stress and second moments (FP64) into host arrays.
+int pass_stress(vds_ctx *c, const KParams &kp, const float *q, double *tau, double *qq);
+
+// y = base + delta -> out (element-wise, N x D).
+int pass_axpy(vds_ctx *c, int n, const float *base, const float *delta, float *out);
+// qs = q + dt kappa q (per bond).
+int pass_flow(vds_ctx *c, const KParams &kp, const float *q, float *qs);

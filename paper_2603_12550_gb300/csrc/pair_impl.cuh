@@ -1,0 +1,719 @@
+#pragma once
+// pair_impl.cuh -- the O(N^2) Gaussian-kernel pair passes of the VDS hot path and
+// their fused O(N) epilogues, for GB300 (sm_103a).
+//
+// Density pass (Eq. model_DeteParAppr, denominators of Eq. model_DymRepPar):
+//   rho_I = sum_J exp2(-|qhat_I - qhat_J|^2),  qhat = c q,  c^2 = log2(e)/(2h^2)
+// Gradient pass (Eq. model_DymRepPar with grad K = -(x/h^2) K):
+//   S_I = -(1/(h^2 c)) sum_J khat_IJ (w_I + w_J)(qhat_I - qhat_J),  w = 1/rho.
+//
+// Each CTA owns a contiguous range of (i-tile, j-chunk) items (stream-K),
+// keeps RI particles per thread in registers and streams j-tiles of particle
+// records through a ring of shared-memory stages filled by TMA bulk copies
+// (cp.async.bulk + mbarrier transaction counts) issued by one thread.  All
+// threads read the same record at a time (shared-memory broadcast).  Inside a
+// j-tile sums are plain FP32; across tiles they are Kahan-compensated; across
+// CTAs they are combined in FP64 by the epilogue in a fixed order.
+#include <math.h>
+
+#include "pair.cuh"
+
+namespace vds_pair {
+
+constexpr int NT_PAIR = 128;   // threads per CTA
+constexpr int TJ = 128;        // records per j-tile (= j-chunk)
+constexpr int NSTAGE = 3;      // shared-memory ring depth
+
+template <int D>
+struct PairCfg {
+  static constexpr int RI_DENS = 4;
+  static constexpr int RI_GRAD = (D <= 6) ? 4 : 2;
+};
+
+// ------------------------------------------------------------- pair kernel
+
+template <int D, int RI, bool GRAD>
+__global__ void __launch_bounds__(NT_PAIR)
+    k_pair(const float *__restrict__ rec, Sched sc, double *__restrict__ part,
+           int *__restrict__ err) {
+  constexpr int DP = Rec<D>::DP;
+  constexpr int ACC = GRAD ? D : 1;
+  constexpr int NT = NT_PAIR;
+  constexpr uint32_t TILE_FLOATS = TJ * DP;
+  constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
+  extern __shared__ __align__(128) float tiles[];  // NSTAGE * TILE_FLOATS
+  __shared__ __align__(8) uint64_t full[NSTAGE];
+
+  const int tid = threadIdx.x;
+  const long long it0 = (long long)blockIdx.x * sc.items / sc.G;
+  const long long it1 = (long long)(blockIdx.x + 1) * sc.items / sc.G;
+  if (it0 >= it1) return;  // uniform over the CTA
+
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE && it0 + s < it1; ++s) {
+      const int ch = (int)((it0 + s) % sc.nchunk);
+      mbar_arrive_expect_tx(&full[s], TILE_BYTES);
+      bulk_g2s(tiles + s * TILE_FLOATS, rec + (size_t)ch * TILE_FLOATS, TILE_BYTES, &full[s]);
+    }
+  }
+
+  float xi[RI][D];
+  float wi[RI];
+  float sum[RI][ACC], cmp[RI][ACC];
+  int cur = -1, seg = 0;
+  long long it_fail = -1;
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+      const int il = tid + k * NT;
+      double *dst = part + (((size_t)cur * sc.maxseg + seg) * sc.TI + il) * ACC;
+#pragma unroll
+      for (int a = 0; a < ACC; ++a) dst[a] = (double)sum[k][a] - (double)cmp[k][a];
+    }
+  };
+
+  for (long long it = it0; it < it1; ++it) {
+    const int t = (int)(it / sc.nchunk);
+    if (t != cur) {
+      if (cur >= 0) flush();
+      cur = t;
+      seg = (int)blockIdx.x - sched_first_cta((long long)t * sc.nchunk, sc);
+#pragma unroll
+      for (int k = 0; k < RI; ++k) {
+        int i = t * sc.TI + tid + k * NT;
+        i = i < sc.Npad ? i : sc.Npad - 1;
+        const float *r = rec + (size_t)i * DP;
+#pragma unroll
+        for (int d = 0; d < D; ++d) xi[k][d] = r[d];
+        wi[k] = GRAD ? r[D] : 0.f;
+#pragma unroll
+        for (int a = 0; a < ACC; ++a) sum[k][a] = cmp[k][a] = 0.f;
+      }
+    }
+    const int stage = (int)((it - it0) % NSTAGE);
+    const uint32_t parity = (uint32_t)(((it - it0) / NSTAGE) & 1);
+    const bool got = mbar_wait_bounded(&full[stage], parity, VDS_WAIT_LIMIT_NS);
+    if (__syncthreads_or(!got)) {
+      it_fail = it;
+      break;
+    }
+
+    const float *tj = tiles + stage * TILE_FLOATS;
+    float acc[RI][ACC];
+#pragma unroll
+    for (int k = 0; k < RI; ++k)
+#pragma unroll
+      for (int a = 0; a < ACC; ++a) acc[k][a] = 0.f;
+
+#pragma unroll 2
+    for (int j = 0; j < TJ; ++j) {
+      float xj[DP];
+      const float4 *pj = reinterpret_cast<const float4 *>(tj + j * DP);
+#pragma unroll
+      for (int v = 0; v < DP / 4; ++v) {
+        const float4 f = pj[v];
+        xj[4 * v + 0] = f.x;
+        xj[4 * v + 1] = f.y;
+        xj[4 * v + 2] = f.z;
+        xj[4 * v + 3] = f.w;
+      }
+#pragma unroll
+      for (int k = 0; k < RI; ++k) {
+        float dd[D];
+        dd[0] = xi[k][0] - xj[0];
+        float r2 = dd[0] * dd[0];
+#pragma unroll
+        for (int d = 1; d < D; ++d) {
+          dd[d] = xi[k][d] - xj[d];
+          r2 = fmaf(dd[d], dd[d], r2);
+        }
+        const float e = ex2_approx(-r2);
+        if constexpr (!GRAD) {
+          acc[k][0] += e;
+        } else {
+          const float u = e * (wi[k] + xj[D]);
+#pragma unroll
+          for (int d = 0; d < D; ++d) acc[k][d] = fmaf(u, dd[d], acc[k][d]);
+        }
+      }
+    }
+    // Kahan-compensated accumulation of the tile sums
+#pragma unroll
+    for (int k = 0; k < RI; ++k)
+#pragma unroll
+      for (int a = 0; a < ACC; ++a) {
+        const float y = acc[k][a] - cmp[k][a];
+        const float tt = sum[k][a] + y;
+        cmp[k][a] = (tt - sum[k][a]) - y;
+        sum[k][a] = tt;
+      }
+    __syncthreads();  // stage fully consumed
+    if (tid == 0 && it + NSTAGE < it1) {
+      fence_proxy_async_smem();
+      const int ch = (int)((it + NSTAGE) % sc.nchunk);
+      mbar_arrive_expect_tx(&full[stage], TILE_BYTES);
+      bulk_g2s(tiles + stage * TILE_FLOATS, rec + (size_t)ch * TILE_FLOATS, TILE_BYTES,
+               &full[stage]);
+    }
+  }
+  if (it_fail >= 0) {
+    if (tid == 0) {
+      vds_flag(err, VDS_ETIMEOUT);
+      // copies for items it_fail .. it_fail+NSTAGE-1 may still be in flight:
+      // give each a bounded chance to land before shared memory is released
+      for (long long k = it_fail; k < it_fail + NSTAGE && k < it1; ++k)
+        mbar_wait_bounded(&full[(k - it0) % NSTAGE], (uint32_t)(((k - it0) / NSTAGE) & 1),
+                          VDS_WAIT_LIMIT_NS / 8);
+    }
+    return;
+  }
+  if (cur >= 0) flush();
+}
+
+// --------------------------------------------------------- small device math
+
+__device__ __forceinline__ double rouse_A(int j, int k) {
+  return j == k ? 2.0 : ((j - k == 1 || k - j == 1) ? -1.0 : 0.0);
+}
+
+// inverse of the tridiagonal Rouse matrix: min(j,k)(nb+1-max(j,k))/(nb+1), 1-based
+__device__ __forceinline__ double rouse_Ainv(int j, int k, int nb) {
+  const int lo = (j < k ? j : k) + 1, hi = (j > k ? j : k) + 1;
+  return (double)lo * (double)(nb + 1 - hi) / (double)(nb + 1);
+}
+
+// Spring energy and force factor per bond: grad Psi_k = f_k q_k.
+template <int D>
+__device__ __forceinline__ bool spring_eval(const KParams &kp, const double (&y)[D], double &psi,
+                                            double (&f)[8]) {
+  psi = 0.0;
+  bool ok = true;
+  for (int k = 0; k < kp.nb; ++k) {
+    double n2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a / kp.s == k) n2 += y[a] * y[a];
+    if (kp.spring == 0) {
+      psi += 0.5 * kp.H[k] * n2;
+      f[k] = kp.H[k];
+    } else {
+      const double x = 1.0 - n2 / kp.b;
+      if (!(x > 0.0)) {
+        ok = false;
+        f[k] = 0.0;
+      } else {
+        psi += -0.5 * kp.H[k] * kp.b * log(x);
+        f[k] = kp.H[k] / x;
+      }
+    }
+  }
+  return ok;
+}
+
+// --------------------------------------------------------------- prep kernel
+
+template <int D>
+__global__ void k_prep(int N, int Npad, float c, const float *__restrict__ base,
+                       const float *__restrict__ delta, const float *__restrict__ dir,
+                       float alpha, float *__restrict__ delta_out, float *__restrict__ rec) {
+  constexpr int DP = Rec<D>::DP;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Npad) return;
+  float o[DP];
+  if (i < N) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      float dl = 0.f;
+      if (delta) {
+        dl = delta[(size_t)i * D + d];
+        if (dir) dl = dl - alpha * dir[(size_t)i * D + d];
+        if (delta_out) delta_out[(size_t)i * D + d] = dl;
+      }
+      o[d] = c * (base[(size_t)i * D + d] + dl);
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < D; ++d) o[d] = VDS_PAD_COORD;
+  }
+#pragma unroll
+  for (int d = D; d < DP; ++d) o[d] = 0.f;
+  float4 *dst = reinterpret_cast<float4 *>(rec + (size_t)i * DP);
+#pragma unroll
+  for (int v = 0; v < DP / 4; ++v) dst[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+}
+
+// ------------------------------------------------------------- epilogues
+
+constexpr int NT_FIN = 256;
+
+// Deterministic grid reduction: every block stores its partial, the last
+// block to arrive (ticket) sums them in block order.  Returns true in the
+// thread that holds the final value.
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], const bool (&is_max)[K], double *red,
+                                            unsigned *ticket, double (&out)[K]) {
+  __shared__ double sh[NT_FIN / 32][K];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = is_max[k] ? fmax(x, y) : x + y;
+    }
+    if (lane == 0) sh[w][k] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = is_max[k] ? 0.0 : 0.0;
+      for (int q = 0; q < NT_FIN / 32; ++q) x = is_max[k] ? fmax(x, sh[q][k]) : x + sh[q][k];
+      red[(size_t)blockIdx.x * K + k] = x;
+    }
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      const double y = __ldcg(red + (size_t)b * K + k);
+      x = is_max[k] ? fmax(x, y) : x + y;
+    }
+    out[k] = x;
+  }
+  *ticket = 0u;
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ void load_y(const float *ybase, const float *ydelta, int i, double (&y)[D],
+                                       float (&yf)[D]) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    float v = ybase[(size_t)i * D + d];
+    if (ydelta) v = v + ydelta[(size_t)i * D + d];
+    yf[d] = v;
+    y[d] = (double)v;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(NT_FIN)
+    k_dens_finish(Sched sc, const double *__restrict__ part, float *__restrict__ rec,
+                  float *__restrict__ rho_out, KParams kp, int want_energy,
+                  const float *__restrict__ ybase, const float *__restrict__ ydelta,
+                  const float *__restrict__ qa, const float *__restrict__ qb, double *red,
+                  unsigned *ticket, double *scal, int *err) {
+  constexpr int DP = Rec<D>::DP;
+  const int i = blockIdx.x * NT_FIN + threadIdx.x;
+  double e = 0.0;
+  if (i < kp.N) {
+    const int t = i / sc.TI, il = i - t * sc.TI;
+    const int f = sched_first_cta((long long)t * sc.nchunk, sc);
+    const int l = sched_first_cta((long long)(t + 1) * sc.nchunk - 1, sc);
+    double rho = 0.0;
+    for (int g = 0; g <= l - f; ++g) rho += part[((size_t)t * sc.maxseg + g) * sc.TI + il];
+    if (!(rho >= 0.5 && rho <= 1e300)) vds_flag(err, VDS_ENAN);
+    rec[(size_t)i * DP + D] = (float)(1.0 / rho);
+    if (rho_out) rho_out[i] = (float)rho;
+    if (want_energy) {
+      double y[D];
+      float yf[D];
+      load_y<D>(ybase, ydelta, i, y, yf);
+      double psi, fk[8];
+      if (!spring_eval<D>(kp, y, psi, fk)) vds_flag(err, VDS_EDOMAIN);
+      e = kp.kBT * (log(rho) + kp.lnorm) + psi;
+      if (qa) {
+        double dl[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          dl[d] = (double)qa[(size_t)i * D + d] - (qb ? (double)qb[(size_t)i * D + d] : 0.0);
+        double quad = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int b = 0; b < D; ++b)
+            if (a % kp.s == b % kp.s) quad += dl[a] * rouse_Ainv(a / kp.s, b / kp.s, kp.nb) * dl[b];
+        e += kp.zeta / (2.0 * kp.dt) * quad;
+      }
+    }
+  }
+  if (want_energy) {
+    double v[1] = {e}, out[1];
+    const bool mx[1] = {false};
+    if (grid_reduce<1>(v, mx, red, ticket, out)) {
+      scal[SC_E] = out[0] / (double)kp.N;
+      if (!(fabs(scal[SC_E]) <= 1e300)) vds_flag(err, VDS_ENAN);
+    }
+  }
+}
+
+template <int D, int MODE>
+__global__ void __launch_bounds__(NT_FIN)
+    k_grad_finish(Sched sc, const double *__restrict__ part, float *__restrict__ rec, KParams kp,
+                  float *__restrict__ out, const float *ybase,
+                  const float *__restrict__ ydelta, const float *__restrict__ qa,
+                  const float *__restrict__ qb, float *q_io, double *red,
+                  unsigned *ticket, double *scal, int *err) {
+  constexpr int DP = Rec<D>::DP;
+  const int i = blockIdx.x * NT_FIN + threadIdx.x;
+  double dec = 0.0, dmax = 0.0, ymax = 0.0;
+  if (i < kp.N) {
+    const int t = i / sc.TI, il = i - t * sc.TI;
+    const int f = sched_first_cta((long long)t * sc.nchunk, sc);
+    const int l = sched_first_cta((long long)(t + 1) * sc.nchunk - 1, sc);
+    double g[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) g[a] = 0.0;
+    for (int s = 0; s <= l - f; ++s) {
+      const double *p = part + (((size_t)t * sc.maxseg + s) * sc.TI + il) * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a) g[a] += p[a];
+    }
+    double y[D];
+    float yf[D];
+    load_y<D>(ybase, ydelta, i, y, yf);
+    double psi, fk[8];
+    if (!spring_eval<D>(kp, y, psi, fk)) vds_flag(err, VDS_EDOMAIN);
+#pragma unroll
+    for (int a = 0; a < D; ++a) g[a] = kp.kBT * (-kp.sfac * g[a]) + fk[a / kp.s] * y[a];
+
+    if constexpr (MODE == GM_OUT) {
+      if (qa) {
+        double dl[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          dl[d] = (double)qa[(size_t)i * D + d] - (qb ? (double)qb[(size_t)i * D + d] : 0.0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          double v = 0.0;
+#pragma unroll
+          for (int b = 0; b < D; ++b)
+            if (a % kp.s == b % kp.s) v += rouse_Ainv(a / kp.s, b / kp.s, kp.nb) * dl[b];
+          g[a] += kp.zeta / kp.dt * v;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) out[(size_t)i * D + a] = (float)g[a];
+    } else if constexpr (MODE == GM_EXPLICIT) {
+      float yn[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int k = a / kp.s, al = a - k * kp.s;
+        double v = 0.0, m = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          const int kb = b / kp.s, be = b - kb * kp.s;
+          if (kb == k) v += kp.kappa[al * kp.s + be] * y[b];
+          if (be == al) m += rouse_A(k, kb) * g[b];
+        }
+        yn[a] = (float)(y[a] + kp.dt * (v - m / kp.zeta));
+      }
+      if (kp.spring == 1) {
+        for (int k = 0; k < kp.nb; ++k) {
+          double n2 = 0.0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+            if (a / kp.s == k) n2 += (double)yn[a] * yn[a];
+          if (!(n2 < kp.b)) vds_flag(err, VDS_EDOMAIN);
+        }
+      }
+      float o[DP];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        q_io[(size_t)i * D + a] = yn[a];
+        o[a] = kp.c * yn[a];
+      }
+#pragma unroll
+      for (int a = D; a < DP; ++a) o[a] = 0.f;
+      float4 *dst = reinterpret_cast<float4 *>(rec + (size_t)i * DP);
+#pragma unroll
+      for (int v = 0; v < DP / 4; ++v) dst[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+    } else {  // GM_IMPLICIT_DIR
+      double dl[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) dl[d] = (double)ydelta[(size_t)i * D + d];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int k = a / kp.s, al = a - k * kp.s;
+        double ag = 0.0, aid = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          const int kb = b / kp.s, be = b - kb * kp.s;
+          if (be == al) {
+            ag += rouse_A(k, kb) * g[b];
+            aid += rouse_Ainv(k, kb, kp.nb) * dl[b];
+          }
+        }
+        const double dr = dl[a] + kp.dt / kp.zeta * ag;
+        const double G = kp.zeta / kp.dt * aid + g[a];
+        const float drf = (float)dr;
+        out[(size_t)i * D + a] = drf;
+        dec += G * dr;
+        dmax = fmax(dmax, fabs((double)drf));
+        ymax = fmax(ymax, fabs((double)yf[a]));
+      }
+    }
+  }
+  if constexpr (MODE == GM_IMPLICIT_DIR) {
+    double v[3] = {dec, dmax, ymax}, o[3];
+    const bool mx[3] = {false, true, true};
+    if (grid_reduce<3>(v, mx, red, ticket, o)) {
+      scal[SC_DEC] = o[0] / (double)kp.N;
+      scal[SC_DMAX] = o[1];
+      scal[SC_YMAX] = o[2];
+      if (!(fabs(o[0]) <= 1e300)) vds_flag(err, VDS_ENAN);
+    }
+  }
+}
+
+// ------------------------------------------------------------ stress kernel
+
+constexpr int STRESS_BP = 128;  // particles staged per block iteration
+
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_stress(KParams kp, const float *__restrict__ q, double *red, unsigned *ticket, double *scal,
+             int *err) {
+  __shared__ float ys[STRESS_BP][D];
+  const int s = kp.s, ne_tau = s * s, ne = ne_tau + D * D;
+  double acc[2] = {0.0, 0.0};  // entries tid and tid+256
+  for (int base = blockIdx.x * STRESS_BP; base < kp.N; base += gridDim.x * STRESS_BP) {
+    __syncthreads();
+    for (int x = threadIdx.x; x < STRESS_BP * D; x += blockDim.x) {
+      const int p = x / D, d = x - p * D;
+      ys[p][d] = (base + p < kp.N) ? q[(size_t)(base + p) * D + d] : 0.f;
+    }
+    __syncthreads();
+    if (kp.spring == 1 && threadIdx.x < STRESS_BP && base + threadIdx.x < kp.N) {
+      const int p = threadIdx.x;
+      for (int k = 0; k < kp.nb; ++k) {
+        double n2 = 0.0;
+        for (int a = 0; a < s; ++a) n2 += (double)ys[p][s * k + a] * ys[p][s * k + a];
+        if (!(n2 < kp.b)) vds_flag(err, VDS_EDOMAIN);
+      }
+    }
+    const int np = min(STRESS_BP, kp.N - base);
+    for (int r = 0; r < 2; ++r) {
+      const int e = threadIdx.x + r * 256;
+      if (e >= ne) continue;
+      double a = 0.0;
+      if (e < ne_tau) {
+        const int al = e / s, be = e - al * s;
+        for (int p = 0; p < np; ++p) {
+          for (int k = 0; k < kp.nb; ++k) {
+            double f = kp.H[k];
+            if (kp.spring == 1) {
+              double n2 = 0.0;
+              for (int c = 0; c < s; ++c) n2 += (double)ys[p][s * k + c] * ys[p][s * k + c];
+              f = kp.H[k] / (1.0 - n2 / kp.b);
+            }
+            a += (double)ys[p][s * k + al] * f * (double)ys[p][s * k + be];
+          }
+        }
+      } else {
+        const int x = e - ne_tau, ra = x / D, rb = x - ra * D;
+        for (int p = 0; p < np; ++p) a += (double)ys[p][ra] * (double)ys[p][rb];
+      }
+      acc[r] += a;
+    }
+  }
+  // block partials of all entries, then ticketed final sum in block order
+  __shared__ bool last;
+  for (int r = 0; r < 2; ++r) {
+    const int e = threadIdx.x + r * 256;
+    if (e < ne) red[(size_t)blockIdx.x * ne + e] = acc[r];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    double x = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) x += __ldcg(red + (size_t)b * ne + e);
+    scal[SC_AUX + e] = x / (double)kp.N;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+template <int D>
+__global__ void k_flow(KParams kp, const float *__restrict__ q, float *__restrict__ qs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kp.N) return;
+  float y[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[a] = q[(size_t)i * D + a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int k = a / kp.s, al = a - k * kp.s;
+    double v = 0.0;
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+      if (b / kp.s == k) v += kp.kappa[al * kp.s + (b - k * kp.s)] * (double)y[b];
+    qs[(size_t)i * D + a] = (float)((double)y[a] + kp.dt * v);
+  }
+}
+
+// ------------------------------------------------------------ host plumbing
+
+template <int D, int RI, bool GRAD>
+int launch_pair(vds_ctx *c, int N, Sched &sc) {
+  constexpr int DP = Rec<D>::DP;
+  constexpr int ACC = GRAD ? D : 1;
+  constexpr int TI = NT_PAIR * RI;
+  const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
+  static int occ = -1;
+  if (occ < 0) {
+    int o = 0;
+    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, GRAD>, NT_PAIR, smem));
+    occ = o > 0 ? o : 1;
+  }
+  sc.TI = TI;
+  sc.Npad = (N + TJ - 1) / TJ * TJ;
+  sc.nchunk = sc.Npad / TJ;
+  sc.n_itiles = (N + TI - 1) / TI;
+  sc.items = (long long)sc.n_itiles * sc.nchunk;
+  const long long cap = (long long)c->num_sms * occ;
+  sc.G = (int)(sc.items < cap ? sc.items : cap);
+  int maxseg = 1;
+  for (int t = 0; t < sc.n_itiles; ++t) {
+    const int f = sched_first_cta((long long)t * sc.nchunk, sc);
+    const int l = sched_first_cta((long long)(t + 1) * sc.nchunk - 1, sc);
+    if (l - f + 1 > maxseg) maxseg = l - f + 1;
+  }
+  sc.maxseg = maxseg;
+  VDS_TRY(vds_ensure(c, c->part, (size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double)));
+  const int pk = GRAD ? PK_GRADIENT : PK_DENSITY;
+  VDS_TRY(vds_time_begin(c, pk));
+  k_pair<D, RI, GRAD><<<sc.G, NT_PAIR, smem, c->stream>>>((const float *)c->rec.ptr, sc,
+                                                           (double *)c->part.ptr, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  VDS_TRY(vds_time_end(c, pk));
+  ++c->launches;
+  return VDS_OK;
+}
+
+template <int D>
+int prep_impl(vds_ctx *c, const KParams &kp, const float *base, const float *delta,
+              const float *dir, float alpha, float *delta_out) {
+  const int Npad = (kp.N + TJ - 1) / TJ * TJ;
+  VDS_TRY(vds_ensure(c, c->rec, (size_t)Npad * Rec<D>::DP * sizeof(float)));
+  k_prep<D><<<(Npad + 255) / 256, 256, 0, c->stream>>>(kp.N, Npad, kp.c, base, delta, dir, alpha,
+                                                       delta_out, (float *)c->rec.ptr);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+template <int D>
+int density_impl(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
+                 const float *ybase, const float *ydelta, const float *qa, const float *qb) {
+  Sched sc;
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, false>(c, kp.N, sc)));
+  const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
+  VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
+  k_dens_finish<D><<<nb, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, (float *)c->rec.ptr,
+                                                 rho_out, kp, want_energy ? 1 : 0, ybase, ydelta, qa,
+                                                 qb, (double *)c->red.ptr, c->ticket + TK_DENS,
+                                                 c->scal, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+template <int D>
+int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,
+              const float *ydelta, const float *qa, const float *qb, float *q_io) {
+  Sched sc;
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, true>(c, kp.N, sc)));
+  const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
+  VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
+  const double *pp = (const double *)c->part.ptr;
+  float *rp = (float *)c->rec.ptr;
+  double *red = (double *)c->red.ptr;
+  unsigned *tk = c->ticket + TK_GRAD;
+  if (mode == GM_OUT)
+    k_grad_finish<D, GM_OUT><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta, qa, qb,
+                                                          q_io, red, tk, c->scal, c->err);
+  else if (mode == GM_EXPLICIT)
+    k_grad_finish<D, GM_EXPLICIT><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta, qa,
+                                                               qb, q_io, red, tk, c->scal, c->err);
+  else
+    k_grad_finish<D, GM_IMPLICIT_DIR><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta,
+                                                                   qa, qb, q_io, red, tk, c->scal,
+                                                                   c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+template <int D>
+int stress_impl(vds_ctx *c, const KParams &kp, const float *q, double *tau, double *qq) {
+  const int ne = kp.s * kp.s + D * D;
+  int nblk = (kp.N + STRESS_BP - 1) / STRESS_BP;
+  if (nblk > 2 * c->num_sms) nblk = 2 * c->num_sms;
+  VDS_TRY(vds_ensure(c, c->red, (size_t)nblk * ne * sizeof(double)));
+  k_stress<D><<<nblk, 256, 0, c->stream>>>(kp, q, (double *)c->red.ptr, c->ticket + TK_STRESS, c->scal,
+                                          c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  VDS_TRY(vds_sync_status(c));
+  for (int e = 0; e < kp.s * kp.s; ++e) tau[e] = c->h_scal[SC_AUX + e];
+  if (qq)
+    for (int e = 0; e < D * D; ++e) qq[e] = c->h_scal[SC_AUX + kp.s * kp.s + e];
+  return VDS_OK;
+}
+
+template <int D>
+int flow_impl(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
+  k_flow<D><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp, q, qs);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+}  // namespace vds_pair
+
+// One translation unit per supported D (pair_d<D>.cu) instantiates the passes
+// through this macro, so the library builds in parallel.
+#define VDS_PAIR_INSTANTIATE(DD)                                                              \
+  int vds_prep_##DD(vds_ctx *c, const KParams &kp, const float *base, const float *delta,     \
+                    const float *dir, float alpha, float *delta_out) {                        \
+    return vds_pair::prep_impl<DD>(c, kp, base, delta, dir, alpha, delta_out);                \
+  }                                                                                           \
+  int vds_density_##DD(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,       \
+                       const float *ybase, const float *ydelta, const float *qa,              \
+                       const float *qb) {                                                     \
+    return vds_pair::density_impl<DD>(c, kp, rho_out, want_energy, ybase, ydelta, qa, qb);    \
+  }                                                                                           \
+  int vds_grad_##DD(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,  \
+                    const float *ydelta, const float *qa, const float *qb, float *q_io) {     \
+    return vds_pair::grad_impl<DD>(c, kp, mode, out, ybase, ydelta, qa, qb, q_io);            \
+  }                                                                                           \
+  int vds_stress_##DD(vds_ctx *c, const KParams &kp, const float *q, double *tau, double *qq) { \
+    return vds_pair::stress_impl<DD>(c, kp, q, tau, qq);                                      \
+  }                                                                                           \
+  int vds_flow_##DD(vds_ctx *c, const KParams &kp, const float *q, float *qs) {               \
+    return vds_pair::flow_impl<DD>(c, kp, q, qs);                                             \
+  }

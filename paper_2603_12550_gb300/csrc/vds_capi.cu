@@ -1,0 +1,332 @@
+// vds_capi.cu -- the C ABI (include/vds.h): context, energy/gradient
+// evaluation, explicit and implicit time steps, stress.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "pair.cuh"
+
+namespace {
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_params(const vds_params *p, int N, int D) {
+  if (!p || N < 1 || D < 2 || D > VDS_MAXD) return VDS_EARG;
+  if (p->s < 2 || p->s > 3 || p->nb < 1 || p->nb > 8 || p->nb * p->s != D) return VDS_EARG;
+  if (!(p->h > 0.0) || !(p->zeta > 0.0) || !(p->kBT >= 0.0)) return VDS_EARG;
+  if (p->spring != 0 && p->spring != 1) return VDS_EARG;
+  if (p->spring == 1 && !(p->b > 0.0)) return VDS_EARG;
+  return VDS_OK;
+}
+
+// Copy the device scalars to the pinned mirror, synchronise, collect status.
+int read_scalars(vds_ctx *c) {
+  VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  return vds_sync_status(c);
+}
+
+float *vec(vds_ctx *c, int k, size_t nd) { return (float *)c->vecs.ptr + (size_t)k * nd; }
+
+}  // namespace
+
+void vds_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+int vds_ensure(vds_ctx *c, DevBuf &b, size_t bytes) {
+  if (bytes <= b.cap) return VDS_OK;
+  if (b.ptr) {
+    VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
+  }
+  const size_t want = bytes + bytes / 4 + 256;
+  VDS_CUDA_TRY(cudaMalloc(&b.ptr, want));
+  b.cap = want;
+  return VDS_OK;
+}
+
+static int timing_harvest(vds_ctx *c) {
+  TimingPool *t = c->timing;
+  if (!t) return VDS_OK;
+  VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int k = 0; k < PK_COUNT; ++k) {
+    for (int i = 0; i < t->used[k]; ++i) {
+      float ms = 0.f;
+      VDS_CUDA_TRY(cudaEventElapsedTime(&ms, t->ev[k][0][i], t->ev[k][1][i]));
+      t->ms[k] += ms;
+      t->count[k] += 1;
+    }
+    t->used[k] = 0;
+  }
+  return VDS_OK;
+}
+
+int vds_time_begin(vds_ctx *c, int pk) {
+  TimingPool *t = c->timing;
+  if (!t || !t->on) return VDS_OK;
+  if (t->used[pk] == 256) VDS_TRY(timing_harvest(c));
+  cudaEvent_t &e = t->ev[pk][0][t->used[pk]];
+  if (!e) VDS_CUDA_TRY(cudaEventCreate(&e));
+  VDS_CUDA_TRY(cudaEventRecord(e, c->stream));
+  return VDS_OK;
+}
+
+int vds_time_end(vds_ctx *c, int pk) {
+  TimingPool *t = c->timing;
+  if (!t || !t->on) return VDS_OK;
+  cudaEvent_t &e = t->ev[pk][1][t->used[pk]];
+  if (!e) VDS_CUDA_TRY(cudaEventCreate(&e));
+  VDS_CUDA_TRY(cudaEventRecord(e, c->stream));
+  t->used[pk] += 1;
+  return VDS_OK;
+}
+
+int vds_sync_status(vds_ctx *c) {
+  VDS_CUDA_TRY(cudaMemcpyAsync(c->h_err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int e = *c->h_err;
+  if (e != 0) {
+    VDS_CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  }
+  return e;
+}
+
+extern "C" {
+
+const char *vds_strerror(int st) {
+  switch (st) {
+    case VDS_OK: return "ok";
+    case VDS_EARG: return "invalid argument";
+    case VDS_ECUDA: return g_last_cuda != cudaSuccess ? cudaGetErrorString(g_last_cuda) : "CUDA error";
+    case VDS_EDOMAIN: return "FENE bond outside |q|^2 < b";
+    case VDS_ENOCONV: return "implicit minimiser did not converge";
+    case VDS_ENAN: return "non-finite density or energy";
+    case VDS_ETIMEOUT: return "bounded device wait gave up";
+    case VDS_ENOMEM: return "device allocation failed";
+    case VDS_ESURROGATE: return "surrogate check failed";
+    default: return "unknown status";
+  }
+}
+
+int vds_create(vds_ctx **out, void *stream, int device) {
+  if (!out) return VDS_EARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VDS_EARG;
+  DeviceGuard g(device);
+  if (!g.ok) return VDS_ECUDA;
+  vds_ctx *c = new vds_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  int st = VDS_OK;
+  do {
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    if (cudaMalloc(&c->err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->ticket, TK_COUNT * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&c->scal, SC_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_scal, SC_COUNT * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->ticket, 0, TK_COUNT * sizeof(unsigned), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->scal, 0, SC_COUNT * sizeof(double), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+  } while (0);
+  if (st != VDS_OK) {
+    vds_destroy(c);
+    return st;
+  }
+  *out = c;
+  return VDS_OK;
+}
+
+void vds_destroy(vds_ctx *c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  DevBuf *bufs[] = {&c->rec, &c->part, &c->red, &c->vecs, &c->gbuf};
+  for (DevBuf *b : bufs)
+    if (b->ptr) cudaFree(b->ptr);
+  if (c->err) cudaFree(c->err);
+  if (c->ticket) cudaFree(c->ticket);
+  if (c->scal) cudaFree(c->scal);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->timing) {
+    for (int k = 0; k < PK_COUNT; ++k)
+      for (int p = 0; p < 2; ++p)
+        for (int i = 0; i < 256; ++i)
+          if (c->timing->ev[k][p][i]) cudaEventDestroy(c->timing->ev[k][p][i]);
+    delete c->timing;
+  }
+  delete c;
+}
+
+int vds_set_stream(vds_ctx *c, void *stream) {
+  if (!c) return VDS_EARG;
+  DeviceGuard g(c->device);
+  VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)stream;
+  return VDS_OK;
+}
+
+int vds_timing(vds_ctx *c, int enable) {
+  if (!c) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  if (!c->timing) c->timing = new TimingPool();
+  VDS_TRY(timing_harvest(c));
+  TimingPool *t = c->timing;
+  for (int k = 0; k < PK_COUNT; ++k) {
+    t->ms[k] = 0.0;
+    t->count[k] = 0;
+  }
+  t->on = enable != 0;
+  c->launches = 0;
+  return VDS_OK;
+}
+
+int vds_timing_read(vds_ctx *c, double *ms, long *launches, long *total_launches) {
+  if (!c) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  if (c->timing) VDS_TRY(timing_harvest(c));
+  for (int k = 0; k < PK_COUNT; ++k) {
+    if (ms) ms[k] = c->timing ? c->timing->ms[k] : 0.0;
+    if (launches) launches[k] = c->timing ? c->timing->count[k] : 0;
+  }
+  if (total_launches) *total_launches = c->launches;
+  return VDS_OK;
+}
+
+int vds_energy_grad(vds_ctx *c, const float *q, int N, int D, const vds_params *p,
+                    const float *q_star, double *E, float *g, float *rho) {
+  if (!c || !q) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  if (q_star && !(p->dt > 0.0)) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  const float *qa = q_star ? q : nullptr;
+  VDS_TRY(pass_prep(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  VDS_TRY(pass_density(c, kp, rho, E != nullptr, q, nullptr, qa, q_star));
+  if (g) VDS_TRY(pass_grad(c, kp, GM_OUT, g, q, nullptr, qa, q_star, nullptr));
+  if (E) {
+    VDS_TRY(read_scalars(c));
+    *E = c->h_scal[SC_E];
+  }
+  return VDS_OK;
+}
+
+static int step_explicit(vds_ctx *c, float *q, const KParams &kp, int nsteps) {
+  VDS_TRY(pass_prep(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  for (int n = 0; n < nsteps; ++n) {
+    VDS_TRY(pass_density(c, kp, nullptr, false, q, nullptr, nullptr, nullptr));
+    VDS_TRY(pass_grad(c, kp, GM_EXPLICIT, nullptr, q, nullptr, nullptr, nullptr, q));
+  }
+  return vds_sync_status(c);
+}
+
+// Implicit Euler step as the minimiser of J (see vds.h).  y = q* + d is
+// carried through d = y - q*, which keeps the dissipation term of J accurate
+// in FP32.
+static int step_implicit(vds_ctx *c, float *q, const KParams &kp, const vds_params *p, int nsteps,
+                         int *iters_out) {
+  const size_t nd = (size_t)kp.N * kp.D;
+  VDS_TRY(vds_ensure(c, c->vecs, 4 * nd * sizeof(float)));
+  float *qs = vec(c, 0, nd), *d0 = vec(c, 1, nd), *d1 = vec(c, 2, nd), *dir = vec(c, 3, nd);
+  for (int n = 0; n < nsteps; ++n) {
+    VDS_TRY(pass_flow(c, kp, q, qs));
+    VDS_CUDA_TRY(cudaMemsetAsync(d0, 0, nd * sizeof(float), c->stream));
+    VDS_TRY(pass_prep(c, kp, qs, d0, nullptr, 0.f, nullptr));
+    VDS_TRY(pass_density(c, kp, nullptr, true, qs, d0, d0, nullptr));
+    VDS_TRY(read_scalars(c));
+    double J = c->h_scal[SC_E];
+    int it = 0;
+    bool converged = false;
+    while (it < p->max_iter) {
+      ++it;
+      VDS_TRY(pass_grad(c, kp, GM_IMPLICIT_DIR, dir, qs, d0, nullptr, nullptr, nullptr));
+      VDS_TRY(read_scalars(c));
+      const double dec = c->h_scal[SC_DEC], dmax = c->h_scal[SC_DMAX], ymax = c->h_scal[SC_YMAX];
+      if (dmax <= p->tol * (1.0 + ymax)) {
+        VDS_TRY(pass_prep(c, kp, qs, d0, dir, 1.f, d1));
+        float *t = d0;
+        d0 = d1;
+        d1 = t;
+        converged = true;
+        break;
+      }
+      double alpha = 1.0, Jn = 0.0;
+      bool acc = false;
+      for (int ls = 0; ls <= 30; ++ls) {
+        VDS_TRY(pass_prep(c, kp, qs, d0, dir, (float)alpha, d1));
+        VDS_TRY(pass_density(c, kp, nullptr, true, qs, d1, d1, nullptr));
+        const int st = read_scalars(c);
+        if (st != VDS_OK && st != VDS_EDOMAIN) return st;
+        Jn = c->h_scal[SC_E];
+        if (st == VDS_OK && Jn <= J - 1e-4 * alpha * dec + p->jfloor * (1.0 + fabs(J))) {
+          acc = true;
+          break;
+        }
+        alpha *= 0.5;
+      }
+      if (!acc) return VDS_ENOCONV;
+      float *t = d0;
+      d0 = d1;
+      d1 = t;
+      J = Jn;
+    }
+    if (iters_out) iters_out[n] = it;
+    VDS_TRY(pass_axpy(c, (int)nd, qs, d0, q));
+    if (!converged) {
+      VDS_TRY(vds_sync_status(c));
+      return VDS_ENOCONV;
+    }
+  }
+  return vds_sync_status(c);
+}
+
+int vds_step(vds_ctx *c, float *q, int N, int D, const vds_params *p, int nsteps, int *iters_out) {
+  if (!c || !q || nsteps < 0) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  if (!(p->dt > 0.0)) return VDS_EARG;
+  if (p->scheme == 1 && (p->max_iter < 1 || !(p->tol >= 0.0))) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  if (nsteps == 0) return VDS_OK;
+  if (p->scheme == 0) return step_explicit(c, q, kp, nsteps);
+  if (p->scheme == 1) return step_implicit(c, q, kp, p, nsteps, iters_out);
+  return VDS_EARG;
+}
+
+int vds_stress(vds_ctx *c, const float *q, int N, int D, const vds_params *p, double *tau,
+               double *qq) {
+  if (!c || !q || !tau) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  return pass_stress(c, kp, q, tau, qq);
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+"""Thin ctypes binding of the C ABI in include/vds.h.
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+arrays are passed as torch CUDA tensors (PyTorch provides device memory and
+streams) or raw integer device addresses.  Importing this module loads the
+compiled library and raises if it is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VDS_OK, VDS_EARG, VDS_ECUDA, VDS_EDOMAIN, VDS_ENOCONV = 0, -1, -2, -3, -4
+VDS_ENAN, VDS_ETIMEOUT, VDS_ENOMEM, VDS_ESURROGATE = -5, -6, -7, -8
+
+
+class VdsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _load():
+    path = _build.library_path()
+    if not os.path.exists(path):
+        raise ImportError(
+            f"CUDA library {path} is not built; run paper_2603_12550_gb300.build.build() "
+            "(or __graft_entry__.build()) first")
+    return ctypes.CDLL(path)
+
+
+lib = _load()
+
+
+class VdsParams(ctypes.Structure):
+    _fields_ = [("spring", ctypes.c_int), ("nb", ctypes.c_int), ("s", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("H", ctypes.c_double * 8),
+                ("b", ctypes.c_double), ("kBT", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double),
+                ("kappa", ctypes.c_double * 9), ("tol", ctypes.c_double),
+                ("jfloor", ctypes.c_double), ("scheme", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
+def params(nb, s, H=1.0, kBT=1.0, zeta=4.0, h=0.3, dt=0.0, kappa=None, spring=0, b=0.0,
+           tol=1e-6, max_iter=50, jfloor=1e-9, scheme=0) -> VdsParams:
+    p = VdsParams()
+    p.spring, p.nb, p.s, p.max_iter, p.scheme = int(spring), int(nb), int(s), int(max_iter), int(scheme)
+    Hs = np.broadcast_to(np.asarray(H, dtype=np.float64), (nb,))
+    for j in range(nb):
+        p.H[j] = float(Hs[j])
+    p.b, p.kBT, p.zeta, p.h, p.dt = float(b), float(kBT), float(zeta), float(h), float(dt)
+    p.tol, p.jfloor = float(tol), float(jfloor)
+    k = np.zeros((s, s)) if kappa is None else np.asarray(kappa, dtype=np.float64).reshape(s, s)
+    for c in range(s * s):
+        p.kappa[c] = float(k.flat[c])
+    return p
+
+
+_vp, _i, _l, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double
+_pp = ctypes.POINTER(VdsParams)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+_SIGS = {
+    "vds_create": ([ctypes.POINTER(_vp), _vp, _i], _i),
+    "vds_destroy": ([_vp], None),
+    "vds_set_stream": ([_vp, _vp], _i),
+    "vds_strerror": ([_i], ctypes.c_char_p),
+    "vds_bandwidth": ([_vp, _vp, _i, _i, _i, _dp], _i),
+    "vds_energy_grad": ([_vp, _vp, _i, _i, _pp, _vp, _dp, _vp, _vp], _i),
+    "vds_step": ([_vp, _vp, _i, _i, _pp, _i, _ip], _i),
+    "vds_stress": ([_vp, _vp, _i, _i, _pp, _dp, _dp], _i),
+    "vds_timing": ([_vp, _i], _i),
+    "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
+    "pod_build": ([_vp, _vp, _l, _i, _i, _d, _i, _i, _dp, ctypes.POINTER(_vp), _ip], _i),
+    "pod_info": ([_vp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_l)], _i),
+    "pod_eigenvalues": ([_vp, _dp, _i], _i),
+    "pod_xh": ([_vp, _dp], _i),
+    "pod_project": ([_vp, _vp, _vp, _i, _i, _vp], _i),
+    "pod_lift": ([_vp, _vp, _vp, _i, _i, _vp], _i),
+    "pod_free": ([_vp], None),
+}
+for _name, (_args, _res) in _SIGS.items():
+    if hasattr(lib, _name):
+        _f = getattr(lib, _name)
+        _f.argtypes = _args
+        _f.restype = _res
+
+
+def exported_symbols():
+    return [n for n in _SIGS if hasattr(lib, n)]
+
+
+def strerror(code) -> str:
+    return lib.vds_strerror(int(code)).decode()
+
+
+def _check(code):
+    if code != VDS_OK:
+        raise VdsError(code, strerror(code))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """Owns a vds_ctx bound to a device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = _vp()
+        _check(lib.vds_create(ctypes.byref(h), _stream_handle(stream), int(device)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib.vds_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(lib.vds_set_stream(self.h, _stream_handle(stream)))
+
+    # -- calls (names follow include/vds.h) --------------------------------
+    def vds_timing(self, enable=True):
+        _check(lib.vds_timing(self.h, 1 if enable else 0))
+
+    def vds_timing_read(self):
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_long * 4)()
+        tot = ctypes.c_long()
+        _check(lib.vds_timing_read(self.h, ms, n, ctypes.byref(tot)))
+        return list(ms), list(n), tot.value
+
+    def vds_bandwidth(self, q, rule=0) -> float:
+        N, D = q.shape
+        h = ctypes.c_double()
+        _check(lib.vds_bandwidth(self.h, _ptr(q), N, D, int(rule), ctypes.byref(h)))
+        return h.value
+
+    def vds_energy_grad(self, q, p: VdsParams, g=None, rho=None, q_star=None, want_energy=True):
+        N, D = q.shape
+        E = ctypes.c_double()
+        _check(lib.vds_energy_grad(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(q_star),
+                                   ctypes.byref(E) if want_energy else None, _ptr(g), _ptr(rho)))
+        return E.value if want_energy else None
+
+    def vds_step(self, q, p: VdsParams, nsteps=1, want_iters=False):
+        N, D = q.shape
+        it = (ctypes.c_int * max(1, nsteps))() if want_iters else None
+        code = lib.vds_step(self.h, _ptr(q), N, D, ctypes.byref(p), int(nsteps), it)
+        _check(code)
+        return list(it[:nsteps]) if want_iters else None
+
+    def vds_stress(self, q, p: VdsParams):
+        N, D = q.shape
+        tau = (ctypes.c_double * 9)()
+        qq = (ctypes.c_double * (D * D))()
+        _check(lib.vds_stress(self.h, _ptr(q), N, D, ctypes.byref(p), tau, qq))
+        s = p.s
+        return (np.array(tau[:s * s]).reshape(s, s), np.array(qq[:]).reshape(D, D))
+
+    def pod_build(self, X, Ns, M, s, energy=0.9999, r_max=64, r_fixed=0, kappa=None):
+        kap = np.zeros(9) if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64).ravel()
+        kbuf = (ctypes.c_double * 9)(*[float(v) for v in kap[:s * s]] + [0.0] * (9 - s * s))
+        out = _vp()
+        r = ctypes.c_int()
+        _check(lib.pod_build(self.h, _ptr(X), int(Ns), int(M), int(s), float(energy), int(r_max),
+                             int(r_fixed), kbuf, ctypes.byref(out), ctypes.byref(r)))
+        return PodBasis(out, M), r.value
+
+    def pod_project(self, basis: "PodBasis", q, p_out):
+        N, D = q.shape
+        _check(lib.pod_project(self.h, basis.h, _ptr(q), N, D, _ptr(p_out)))
+
+    def pod_lift(self, basis: "PodBasis", p_in, q_out):
+        N, D = q_out.shape
+        _check(lib.pod_lift(self.h, basis.h, _ptr(p_in), N, D, _ptr(q_out)))
+
+
+class PodBasis:
+    def __init__(self, h, M):
+        self.h = h
+        self.M = M
+
+    def info(self):
+        r, ld, phi, Ns = ctypes.c_int(), ctypes.c_int(), _vp(), ctypes.c_long()
+        _check(lib.pod_info(self.h, ctypes.byref(r), ctypes.byref(ld), ctypes.byref(phi), ctypes.byref(Ns)))
+        return dict(r=r.value, ld=ld.value, phi=phi.value, Ns=Ns.value)
+
+    def eigenvalues(self):
+        buf = (ctypes.c_double * self.M)()
+        _check(lib.pod_eigenvalues(self.h, buf, self.M))
+        return np.array(buf[:])
+
+    def xh(self):
+        r = self.info()["r"]
+        buf = (ctypes.c_double * (r * r))()
+        _check(lib.pod_xh(self.h, buf))
+        return np.array(buf[:]).reshape(r, r)
+
+    def phi(self):
+        """Copy of Phi as an (N s) x r torch tensor (device)."""
+        import torch
+        inf = self.info()
+        Ns, r, ld = inf["Ns"], inf["r"], inf["ld"]
+        buf = torch.empty((Ns, ld), dtype=torch.float32, device="cuda")
+        cudart_copy(buf.data_ptr(), inf["phi"], Ns * ld * 4)
+        return buf[:, :r].contiguous()
+
+    def free(self):
+        if self.h:
+            lib.pod_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def cudart_copy(dst, src, nbytes):
+    """Device-to-device copy of raw addresses through torch (plumbing only)."""
+    import torch
+    t_src = torch.as_tensor(_DeviceBuffer(src, nbytes), device="cuda")
+    t_dst = torch.as_tensor(_DeviceBuffer(dst, nbytes), device="cuda")
+    t_dst.copy_(t_src)
+    torch.cuda.current_stream().synchronize()
+
+
+class _DeviceBuffer:
+    """Minimal __cuda_array_interface__ wrapper for a raw device address."""
+
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = {
+            "shape": (int(nbytes),), "typestr": "|u1", "data": (int(ptr), False), "version": 3,
+            "strides": None}
