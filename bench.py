@@ -118,7 +118,24 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def _oracle_rate(wl, target_s=12.0, max_n=16384):
+def _profiled_traffic():
+    """DRAM bytes per gradient-pass launch from the committed ncu summary, or
+    None when the kernel source changed since those counters were taken."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2603_12550_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in ("pair_impl.cuh", "vds_internal.cuh"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_pair_traffic.txt")) as fh:
+            tag, nbytes = fh.read().split()[:2]
+    except (OSError, ValueError):
+        return None
+    return int(nbytes) if tag == h.hexdigest()[:12] else None
+
+
+def _oracle_rate(wl, target_s=12.0, max_n=65536):
     """FP64 oracle explicit step on the first n particles of the same cloud;
     returns (ordered pairs per second across both passes, n, seconds, cores)."""
     import oracle
@@ -149,7 +166,7 @@ def run_reference(a, wl, rank):
     q = inputs.equilibrium_cloud(wl["N"], wl["nb"], wl["s"], H=wl["H"], seed=wl["seed"]).astype(np.float64)
     p = oracle.params(wl["nb"], wl["s"], H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=wl["_h"],
                       dt=wl["dt"], kappa=inputs.shear_kappa(wl["s"], wl["rate"]))
-    n = 4096
+    n = 16384
     sample = q[:n].copy()
     for _ in range(a.warmup):
         sample = oracle.explicit_steps(sample, p, 1)
@@ -280,7 +297,7 @@ def main():
     t_dens = pass_ms[0] / max(1, pass_n[0]) / 1e3
     ops_grad = float(N) * N * (3 * D + 2)
     ops_dens = float(N) * N * (2 * D + 1)
-    traffic = None
+    traffic = _profiled_traffic()
     roof = {"bound": "alu", "kernel": "k_pair<D=9,GRAD> (gradient pair pass)",
             "achieved": ops_grad / t_grad / 1e12, "peak": peak_tops,
             "unit": "TOP/s (FP32 lane-ops)", "frac": ops_grad / t_grad / 1e12 / peak_tops,

@@ -79,6 +79,14 @@ VDS_API void vds_destroy(vds_ctx *ctx);
 VDS_API int vds_set_stream(vds_ctx *ctx, void *cuda_stream);
 VDS_API const char *vds_strerror(int status);
 
+/* Kernel bandwidth (Sec. 2.2).  rule 0: median rule of Eq. model_bandwidth,
+ * h = med_{J<K} |q_J - q_K| / sqrt(2 ln N), med the lower middle order
+ * statistic of the N(N-1)/2 distances (exact selection on FP32 squared
+ * distances).  rule 1: Silverman, h = sigma (4/((D+2)N))^(1/(D+4)) with sigma
+ * the mean per-coordinate sample standard deviation.  N >= 2.  *h: host. */
+VDS_API int vds_bandwidth(vds_ctx *ctx, const float *q, int N, int D, int rule,
+                  double *h);
+
 /* Density and free-energy gradient (Eq. model_DeteParAppr, Eq. model_DymRepPar).
  *   rho_I = sum_J exp(-|q_I - q_J|^2 / 2h^2)   (self term included)
  *   S_I   = -(1/h^2) sum_J khat_IJ (q_I - q_J)(1/rho_I + 1/rho_J)
