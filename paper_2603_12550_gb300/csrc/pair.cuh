@@ -53,9 +53,10 @@ int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy
                  const float *qb);
 
 // Gradient pass (records must hold w from pass_density) and its epilogues.
-enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2 };
+enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2, GM_VEL = 3 };
 // GM_OUT: g = kBT S + grad Psi(y) (+ (zeta/dt)(A^-1 (x) I)(qa - qb) if qa).
 // GM_EXPLICIT: q_io += dt [kappa q - (1/zeta)(A (x) I) g]; rebuild records.
+// GM_VEL: out = kappa y - (1/zeta)(A (x) I) g (the particle velocity).
 // GM_IMPLICIT_DIR: dir = d + (dt/zeta)(A (x) I) g with d = ydelta, and
 //   scal[SC_DEC] = (1/N) sum <G, dir>, G = (zeta/dt)(A^-1 (x) I) d + g,
 //   scal[SC_DMAX] = max|dir|, scal[SC_YMAX] = max|y|.

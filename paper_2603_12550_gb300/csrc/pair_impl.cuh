@@ -409,6 +409,19 @@ __global__ void __launch_bounds__(NT_FIN)
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) out[(size_t)i * D + a] = (float)g[a];
+    } else if constexpr (MODE == GM_VEL) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int k = a / kp.s, al = a - k * kp.s;
+        double v = 0.0, m = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          const int kb = b / kp.s, be = b - kb * kp.s;
+          if (kb == k) v += kp.kappa[al * kp.s + be] * y[b];
+          if (be == al) m += rouse_A(k, kb) * g[b];
+        }
+        out[(size_t)i * D + a] = (float)(v - m / kp.zeta);
+      }
     } else if constexpr (MODE == GM_EXPLICIT) {
       float yn[D];
 #pragma unroll
@@ -657,6 +670,9 @@ int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *
   else if (mode == GM_EXPLICIT)
     k_grad_finish<D, GM_EXPLICIT><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta, qa,
                                                                qb, q_io, red, tk, c->scal, c->err);
+  else if (mode == GM_VEL)
+    k_grad_finish<D, GM_VEL><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta, qa, qb,
+                                                          q_io, red, tk, c->scal, c->err);
   else
     k_grad_finish<D, GM_IMPLICIT_DIR><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta,
                                                                    qa, qb, q_io, red, tk, c->scal,

@@ -1,0 +1,883 @@
+// pod.cu -- POD by the method of snapshots (Sec. 2.3, Sec. 3.1) and the
+// project / lift maps of Eq. model_pq, for GB300 (sm_103a).
+//
+// pod_build:
+//   C = X^T X            FP32 snapshots, exact FP64 products and sums (the
+//                        upper-triangle 64x64 tiles, k split across CTAs,
+//                        partials combined in a fixed order)
+//   C = V Lambda V^T     two-sided cyclic Jacobi in FP64 with the round-robin
+//                        ordering: each round applies M/2 disjoint rotations
+//                        in one launch (block (a,b) of A' = R_a^T A_ab R_b)
+//   r                    energy rule on the sorted eigenvalues (FP64 prefix
+//                        sums in descending order), or r_fixed
+//   Phi = X V_r Lambda_r^(-1/2)   FP64 accumulation, stored FP32
+//   Cholesky-QR          G = Phi^T Phi, G = L L^T, Phi <- Phi L^-T
+//   sign                 largest-|.| entry of each column made positive
+//   X^H = Phi^T (I (x) kappa) Phi (Sec. 2.4)
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "pod_internal.cuh"
+
+
+
+namespace {
+
+struct KappaArg {
+  double k[9];
+};
+
+constexpr int GT = 64;   // Gram tile (columns)
+constexpr int GK = 32;   // Gram k-step
+
+// ------------------------------------------------------------------ Gram
+
+__global__ void __launch_bounds__(256)
+    k_gram_x(const float *__restrict__ X, long Ns, int M, int nbt, long kchunk,
+             double *__restrict__ part) {
+  const int bi = blockIdx.x / nbt, bj = blockIdx.x - (blockIdx.x / nbt) * nbt;
+  if (bi > bj) return;
+  const long k0 = (long)blockIdx.y * kchunk;
+  const long k1 = min(Ns, k0 + kchunk);
+  __shared__ float As[GK][GT + 1], Bs[GK][GT + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long kb = k0; kb < k1; kb += GK) {
+#pragma unroll
+    for (int u = 0; u < (GK * GT) / 256; ++u) {
+      const int e = tid + 256 * u, kk = e & (GK - 1), c = e / GK;
+      const long row = kb + kk;
+      const int ca = bi * GT + c, cb = bj * GT + c;
+      As[kk][c] = (row < k1 && ca < M) ? X[row + (long)ca * Ns] : 0.f;
+      Bs[kk][c] = (row < k1 && cb < M) ? X[row + (long)cb * Ns] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = (double)As[kk][tx * 4 + i];
+        b[i] = (double)Bs[kk][ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *dst = part + ((size_t)blockIdx.y * nbt * nbt + blockIdx.x) * (GT * GT);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(tx * 4 + i) * GT + ty * 4 + j] = acc[i][j];
+}
+
+// C (M x M, FP64) = sum over k-splits of the tile partials; symmetric fill.
+__global__ void k_gram_reduce(const double *__restrict__ part, int M, int nbt, int nks,
+                              double *__restrict__ C) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * M) return;
+  const int i = (int)(idx / M), j = (int)(idx - (long)(idx / M) * M);
+  const int ii = i <= j ? i : j, jj = i <= j ? j : i;
+  const int bi = ii / GT, bj = jj / GT;
+  const size_t off = (size_t)(bi * nbt + bj) * (GT * GT) + (ii - bi * GT) * GT + (jj - bj * GT);
+  double v = 0.0;
+  for (int k = 0; k < nks; ++k) v += part[(size_t)k * nbt * nbt * (GT * GT) + off];
+  C[idx] = v;
+}
+
+// ------------------------------------------------------------------ Jacobi
+
+__device__ __forceinline__ void jac_pair(int a, int rnd, int Mp, int &p, int &q) {
+  if (a == 0) {
+    p = rnd;
+    q = Mp - 1;
+  } else {
+    p = (rnd + a) % (Mp - 1);
+    q = (rnd - a + Mp - 1) % (Mp - 1);
+  }
+  if (p > q) {
+    const int t = p;
+    p = q;
+    q = t;
+  }
+}
+
+// Rotation R = [[c, s], [-s, c]] on (p, q) with R^T A R zeroing the (p, q)
+// entry (classical Jacobi with the smaller rotation angle).
+__device__ __forceinline__ void jac_rot(const double *A, int M, int p, int q, double &c, double &s) {
+  c = 1.0;
+  s = 0.0;
+  if (q >= M) return;
+  const double apq = A[(size_t)p * M + q];
+  if (apq == 0.0) return;
+  const double app = A[(size_t)p * M + p], aqq = A[(size_t)q * M + q];
+  if (fabs(apq) <= 1e-300 * (fabs(app) + fabs(aqq))) return;
+  const double theta = (aqq - app) / (2.0 * apq);
+  double t;
+  if (fabs(theta) > 1e150) t = 0.5 / theta;
+  else t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+  c = 1.0 / sqrt(t * t + 1.0);
+  s = t * c;
+}
+
+__global__ void __launch_bounds__(256)
+    k_jacobi_round(const double *__restrict__ A, double *__restrict__ A2, const double *__restrict__ V,
+                   double *__restrict__ V2, int M, int Mp, int rnd) {
+  const int H = Mp / 2;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nA = (long)H * H;
+  if (idx < nA) {
+    const int a = (int)(idx / H), b = (int)(idx - (long)(idx / H) * H);
+    int p, q, p2, q2;
+    jac_pair(a, rnd, Mp, p, q);
+    jac_pair(b, rnd, Mp, p2, q2);
+    double ca, sa, cb, sb;
+    jac_rot(A, M, p, q, ca, sa);
+    jac_rot(A, M, p2, q2, cb, sb);
+    auto get = [&](int i, int j) -> double { return (i < M && j < M) ? A[(size_t)i * M + j] : 0.0; };
+    const double x00 = get(p, p2), x01 = get(p, q2), x10 = get(q, p2), x11 = get(q, q2);
+    const double t00 = ca * x00 - sa * x10, t01 = ca * x01 - sa * x11;
+    const double t10 = sa * x00 + ca * x10, t11 = sa * x01 + ca * x11;
+    double y00 = t00 * cb - t01 * sb, y01 = t00 * sb + t01 * cb;
+    double y10 = t10 * cb - t11 * sb, y11 = t10 * sb + t11 * cb;
+    if (a == b) {
+      y01 = 0.0;
+      y10 = 0.0;
+    }
+    if (p < M && p2 < M) A2[(size_t)p * M + p2] = y00;
+    if (p < M && q2 < M) A2[(size_t)p * M + q2] = y01;
+    if (q < M && p2 < M) A2[(size_t)q * M + p2] = y10;
+    if (q < M && q2 < M) A2[(size_t)q * M + q2] = y11;
+  } else {
+    const long v = idx - nA;
+    if (v >= (long)M * H) return;
+    const int i = (int)(v / H), b = (int)(v - (long)(v / H) * H);
+    int p2, q2;
+    jac_pair(b, rnd, Mp, p2, q2);
+    double cb, sb;
+    jac_rot(A, M, p2, q2, cb, sb);
+    if (q2 >= M) {
+      if (p2 < M) V2[(size_t)i * M + p2] = V[(size_t)i * M + p2];
+      return;
+    }
+    const double vp = V[(size_t)i * M + p2], vq = V[(size_t)i * M + q2];
+    V2[(size_t)i * M + p2] = vp * cb - vq * sb;
+    V2[(size_t)i * M + q2] = vp * sb + vq * cb;
+  }
+}
+
+__global__ void k_identity(double *V, int M) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (long)M * M) V[idx] = (idx / M == idx % M) ? 1.0 : 0.0;
+}
+
+// off-diagonal and total squared Frobenius norms -> scal[SC_AUX], scal[SC_AUX+1]
+__global__ void __launch_bounds__(256)
+    k_offnorm(const double *__restrict__ A, int M, double *red, unsigned *ticket, double *scal) {
+  __shared__ double sh[8][2];
+  __shared__ bool last;
+  double off = 0.0, tot = 0.0;
+  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long)M * M;
+       idx += (long)gridDim.x * blockDim.x) {
+    const double v = A[idx];
+    tot += v * v;
+    if (idx / M != idx % M) off += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off += __shfl_xor_sync(0xffffffffu, off, o);
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5][0] = off;
+    sh[threadIdx.x >> 5][1] = tot;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double o = 0.0, t = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      o += sh[w][0];
+      t += sh[w][1];
+    }
+    red[2 * blockIdx.x] = o;
+    red[2 * blockIdx.x + 1] = t;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  double o = 0.0, t = 0.0;
+  for (unsigned b = 0; b < gridDim.x; ++b) {
+    o += __ldcg(red + 2 * b);
+    t += __ldcg(red + 2 * b + 1);
+  }
+  scal[SC_AUX] = o;
+  scal[SC_AUX + 1] = t;
+  *ticket = 0u;
+}
+
+// ------------------------------------------------------- sort and rank rule
+
+// Sort eigenvalues descending (ties: lower index first), choose r, and build
+// W = V[:, order[t]] / sqrt(lambda_t) for t < r (M x 64, FP64).
+__global__ void __launch_bounds__(1024)
+    k_eig_sort(const double *__restrict__ A, const double *__restrict__ V, int M, double energy,
+               int r_max, int r_fixed, double *lam_sorted, int *order, double *W, double *scal) {
+  __shared__ int r_sh;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) {
+    const double li = A[(size_t)i * M + i];
+    int rank = 0;
+    for (int j = 0; j < M; ++j) {
+      const double lj = A[(size_t)j * M + j];
+      rank += (lj > li) || (lj == li && j < i);
+    }
+    order[rank] = i;
+    lam_sorted[rank] = li;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < M; ++k) tot += lam_sorted[k];
+    int r;
+    if (r_fixed > 0) {
+      r = r_fixed < M ? r_fixed : M;
+    } else {
+      r = M;
+      double cum = 0.0;
+      for (int k = 0; k < M; ++k) {
+        cum += lam_sorted[k];
+        if (cum >= energy * tot) {
+          r = k + 1;
+          break;
+        }
+      }
+      if (r > r_max) r = r_max;
+    }
+    // modes whose eigenvalue is not resolved in FP64 cannot be normalised
+    int rp = 0;
+    while (rp < r && lam_sorted[rp] > 1e-13 * lam_sorted[0] && lam_sorted[rp] > 0.0) ++rp;
+    scal[SC_AUX + 2] = (double)r;
+    scal[SC_AUX + 3] = (double)rp;
+    r_sh = rp;
+  }
+  __syncthreads();
+  const int r = r_sh;
+  for (int idx = threadIdx.x; idx < M * 64; idx += blockDim.x) {
+    const int m = idx / 64, t = idx - (idx / 64) * 64;
+    W[idx] = t < r ? V[(size_t)m * M + order[t]] / sqrt(lam_sorted[t]) : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- basis
+
+constexpr int BT = 16;  // basis columns per CTA
+constexpr int BM = 128; // W rows staged per step
+
+// Phi[row, t] = sum_m X[row + m Ns] W[m, t]  (FP64 accumulation)
+__global__ void __launch_bounds__(256)
+    k_basis(const float *__restrict__ X, long Ns, int M, const double *__restrict__ W, int r, int ld,
+            float *__restrict__ phi) {
+  __shared__ double Ws[BM][BT];
+  const long row = (long)blockIdx.x * 256 + threadIdx.x;
+  const int t0 = blockIdx.y * BT;
+  double acc[BT];
+#pragma unroll
+  for (int t = 0; t < BT; ++t) acc[t] = 0.0;
+  for (int m0 = 0; m0 < M; m0 += BM) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < BM * BT; e += 256) {
+      const int mm = e / BT, t = e - (e / BT) * BT;
+      Ws[mm][t] = (m0 + mm < M) ? W[(size_t)(m0 + mm) * 64 + t0 + t] : 0.0;
+    }
+    __syncthreads();
+    if (row < Ns) {
+      const int mend = min(BM, M - m0);
+      for (int mm = 0; mm < mend; ++mm) {
+        const double x = (double)X[row + (long)(m0 + mm) * Ns];
+#pragma unroll
+        for (int t = 0; t < BT; ++t) acc[t] = fma(x, Ws[mm][t], acc[t]);
+      }
+    }
+  }
+  if (row < Ns) {
+#pragma unroll
+    for (int t = 0; t < BT; ++t)
+      if (t0 + t < ld) phi[row * ld + t0 + t] = (t0 + t < r) ? (float)acc[t] : 0.f;
+  }
+}
+
+// ------------------------------------------------- tall-skinny Gram A^T B
+
+constexpr int TR = 32;  // rows per tile
+
+// partial[blk][64x64] = sum over the block's rows of A[row,:]^T B[row,:]
+__global__ void __launch_bounds__(256)
+    k_tsgram(const float *__restrict__ A, const float *__restrict__ B, long Ns, int ld, long rchunk,
+             double *__restrict__ part) {
+  __shared__ float As[TR][64], Bs[TR][64];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const long r0 = (long)blockIdx.x * rchunk, r1 = min(Ns, r0 + rchunk);
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (long rb = r0; rb < r1; rb += TR) {
+    for (int e = tid; e < TR * 64; e += 256) {
+      const int rr = e / 64, c = e - (e / 64) * 64;
+      const long row = rb + rr;
+      const bool ok = row < r1 && c < ld;
+      As[rr][c] = ok ? A[row * ld + c] : 0.f;
+      Bs[rr][c] = ok ? B[row * ld + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < TR; ++rr) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = (double)As[rr][tx * 4 + i];
+        b[i] = (double)Bs[rr][ty * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double *dst = part + (size_t)blockIdx.x * 4096;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dst[(tx * 4 + i) * 64 + ty * 4 + j] = acc[i][j];
+}
+
+__global__ void k_tsgram_reduce(const double *__restrict__ part, int nblk, int r,
+                                double *__restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= r * r) return;
+  const int i = idx / r, j = idx - (idx / r) * r;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * 4096 + i * 64 + j];
+  G[idx] = v;
+}
+
+// Cholesky G = L L^T (FP64, one thread) and Linv = L^-1; failure flags.
+__global__ void k_chol_inv(const double *__restrict__ G, int r, double *__restrict__ Linv,
+                           int *err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double L[64 * 64];
+  for (int i = 0; i < r * r; ++i) L[i] = 0.0;
+  for (int j = 0; j < r; ++j) {
+    double d = G[j * r + j];
+    for (int k = 0; k < j; ++k) d -= L[j * r + k] * L[j * r + k];
+    if (!(d > 0.0)) {
+      vds_flag(err, VDS_ENAN);
+      return;
+    }
+    const double ljj = sqrt(d);
+    L[j * r + j] = ljj;
+    for (int i = j + 1; i < r; ++i) {
+      double v = G[i * r + j];
+      for (int k = 0; k < j; ++k) v -= L[i * r + k] * L[j * r + k];
+      L[i * r + j] = v / ljj;
+    }
+  }
+  // forward substitution column by column: L X = I
+  for (int c = 0; c < r; ++c) {
+    for (int i = 0; i < r; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) v -= L[i * r + k] * Linv[k * r + c];
+      Linv[i * r + c] = (i >= c) ? v / L[i * r + i] : 0.0;
+    }
+  }
+}
+
+// Phi[row, t] <- sum_{u <= t} Phi[row, u] Linv[t, u]  (Phi L^-T)
+__global__ void __launch_bounds__(256)
+    k_apply_linv(float *__restrict__ phi, long Ns, int ld, int r, const double *__restrict__ Linv) {
+  __shared__ double Ls[64 * 64];
+  for (int e = threadIdx.x; e < r * r; e += 256) Ls[e] = Linv[e];
+  __syncthreads();
+  const long row = (long)blockIdx.x * 256 + threadIdx.x;
+  if (row >= Ns) return;
+  float x[64];
+  for (int u = 0; u < r; ++u) x[u] = phi[row * ld + u];
+  for (int t = 0; t < r; ++t) {
+    double v = 0.0;
+    for (int u = 0; u <= t; ++u) v = fma((double)x[u], Ls[t * r + u], v);
+    phi[row * ld + t] = (float)v;
+  }
+}
+
+// --------------------------------------------------------------- sign fix
+
+// per block and column: largest |phi| and its (lowest) row
+__global__ void __launch_bounds__(256)
+    k_colmax(const float *__restrict__ phi, long Ns, int ld, int r, long rchunk, float *bmax,
+             long *brow) {
+  __shared__ float sv[256];
+  __shared__ long sr[256];
+  const long r0 = (long)blockIdx.x * rchunk, r1 = min(Ns, r0 + rchunk);
+  for (int t = 0; t < r; ++t) {
+    float best = -1.f;
+    long brw = 0x7fffffffffffffffL;
+    for (long row = r0 + threadIdx.x; row < r1; row += 256) {
+      const float v = fabsf(phi[row * ld + t]);
+      if (v > best) {
+        best = v;
+        brw = row;
+      }
+    }
+    sv[threadIdx.x] = best;
+    sr[threadIdx.x] = brw;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const float v2 = sv[threadIdx.x + o];
+        const long r2 = sr[threadIdx.x + o];
+        if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && r2 < sr[threadIdx.x])) {
+          sv[threadIdx.x] = v2;
+          sr[threadIdx.x] = r2;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      bmax[(size_t)blockIdx.x * 64 + t] = sv[0];
+      brow[(size_t)blockIdx.x * 64 + t] = sr[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_colsign(const float *__restrict__ phi, int ld, int r, int nblk,
+                          const float *__restrict__ bmax, const long *__restrict__ brow,
+                          float *__restrict__ sgn) {
+  const int t = threadIdx.x;
+  if (t >= r) return;
+  float best = -1.f;
+  long brw = 0x7fffffffffffffffL;
+  for (int b = 0; b < nblk; ++b) {
+    const float v = bmax[(size_t)b * 64 + t];
+    const long rw = brow[(size_t)b * 64 + t];
+    if (v > best || (v == best && rw < brw)) {
+      best = v;
+      brw = rw;
+    }
+  }
+  sgn[t] = (best > 0.f && phi[brw * ld + t] < 0.f) ? -1.f : 1.f;
+}
+
+__global__ void k_colscale(float *__restrict__ phi, long Ns, int ld, int r, const float *__restrict__ sgn) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * ld) return;
+  const int t = (int)(idx % ld);
+  if (t < r) phi[idx] *= sgn[t];
+}
+
+// (I (x) kappa) Phi: out[(I a), t] = sum_b kappa[a][b] Phi[(I b), t]
+__global__ void k_kappa_phi(const float *__restrict__ phi, long Ns, int ld, int s, KappaArg kap,
+                            float *__restrict__ out) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Ns * ld) return;
+  const long row = idx / ld;
+  const int t = (int)(idx - row * ld);
+  const long I = row / s;
+  const int a = (int)(row - I * s);
+  double v = 0.0;
+  for (int b = 0; b < s; ++b) v += kap.k[a * s + b] * (double)phi[(I * s + b) * ld + t];
+  out[idx] = (float)v;
+}
+
+// ------------------------------------------------------- project and lift
+
+constexpr int PJ_PART = 32;  // particles per CTA
+
+// partial[blk][t*nb + k] = sum over the block's particles of
+//   sum_a Phi[(I s + a), t] q[I D + s k + a]
+__global__ void __launch_bounds__(256)
+    k_project(const float *__restrict__ phi, int ld, int r, const float *__restrict__ q, int N, int D,
+              int s, int nb, double *__restrict__ part) {
+  extern __shared__ float psm[];
+  float *ph = psm;                    // PJ_PART * s * ld
+  float *qs = psm + PJ_PART * s * ld; // PJ_PART * D
+  const int I0 = blockIdx.x * PJ_PART;
+  const int np = min(PJ_PART, N - I0);
+  for (int e = threadIdx.x; e < np * s * ld; e += 256) ph[e] = phi[(size_t)I0 * s * ld + e];
+  for (int e = threadIdx.x; e < np * D; e += 256) qs[e] = q[(size_t)I0 * D + e];
+  __syncthreads();
+  for (int o = threadIdx.x; o < r * nb; o += 256) {
+    const int t = o / nb, k = o - (o / nb) * nb;
+    float acc = 0.f;
+    for (int p = 0; p < np; ++p)
+      for (int a = 0; a < s; ++a) acc = fmaf(ph[(p * s + a) * ld + t], qs[p * D + s * k + a], acc);
+    part[(size_t)blockIdx.x * (r * nb) + o] = (double)acc;
+  }
+}
+
+__global__ void k_project_reduce2(const double *__restrict__ part, int nblk, int n, double *__restrict__ pd,
+                                  float *__restrict__ pf) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * n + o];
+  if (pd) pd[o] = v;
+  if (pf) pf[o] = (float)v;
+}
+
+__global__ void k_project_reduce(const double *__restrict__ part, int nblk, int n, float *__restrict__ p) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  double v = 0.0;
+  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * n + o];
+  p[o] = (float)v;
+}
+
+// q[I D + s k + a] = sum_t Phi[(I s + a), t] p[t nb + k]
+__global__ void __launch_bounds__(256)
+    k_lift(const float *__restrict__ phi, int ld, int r, const float *__restrict__ p, int N, int D,
+           int s, int nb, float *__restrict__ q) {
+  __shared__ float ps[64 * 8];
+  for (int e = threadIdx.x; e < r * nb; e += 256) ps[e] = p[e];
+  __syncthreads();
+  const long row = (long)blockIdx.x * 256 + threadIdx.x;
+  if (row >= (long)N * s) return;
+  const long I = row / s;
+  const int a = (int)(row - I * s);
+  float acc[8];
+  for (int k = 0; k < nb; ++k) acc[k] = 0.f;
+  for (int t = 0; t < r; ++t) {
+    const float f = phi[row * ld + t];
+    for (int k = 0; k < nb; ++k) acc[k] = fmaf(f, ps[t * nb + k], acc[k]);
+  }
+  for (int k = 0; k < nb; ++k) q[I * D + s * k + a] = acc[k];
+}
+
+struct TmpBufs {
+  void *p[12] = {};
+  ~TmpBufs() {
+    for (void *x : p)
+      if (x) cudaFree(x);
+  }
+};
+
+int tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *part,
+           int nblk, long rchunk, double *G) {
+  k_tsgram<<<nblk, 256, 0, c->stream>>>(A, B, Ns, ld, rchunk, part);
+  VDS_CUDA_TRY(cudaGetLastError());
+  k_tsgram_reduce<<<(r * r + 255) / 256, 256, 0, c->stream>>>(part, nblk, r, G);
+  VDS_CUDA_TRY(cudaGetLastError());
+  c->launches += 2;
+  return VDS_OK;
+}
+
+}  // namespace
+
+int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *G) {
+  int nblk = 4 * c->num_sms;
+  long rchunk = (Ns + nblk - 1) / nblk;
+  rchunk = (rchunk + TR - 1) / TR * TR;
+  nblk = (int)((Ns + rchunk - 1) / rchunk);
+  VDS_TRY(vds_ensure(c, c->gbuf, (size_t)nblk * 4096 * sizeof(double)));
+  return tsgram(c, A, B, Ns, ld, r, (double *)c->gbuf.ptr, nblk, rchunk, G);
+}
+
+int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf) {
+  const int nb = D / b->s;
+  const int nblk = (N + PJ_PART - 1) / PJ_PART;
+  const int n = b->r * nb;
+  VDS_TRY(vds_ensure(c, c->gbuf, (size_t)nblk * n * sizeof(double)));
+  const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
+  k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->gbuf.ptr);
+  VDS_CUDA_TRY(cudaGetLastError());
+  k_project_reduce2<<<(n + 255) / 256, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, nblk, n, pd, pf);
+  VDS_CUDA_TRY(cudaGetLastError());
+  c->launches += 2;
+  return VDS_OK;
+}
+
+int pod_lift_dev(vds_ctx *c, const pod_basis *b, const float *p, int N, int D, float *q) {
+  const int nb = D / b->s;
+  k_lift<<<(unsigned)(((long)N * b->s + 255) / 256), 256, 0, c->stream>>>(b->phi, b->ld, b->r, p, N, D, b->s,
+                                                                         nb, q);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+extern "C" {
+
+int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, int r_max,
+              int r_fixed, const double *kappa, pod_basis **out, int *r_out) {
+  if (!c || !X || !out || Ns < 1 || M < 1 || M > 2048 || (s != 2 && s != 3) || Ns % s != 0)
+    return VDS_EARG;
+  if (r_max < 1 || r_max > 64 || r_fixed < 0 || r_fixed > 64 || !(energy > 0.0 && energy <= 1.0))
+    return VDS_EARG;
+  *out = nullptr;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  struct Restore {
+    int prev, dev;
+    ~Restore() {
+      if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+  } restore{prev, c->device};
+
+  TmpBufs tb;
+  const int nbt = (M + GT - 1) / GT;
+  // k split: about four CTAs per SM over the upper-triangle tiles
+  const int ntiles = nbt * (nbt + 1) / 2;
+  int nks = (4 * c->num_sms + ntiles - 1) / ntiles;
+  long kchunk = (Ns + nks - 1) / nks;
+  kchunk = (kchunk + GK - 1) / GK * GK;
+  nks = (int)((Ns + kchunk - 1) / kchunk);
+  const size_t MM = (size_t)M * M;
+  double *gpart, *A0, *A1, *V0, *V1, *W, *lam_s, *G, *Linv;
+  int *order;
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[0], (size_t)nks * nbt * nbt * GT * GT * sizeof(double)));
+  gpart = (double *)tb.p[0];
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[1], 4 * MM * sizeof(double)));
+  A0 = (double *)tb.p[1];
+  A1 = A0 + MM;
+  V0 = A1 + MM;
+  V1 = V0 + MM;
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[2], (size_t)M * 64 * sizeof(double) + (size_t)M * sizeof(double) +
+                                        2 * 64 * 64 * sizeof(double)));
+  W = (double *)tb.p[2];
+  lam_s = W + (size_t)M * 64;
+  G = lam_s + M;
+  Linv = G + 64 * 64;
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[3], (size_t)M * sizeof(int)));
+  order = (int *)tb.p[3];
+
+  // 1. Gram
+  k_gram_x<<<dim3(nbt * nbt, nks), 256, 0, c->stream>>>(X, Ns, M, nbt, kchunk, gpart);
+  VDS_CUDA_TRY(cudaGetLastError());
+  k_gram_reduce<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(gpart, M, nbt, nks, A0);
+  VDS_CUDA_TRY(cudaGetLastError());
+  k_identity<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(V0, M);
+  VDS_CUDA_TRY(cudaGetLastError());
+  c->launches += 3;
+
+  // 2. cyclic Jacobi, round-robin ordering
+  VDS_TRY(vds_ensure(c, c->red, 2 * 1024 * sizeof(double)));
+  const int Mpe = (M % 2 == 0) ? M : M + 1;  // odd M: one dummy index
+  const int H = Mpe / 2;
+  const long nthreads = (long)H * H + (long)M * H;
+  const unsigned nblk_round = (unsigned)((nthreads + 255) / 256);
+  int offblk = (int)((MM + 255) / 256);
+  if (offblk > 1024) offblk = 1024;
+  double prev_off = -1.0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int rnd = 0; rnd < Mpe - 1; ++rnd) {
+      k_jacobi_round<<<nblk_round, 256, 0, c->stream>>>(A0, A1, V0, V1, M, Mpe, rnd);
+      VDS_CUDA_TRY(cudaGetLastError());
+      ++c->launches;
+      double *t = A0;
+      A0 = A1;
+      A1 = t;
+      t = V0;
+      V0 = V1;
+      V1 = t;
+    }
+    k_offnorm<<<offblk, 256, 0, c->stream>>>(A0, M, (double *)c->red.ptr, c->ticket + TK_MISC, c->scal);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    VDS_TRY(vds_sync_status(c));
+    const double off = c->h_scal[SC_AUX], tot = c->h_scal[SC_AUX + 1];
+    if (off <= 1e-30 * tot || (prev_off >= 0.0 && off >= prev_off && off <= 1e-24 * tot)) break;
+    prev_off = off;
+  }
+
+  // 3. sort, rank rule, W = V_r Lambda_r^-1/2
+  k_eig_sort<<<1, 1024, 0, c->stream>>>(A0, V0, M, energy, r_max, r_fixed, lam_s, order, W, c->scal);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  VDS_TRY(vds_sync_status(c));
+  const int r_rule = (int)c->h_scal[SC_AUX + 2];
+  const int r = (int)c->h_scal[SC_AUX + 3];
+  if (r < 1 || r != r_rule) return VDS_EARG;  // rank exceeds the resolved spectrum
+  const int ld = (r + 3) / 4 * 4;
+
+  pod_basis *b = new pod_basis();
+  b->device = c->device;
+  b->Ns = Ns;
+  b->M = M;
+  b->r = r;
+  b->ld = ld;
+  b->s = s;
+  int st = VDS_OK;
+  do {
+    if (cudaMalloc(&b->phi, (size_t)Ns * ld * sizeof(float)) != cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    b->lam = (double *)malloc(sizeof(double) * M);
+    b->xh = (double *)malloc(sizeof(double) * r * r);
+    if (!b->lam || !b->xh) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    // 4. basis
+    k_basis<<<dim3((unsigned)((Ns + 255) / 256), (ld + BT - 1) / BT), 256, 0, c->stream>>>(X, Ns, M, W, r,
+                                                                                         ld, b->phi);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    ++c->launches;
+    // 5. Cholesky-QR
+    int nblk = 4 * c->num_sms;
+    long rchunk = (Ns + nblk - 1) / nblk;
+    rchunk = (rchunk + TR - 1) / TR * TR;
+    nblk = (int)((Ns + rchunk - 1) / rchunk);
+    if (cudaMalloc(&tb.p[4], (size_t)nblk * 4096 * sizeof(double)) != cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    double *tpart = (double *)tb.p[4];
+    if ((st = tsgram(c, b->phi, b->phi, Ns, ld, r, tpart, nblk, rchunk, G)) != VDS_OK) break;
+    k_chol_inv<<<1, 1, 0, c->stream>>>(G, r, Linv, c->err);
+    k_apply_linv<<<(unsigned)((Ns + 255) / 256), 256, 0, c->stream>>>(b->phi, Ns, ld, r, Linv);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    c->launches += 2;
+    // 6. sign fix
+    if (cudaMalloc(&tb.p[5], (size_t)nblk * 64 * (sizeof(float) + sizeof(long)) + 64 * sizeof(float)) !=
+        cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    float *bmax = (float *)tb.p[5];
+    long *brow = (long *)(bmax + (size_t)nblk * 64);
+    float *sgn = (float *)(brow + (size_t)nblk * 64);
+    k_colmax<<<nblk, 256, 0, c->stream>>>(b->phi, Ns, ld, r, rchunk, bmax, brow);
+    k_colsign<<<1, 64, 0, c->stream>>>(b->phi, ld, r, nblk, bmax, brow, sgn);
+    k_colscale<<<(unsigned)((Ns * ld + 255) / 256), 256, 0, c->stream>>>(b->phi, Ns, ld, r, sgn);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    c->launches += 3;
+    // 7. X^H = Phi^T (I (x) kappa) Phi
+    if (cudaMalloc(&tb.p[6], (size_t)Ns * ld * sizeof(float)) != cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    KappaArg ka;
+    for (int k = 0; k < 9; ++k) ka.k[k] = 0.0;
+    if (kappa)
+      for (int k = 0; k < s * s; ++k) ka.k[k] = kappa[k];
+    k_kappa_phi<<<(unsigned)((Ns * ld + 255) / 256), 256, 0, c->stream>>>(b->phi, Ns, ld, s, ka,
+                                                                         (float *)tb.p[6]);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    ++c->launches;
+    if ((st = tsgram(c, b->phi, (const float *)tb.p[6], Ns, ld, r, tpart, nblk, rchunk, G)) != VDS_OK) break;
+    if (cudaMemcpyAsync(b->xh, G, sizeof(double) * r * r, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(b->lam, lam_s, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    st = vds_sync_status(c);
+  } while (0);
+  if (st != VDS_OK) {
+    pod_free(b);
+    return st;
+  }
+  *out = b;
+  if (r_out) *r_out = r;
+  return VDS_OK;
+}
+
+int pod_info(const pod_basis *b, int *r, int *ld, const float **phi, long *Ns) {
+  if (!b) return VDS_EARG;
+  if (r) *r = b->r;
+  if (ld) *ld = b->ld;
+  if (phi) *phi = b->phi;
+  if (Ns) *Ns = b->Ns;
+  return VDS_OK;
+}
+
+int pod_eigenvalues(const pod_basis *b, double *lam, int M) {
+  if (!b || !lam || M < b->M) return VDS_EARG;
+  memcpy(lam, b->lam, sizeof(double) * b->M);
+  return VDS_OK;
+}
+
+int pod_xh(const pod_basis *b, double *xh) {
+  if (!b || !xh) return VDS_EARG;
+  memcpy(xh, b->xh, sizeof(double) * b->r * b->r);
+  return VDS_OK;
+}
+
+void pod_free(pod_basis *b) {
+  if (!b) return;
+  if (b->phi) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != b->device) cudaSetDevice(b->device);
+    cudaFree(b->phi);
+    if (prev >= 0 && prev != b->device) cudaSetDevice(prev);
+  }
+  free(b->lam);
+  free(b->xh);
+  delete b;
+}
+
+int pod_project(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, float *p) {
+  if (!c || !b || !q || !p || N < 1 || D % b->s != 0 || (long)N * b->s != b->Ns) return VDS_EARG;
+  const int nb = D / b->s;
+  if (nb < 1 || nb > 8) return VDS_EARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  const int nblk = (N + PJ_PART - 1) / PJ_PART;
+  const int n = b->r * nb;
+  int st = vds_ensure(c, c->red, (size_t)nblk * n * sizeof(double));
+  if (st == VDS_OK) {
+    const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
+    k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->red.ptr);
+    k_project_reduce<<<(n + 255) / 256, 256, 0, c->stream>>>((const double *)c->red.ptr, nblk, n, p);
+    c->launches += 2;
+    if (cudaGetLastError() != cudaSuccess) st = VDS_ECUDA;
+  }
+  if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+  return st;
+}
+
+int pod_lift(vds_ctx *c, const pod_basis *b, const float *p, int N, int D, float *q) {
+  if (!c || !b || !q || !p || N < 1 || D % b->s != 0 || (long)N * b->s != b->Ns) return VDS_EARG;
+  const int nb = D / b->s;
+  if (nb < 1 || nb > 8) return VDS_EARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  k_lift<<<(unsigned)(((long)N * b->s + 255) / 256), 256, 0, c->stream>>>(b->phi, b->ld, b->r, p, N, D, b->s,
+                                                                         nb, q);
+  ++c->launches;
+  const int st = cudaGetLastError() == cudaSuccess ? VDS_OK : VDS_ECUDA;
+  if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
+  return st;
+}
+
+}  // extern "C"

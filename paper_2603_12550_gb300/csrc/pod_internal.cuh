@@ -1,0 +1,21 @@
+// pod_internal.cuh -- the POD basis object and helpers shared by pod.cu and
+// reduced.cu (not part of the public ABI).
+#pragma once
+#include "../../include/vds_pod.h"
+#include "vds_internal.cuh"
+
+struct pod_basis {
+  int device = 0;
+  long Ns = 0;
+  int M = 0, r = 0, ld = 0, s = 0;
+  float *phi = nullptr;        // device, Ns x ld row-major (columns >= r zero)
+  double *lam = nullptr;       // host, M eigenvalues descending
+  double *xh = nullptr;        // host, r x r
+};
+
+// G (device, r x r FP64) = A^T B for row-major Ns x ld FP32 matrices.
+int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *G);
+// P = Phi^T q (r x nb) into pd (FP64, may be NULL) and/or pf (FP32, may be NULL).
+int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf);
+// q = Phi P from FP32 P (r x nb).
+int pod_lift_dev(vds_ctx *c, const pod_basis *b, const float *p, int N, int D, float *q);

@@ -1,0 +1,313 @@
+// reduced.cu -- the reduced-order (POD-MOR) steps of Sec. 2.3-2.4 on GB300.
+//
+// Mode 1, Galerkin (Eq. model_DymRepParPod): Pdot = Phi^T v(Phi P), the
+//   full-order particle velocity at the lifted state, projected; explicit
+//   Euler on P.  Costs a full density + gradient evaluation per step.
+// Mode 2, frozen linearised Brownian terms (Eq. model_DymReduced):
+//   Pdot = X^H P - (kBT/zeta)(X^B1 + X^B2) P A - (1/zeta) P diag(H) A,
+//   with X^B1, X^B2 rebuilt every `refresh_every` steps at the lifted state
+//   ("mapping back and forth", Sec. 2.4, Sec. 3.2) and frozen in between.
+//
+// The refresh is a pair pass over the lifted particles that accumulates, for
+// each particle I and basis column t (RT columns per CTA),
+//   W1_(Ia)t = sum_K Z_IK Phi_(Ka)t,  W2_(Ia)t = sum_K Z_IK Phi_(Ka)t / rho_K,
+//   c_I = sum_K Z_IK / rho_K,
+// and writes U1 = Phi - W1 / rho_I and U2 = c Phi - W2, so that
+//   X^B1 = -(1/h^2) Phi^T U1,  X^B2 = -(1/h^2) Phi^T U2
+// (the row sum of Z is rho_I).  Both contractions are FP64-accumulated
+// tall-skinny Grams.
+#include <math.h>
+
+#include "pair.cuh"
+#include "pod_internal.cuh"
+
+namespace {
+
+constexpr int RF_NT = 128;  // threads (particles) per CTA
+constexpr int RF_TJ = 64;   // j records per shared-memory tile
+constexpr int RT = 8;       // basis columns per CTA
+
+template <int D, int S>
+__global__ void __launch_bounds__(RF_NT)
+    k_refresh(const float *__restrict__ rec, int N, const float *__restrict__ phi, int ld, int r,
+              float *__restrict__ U1, float *__restrict__ U2) {
+  constexpr int DP = Rec<D>::DP;
+  __shared__ __align__(16) float srec[RF_TJ * DP];
+  __shared__ float sphi[RF_TJ][S][RT];
+  const int tid = threadIdx.x;
+  const int i = blockIdx.x * RF_NT + tid;
+  const int t0 = blockIdx.y * RT;
+  const bool vi = i < N;
+  const int ic = vi ? i : N - 1;
+  float xi[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) xi[d] = rec[(size_t)ic * DP + d];
+  const float wi = rec[(size_t)ic * DP + D];
+  float W1[S][RT], W2[S][RT], cs = 0.f;
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int t = 0; t < RT; ++t) W1[a][t] = W2[a][t] = 0.f;
+
+  for (int jt = 0; jt < N; jt += RF_TJ) {
+    __syncthreads();
+    for (int e = tid; e < RF_TJ * DP; e += RF_NT) srec[e] = rec[(size_t)jt * DP + e];
+    for (int e = tid; e < RF_TJ * S * RT; e += RF_NT) {
+      const int j = e / (S * RT), rem = e - j * (S * RT), a = rem / RT, t = rem - a * RT;
+      const int J = jt + j;
+      sphi[j][a][t] = (J < N && t0 + t < r) ? phi[((size_t)J * S + a) * ld + t0 + t] : 0.f;
+    }
+    __syncthreads();
+    float a1[S][RT], a2[S][RT], ac = 0.f;
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int t = 0; t < RT; ++t) a1[a][t] = a2[a][t] = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < RF_TJ; ++j) {
+      const float *rj = srec + j * DP;
+      float r2 = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float dd = xi[d] - rj[d];
+        r2 = fmaf(dd, dd, r2);
+      }
+      const float K = ex2_approx(-r2);
+      const float kw = K * rj[D];
+      ac += kw;
+#pragma unroll
+      for (int a = 0; a < S; ++a)
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+          const float f = sphi[j][a][t];
+          a1[a][t] = fmaf(K, f, a1[a][t]);
+          a2[a][t] = fmaf(kw, f, a2[a][t]);
+        }
+    }
+    cs += ac;
+#pragma unroll
+    for (int a = 0; a < S; ++a)
+#pragma unroll
+      for (int t = 0; t < RT; ++t) {
+        W1[a][t] += a1[a][t];
+        W2[a][t] += a2[a][t];
+      }
+  }
+  if (!vi) return;
+#pragma unroll
+  for (int a = 0; a < S; ++a)
+#pragma unroll
+    for (int t = 0; t < RT; ++t) {
+      if (t0 + t >= r) continue;
+      const size_t o = ((size_t)i * S + a) * ld + t0 + t;
+      const float f = phi[o];
+      U1[o] = f - W1[a][t] * wi;
+      U2[o] = cs * f - W2[a][t];
+    }
+}
+
+struct RedParams {
+  double kBT, zeta, dt;
+  double H[8];
+};
+
+__device__ __forceinline__ double rA(int j, int k) {
+  return j == k ? 2.0 : ((j - k == 1 || k - j == 1) ? -1.0 : 0.0);
+}
+
+// nsteps explicit Euler steps of Eq. model_DymReduced with frozen X^B, one
+// block; P kept in FP64 (shared memory), written back to Pd and Pf.
+__global__ void __launch_bounds__(512)
+    k_reduced_euler(double *__restrict__ Pd, float *__restrict__ Pf, const double *__restrict__ XH,
+                    const double *__restrict__ XB, int r, int nb, RedParams rp, int nsteps) {
+  __shared__ double P[64 * 8], Pdot[64 * 8], Y[64 * 8];
+  const int n = r * nb;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) P[o] = Pd[o];
+  __syncthreads();
+  for (int step = 0; step < nsteps; ++step) {
+    // Y = X^B P
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+      const int t = o / nb, j = o - t * nb;
+      double y = 0.0;
+      for (int u = 0; u < r; ++u) y += XB[t * r + u] * P[u * nb + j];
+      Y[o] = y;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < n; o += blockDim.x) {
+      const int t = o / nb, k = o - t * nb;
+      double a = 0.0, b = 0.0, cc = 0.0;
+      for (int u = 0; u < r; ++u) a += XH[t * r + u] * P[u * nb + k];
+      for (int j = 0; j < nb; ++j) {
+        const double A = rA(j, k);
+        b += Y[t * nb + j] * A;
+        cc += P[t * nb + j] * rp.H[j] * A;
+      }
+      Pdot[o] = a - (rp.kBT / rp.zeta) * b - cc / rp.zeta;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < n; o += blockDim.x) P[o] += rp.dt * Pdot[o];
+    __syncthreads();
+  }
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    Pd[o] = P[o];
+    Pf[o] = (float)P[o];
+  }
+}
+
+__global__ void k_f2d(const float *__restrict__ a, double *__restrict__ b, int n) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n) b[o] = (double)a[o];
+}
+
+__global__ void k_euler_p(double *__restrict__ Pd, float *__restrict__ Pf, const double *__restrict__ Pdot,
+                          double dt, int n) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n) {
+    const double v = Pd[o] + dt * Pdot[o];
+    Pd[o] = v;
+    Pf[o] = (float)v;
+  }
+}
+
+__global__ void k_combine_xb(const double *__restrict__ G1, const double *__restrict__ G2, double scale,
+                             double *__restrict__ XB, int n) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o < n) XB[o] = scale * (G1[o] + G2[o]);
+}
+
+template <int D, int S>
+int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
+  dim3 grid((N + RF_NT - 1) / RF_NT, (b->r + RT - 1) / RT);
+  VDS_TRY(vds_time_begin(c, PK_REFRESH));
+  k_refresh<D, S><<<grid, RF_NT, 0, c->stream>>>((const float *)c->rec.ptr, N, b->phi, b->ld, b->r, U1, U2);
+  VDS_CUDA_TRY(cudaGetLastError());
+  VDS_TRY(vds_time_end(c, PK_REFRESH));
+  ++c->launches;
+  return VDS_OK;
+}
+
+int refresh_dispatch(vds_ctx *c, const pod_basis *b, int N, int D, float *U1, float *U2) {
+  const int s = b->s;
+#define RF(DD, SS) \
+  if (D == DD && s == SS) return refresh_impl<DD, SS>(c, b, N, U1, U2);
+  RF(2, 2) RF(3, 3) RF(4, 2) RF(6, 2) RF(6, 3) RF(8, 2) RF(9, 3) RF(10, 2) RF(12, 2) RF(12, 3)
+  RF(14, 2) RF(15, 3) RF(16, 2)
+#undef RF
+  return VDS_EARG;
+}
+
+int check(const vds_params *p, const pod_basis *b, int N, int D) {
+  if (!p || !b || N < 1 || D < 2 || D > VDS_MAXD) return VDS_EARG;
+  if (p->s != b->s || p->nb * p->s != D || (long)N * b->s != b->Ns || p->nb > 8) return VDS_EARG;
+  if (!(p->h > 0.0) || !(p->zeta > 0.0) || !(p->kBT >= 0.0)) return VDS_EARG;
+  if (p->spring != 0 && p->spring != 1) return VDS_EARG;
+  if (p->spring == 1 && !(p->b > 0.0)) return VDS_EARG;
+  return VDS_OK;
+}
+
+struct Dev {
+  int prev = -1, dev;
+  explicit Dev(int d) : dev(d) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Dev() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+// Lift P, evaluate the density at the lifted state, run the refresh pass and
+// the two contractions: G1 = Phi^T U1, G2 = Phi^T U2 (device FP64 r x r).
+int brownian_dev(vds_ctx *c, const pod_basis *b, const float *P, int N, int D, const KParams &kp,
+                 float *qt, float *U1, float *U2, double *G1, double *G2) {
+  VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
+  VDS_TRY(pass_prep(c, kp, qt, nullptr, nullptr, 0.f, nullptr));
+  VDS_TRY(pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr));
+  VDS_TRY(refresh_dispatch(c, b, N, D, U1, U2));
+  VDS_TRY(pod_tsgram(c, b->phi, U1, b->Ns, b->ld, b->r, G1));
+  VDS_TRY(pod_tsgram(c, b->phi, U2, b->Ns, b->ld, b->r, G2));
+  return VDS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pod_brownian(vds_ctx *c, const pod_basis *b, const float *P, int N, int D, const vds_params *p,
+                 double *xb1, double *xb2) {
+  if (!c || !P) return VDS_EARG;
+  VDS_TRY(check(p, b, N, D));
+  Dev dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  const size_t nd = (size_t)N * D, nu = (size_t)b->Ns * b->ld;
+  const int r = b->r;
+  VDS_TRY(vds_ensure(c, c->vecs, nd * sizeof(float)));
+  VDS_TRY(vds_ensure(c, c->ubuf, 2 * nu * sizeof(float) + 2 * 4096 * sizeof(double)));
+  float *U1 = (float *)c->ubuf.ptr, *U2 = U1 + nu;
+  double *G1 = (double *)(U2 + nu), *G2 = G1 + 4096;
+  VDS_TRY(brownian_dev(c, b, P, N, D, kp, (float *)c->vecs.ptr, U1, U2, G1, G2));
+  const double scale = -1.0 / (p->h * p->h);
+  if (xb1) VDS_CUDA_TRY(cudaMemcpyAsync(xb1, G1, sizeof(double) * r * r, cudaMemcpyDeviceToHost, c->stream));
+  if (xb2) VDS_CUDA_TRY(cudaMemcpyAsync(xb2, G2, sizeof(double) * r * r, cudaMemcpyDeviceToHost, c->stream));
+  VDS_TRY(vds_sync_status(c));
+  for (int k = 0; k < r * r; ++k) {
+    if (xb1) xb1[k] *= scale;
+    if (xb2) xb2[k] *= scale;
+  }
+  return VDS_OK;
+}
+
+int pod_step(vds_ctx *c, const pod_basis *b, float *P, int N, int D, const vds_params *p, int nsteps,
+             int refresh_every, int mode) {
+  if (!c || !P || nsteps < 0 || (mode != 1 && mode != 2)) return VDS_EARG;
+  VDS_TRY(check(p, b, N, D));
+  if (!(p->dt > 0.0)) return VDS_EARG;
+  if (mode == 2 && (p->spring != 0 || refresh_every < 1)) return VDS_EARG;
+  if (nsteps == 0) return VDS_OK;
+  Dev dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  const int r = b->r, nb = p->nb, n = r * nb;
+  const size_t nd = (size_t)N * D, nu = (size_t)b->Ns * b->ld;
+  VDS_TRY(vds_ensure(c, c->vecs, 2 * nd * sizeof(float)));
+  float *qt = (float *)c->vecs.ptr, *vel = qt + nd;
+  // small FP64 state: Pd, Pdot, XH, XB, G1, G2
+  VDS_TRY(vds_ensure(c, c->ubuf, (mode == 2 ? 2 * nu * sizeof(float) : 0) + (2 * 512 + 4 * 4096) * sizeof(double)));
+  float *U1 = (float *)c->ubuf.ptr, *U2 = U1 + (mode == 2 ? nu : 0);
+  double *Pd = (double *)(U2 + (mode == 2 ? nu : 0));
+  double *Pdot = Pd + 512, *XH = Pdot + 512, *XB = XH + 4096, *G1 = XB + 4096, *G2 = G1 + 4096;
+  k_f2d<<<(n + 255) / 256, 256, 0, c->stream>>>(P, Pd, n);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  RedParams rp;
+  rp.kBT = p->kBT;
+  rp.zeta = p->zeta;
+  rp.dt = p->dt;
+  for (int j = 0; j < 8; ++j) rp.H[j] = p->H[j];
+  if (mode == 2) {
+    VDS_CUDA_TRY(cudaMemcpyAsync(XH, b->xh, sizeof(double) * r * r, cudaMemcpyHostToDevice, c->stream));
+    const double scale = -1.0 / (p->h * p->h);
+    for (int n0 = 0; n0 < nsteps;) {
+      VDS_TRY(brownian_dev(c, b, P, N, D, kp, qt, U1, U2, G1, G2));
+      k_combine_xb<<<(r * r + 255) / 256, 256, 0, c->stream>>>(G1, G2, scale, XB, r * r);
+      const int m = (nsteps - n0) < refresh_every ? (nsteps - n0) : refresh_every;
+      k_reduced_euler<<<1, 512, 0, c->stream>>>(Pd, P, XH, XB, r, nb, rp, m);
+      VDS_CUDA_TRY(cudaGetLastError());
+      c->launches += 2;
+      n0 += m;
+    }
+  } else {
+    for (int n0 = 0; n0 < nsteps; ++n0) {
+      VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
+      VDS_TRY(pass_prep(c, kp, qt, nullptr, nullptr, 0.f, nullptr));
+      VDS_TRY(pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr));
+      VDS_TRY(pass_grad(c, kp, GM_VEL, vel, qt, nullptr, nullptr, nullptr, nullptr));
+      VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
+      k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
+      VDS_CUDA_TRY(cudaGetLastError());
+      ++c->launches;
+    }
+  }
+  return vds_sync_status(c);
+}
+
+}  // extern "C"

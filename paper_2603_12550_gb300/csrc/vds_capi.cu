@@ -167,7 +167,7 @@ void vds_destroy(vds_ctx *c) {
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf *bufs[] = {&c->rec, &c->part, &c->red, &c->vecs, &c->gbuf};
+  DevBuf *bufs[] = {&c->rec, &c->part, &c->red, &c->vecs, &c->gbuf, &c->ubuf};
   for (DevBuf *b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c->err) cudaFree(c->err);

@@ -180,7 +180,8 @@ struct vds_ctx {
   DevBuf part;     // pair-pass partial sums (FP64)
   DevBuf red;      // block partials of reductions (FP64)
   DevBuf vecs;     // minimiser vectors / scratch (FP32)
-  DevBuf gbuf;     // gradient scratch (FP32 N x D)
+  DevBuf gbuf;     // Gram / projection partials (FP64)
+  DevBuf ubuf;     // reduced-order scratch (refresh outputs, reduced state)
   int *err = nullptr;          // device error flag
   unsigned *ticket = nullptr;  // last-block tickets (zeroed, self-resetting)
   double *scal = nullptr;      // device scalars

@@ -84,6 +84,8 @@ _SIGS = {
     "pod_project": ([_vp, _vp, _vp, _i, _i, _vp], _i),
     "pod_lift": ([_vp, _vp, _vp, _i, _i, _vp], _i),
     "pod_free": ([_vp], None),
+    "pod_brownian": ([_vp, _vp, _vp, _i, _i, _pp, _dp, _dp], _i),
+    "pod_step": ([_vp, _vp, _vp, _i, _i, _pp, _i, _i, _i], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     if hasattr(lib, _name):
@@ -197,6 +199,18 @@ class Context:
     def pod_lift(self, basis: "PodBasis", p_in, q_out):
         N, D = q_out.shape
         _check(lib.pod_lift(self.h, basis.h, _ptr(p_in), N, D, _ptr(q_out)))
+
+
+    def pod_brownian(self, basis: "PodBasis", P, N, D, p: VdsParams):
+        r = basis.info()["r"]
+        b1 = (ctypes.c_double * (r * r))()
+        b2 = (ctypes.c_double * (r * r))()
+        _check(lib.pod_brownian(self.h, basis.h, _ptr(P), int(N), int(D), ctypes.byref(p), b1, b2))
+        return np.array(b1[:]).reshape(r, r), np.array(b2[:]).reshape(r, r)
+
+    def pod_step(self, basis: "PodBasis", P, N, D, p: VdsParams, nsteps=1, refresh_every=1, mode=2):
+        _check(lib.pod_step(self.h, basis.h, _ptr(P), int(N), int(D), ctypes.byref(p), int(nsteps),
+                            int(refresh_every), int(mode)))
 
 
 class PodBasis:

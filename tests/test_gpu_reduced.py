@@ -1,0 +1,107 @@
+"""GPU parity of the reduced-order steps (Sec. 2.3-2.4): the frozen Brownian
+matrices X^B1, X^B2, mode 1 (Galerkin, Eq. model_DymRepParPod) and mode 2
+(Eq. model_DymReduced with periodic refresh) against the FP64 oracle.
+
+Both sides start from the same reduced state P0 (the oracle's projection of an
+oracle trajectory state) and use their own bases built from the same FP32
+snapshot matrix.  Tolerances: X^B within 1e-4 relative (Frobenius; FP32 pair
+sums with O(1) cancellation in Phi - W/rho), P within 1e-4 relative after the
+steps.
+"""
+import numpy as np
+import pytest
+
+from paper_2603_12550_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_12550_gb300 import build
+    build.build()
+    from paper_2603_12550_gb300 import vds as v
+    return v
+
+
+@pytest.fixture(scope="module")
+def ctx(vds):
+    c = vds.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def setup(orc, vds, ctx):
+    N, nb, s, r = 500, 3, 3, 10
+    kap = inputs.shear_kappa(s, 1.0)
+    q = inputs.equilibrium_cloud(N, nb, s, seed=21).astype(np.float64)
+    po = orc.params(nb, s, h=0.9, dt=0.005, kappa=kap)
+    states = [q]
+    for _ in range(9):
+        q = orc.explicit_steps(q, po, 5)
+        states.append(q)
+    X = orc.snapshots_from_states([x.astype(np.float32).astype(np.float64) for x in states], s, nb)
+    X32 = X.astype(np.float32)
+    o = orc.pod_build(X32.astype(np.float64), r_fixed=r)
+    basis, rg = ctx.pod_build(torch.from_numpy(np.ascontiguousarray(X32.T)).cuda(), N * s, X.shape[1], s,
+                              r_fixed=r, kappa=kap)
+    assert rg == r
+    P0 = orc.project(o["Phi"], states[0], s, nb)
+    pg = vds.params(nb, s, h=0.9, dt=0.005, kappa=kap)
+    return dict(N=N, nb=nb, s=s, r=r, kap=kap, po=po, pg=pg, Phi=o["Phi"], basis=basis, P0=P0)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_brownian_matrices_match_oracle(orc, vds, ctx, setup):
+    S = setup
+    P = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    B1, B2 = ctx.pod_brownian(S["basis"], P, S["N"], S["nb"] * S["s"], S["pg"])
+    q = orc.lift(S["Phi"], S["P0"].astype(np.float32).astype(np.float64), S["s"], S["nb"])
+    B1o, B2o, _ = orc.x_b(S["Phi"], q, 0.9, S["s"])
+    assert _rel(B1, B1o) <= 1e-4
+    assert _rel(B2, B2o) <= 1e-4
+
+
+def test_mode2_frozen_steps_match_oracle(orc, vds, ctx, setup):
+    S = setup
+    P = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    ctx.pod_step(S["basis"], P, S["N"], S["nb"] * S["s"], S["pg"], nsteps=12, refresh_every=5, mode=2)
+    P_o = orc.reduced_run(S["P0"].astype(np.float32).astype(np.float64), S["Phi"], S["po"], 12, 5)
+    assert _rel(P.cpu().numpy(), P_o) <= 1e-4
+
+
+def test_mode1_galerkin_steps_match_oracle(orc, vds, ctx, setup):
+    S = setup
+    P = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    ctx.pod_step(S["basis"], P, S["N"], S["nb"] * S["s"], S["pg"], nsteps=3, mode=1)
+    Po = S["P0"].astype(np.float32).astype(np.float64)
+    for _ in range(3):
+        Po = Po + S["po"].dt * orc.galerkin_rhs(Po, S["Phi"], S["po"])
+    assert _rel(P.cpu().numpy(), Po) <= 1e-4
+
+
+def test_mode2_with_refresh_every_step_is_galerkin(vds, ctx, setup):
+    # Sec. 2.4: the frozen terms are exact at a refresh instant, so refreshing
+    # every step reproduces the Galerkin trajectory (here: GPU against GPU).
+    S = setup
+    P1 = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    P2 = P1.clone()
+    D = S["nb"] * S["s"]
+    ctx.pod_step(S["basis"], P1, S["N"], D, S["pg"], nsteps=4, refresh_every=1, mode=2)
+    ctx.pod_step(S["basis"], P2, S["N"], D, S["pg"], nsteps=4, mode=1)
+    assert _rel(P1.cpu().numpy(), P2.cpu().numpy()) <= 1e-4
+
+
+def test_mode2_rejects_fene(vds, ctx, setup):
+    S = setup
+    P = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    pf = vds.params(S["nb"], S["s"], h=0.9, dt=0.005, spring=1, b=50.0)
+    with pytest.raises(vds.VdsError):
+        ctx.pod_step(S["basis"], P, S["N"], S["nb"] * S["s"], pf, nsteps=1, mode=2)
