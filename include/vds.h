@@ -47,7 +47,8 @@ enum {
   VDS_ENAN = -5,      /* non-finite density / energy */
   VDS_ETIMEOUT = -6,  /* a bounded device-side wait gave up */
   VDS_ENOMEM = -7,    /* device allocation failed */
-  VDS_ESURROGATE = -8 /* surrogate check failed */
+  VDS_ESURROGATE = -8, /* surrogate check failed */
+  VDS_ESIZE = -9       /* problem larger than a fixed-size buffer allows */
 };
 
 /* Physical and numerical parameters (Sec. 2.1-2.2, Sec. 3.1, Appendix A). */
@@ -121,6 +122,33 @@ VDS_API int vds_step(vds_ctx *ctx, float *q, int N, int D, const vds_params *p,
  * The Kramers form is tau - nb kBT Id. */
 VDS_API int vds_stress(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
                double *tau, double *qq);
+
+/* Allocation-free density and gradient evaluation.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate
+ * device memory at the point of the call: a flow solver that couples one VDS
+ * ensemble per grid point and reserves its whole device-memory budget up
+ * front, a host that forbids allocation after initialisation (real-time or
+ * plugin integrations), or code that must not take the allocator's locks and
+ * implicit synchronisation.  It computes what vds_energy_grad computes
+ * (q_star = NULL): E (host, may be NULL), g (device N x D, may be NULL) and
+ * rho (device N, may be NULL) for the device array q (N x D), on the given
+ * stream (a cudaStream_t of the current device; NULL = legacy default
+ * stream), and synchronises that stream before returning.
+ *  - No context and no allocation: all scratch lives in one fixed-size static
+ *    device array of the library (about 4.7 MiB, held by every GPU that loads
+ *    the library until the process exits); the caller passes inputs and
+ *    outputs only.
+ *  - N must not exceed VDS_NOALLOC_MAX_N; larger N returns VDS_ESIZE.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (the call's one-time set-up); make that first call
+ *    before any stream capture on the device.
+ *  - Every call shares the one array: calls that overlap on the GPU (from
+ *    several host threads, or on several streams) race and give wrong results.
+ *    Calls made one after another do not overlap, because each synchronises
+ *    its stream before returning. */
+#define VDS_NOALLOC_MAX_N 8192
+VDS_API int vds_energy_grad_noalloc(const float *q, int N, int D, const vds_params *p,
+                                    double *E, float *g, float *rho, void *cuda_stream);
 
 /* Instrumentation (no counterpart in the paper; used to report a kernel's
  * achieved rate).  vds_timing(ctx, 1) clears the counters and starts

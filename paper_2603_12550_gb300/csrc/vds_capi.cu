@@ -118,6 +118,7 @@ const char *vds_strerror(int st) {
     case VDS_ETIMEOUT: return "bounded device wait gave up";
     case VDS_ENOMEM: return "device allocation failed";
     case VDS_ESURROGATE: return "surrogate check failed";
+    case VDS_ESIZE: return "problem larger than the fixed-size scratch allows";
     default: return "unknown status";
   }
 }

@@ -15,7 +15,8 @@ import numpy as np
 from . import build as _build
 
 VDS_OK, VDS_EARG, VDS_ECUDA, VDS_EDOMAIN, VDS_ENOCONV = 0, -1, -2, -3, -4
-VDS_ENAN, VDS_ETIMEOUT, VDS_ENOMEM, VDS_ESURROGATE = -5, -6, -7, -8
+VDS_ENAN, VDS_ETIMEOUT, VDS_ENOMEM, VDS_ESURROGATE, VDS_ESIZE = -5, -6, -7, -8, -9
+VDS_NOALLOC_MAX_N = 8192
 
 
 class VdsError(RuntimeError):
@@ -76,6 +77,7 @@ _SIGS = {
     "vds_step": ([_vp, _vp, _i, _i, _pp, _i, _ip], _i),
     "vds_stress": ([_vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "vds_timing": ([_vp, _i], _i),
+    "vds_energy_grad_noalloc": ([_vp, _i, _i, _pp, _dp, _vp, _vp, _vp], _i),
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
     "pod_build": ([_vp, _vp, _l, _i, _i, _d, _i, _i, _dp, ctypes.POINTER(_vp), _ip], _i),
     "pod_info": ([_vp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_l)], _i),
@@ -120,6 +122,17 @@ def _stream_handle(stream):
         import torch
         stream = torch.cuda.current_stream()
     return getattr(stream, "cuda_stream", stream)
+
+
+def energy_grad_noalloc(q, p: VdsParams, g=None, rho=None, want_energy=True, stream=None):
+    """vds_energy_grad_noalloc: the allocation-free evaluation (no context);
+    returns E (or None)."""
+    N, D = q.shape
+    E = ctypes.c_double()
+    _check(lib.vds_energy_grad_noalloc(_ptr(q), N, D, ctypes.byref(p),
+                                       ctypes.byref(E) if want_energy else None, _ptr(g), _ptr(rho),
+                                       _stream_handle(stream)))
+    return E.value if want_energy else None
 
 
 class Context:
