@@ -83,6 +83,7 @@ int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double 
   constexpr int TI = NT_PAIR * RI;
   const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
   int occ = 0;
+  VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<D, RI, GRAD>, NT_PAIR, smem));
   if (occ < 1) occ = 1;
   sc.TI = TI;

@@ -596,6 +596,9 @@ int launch_pair(vds_ctx *c, int N, Sched &sc) {
   const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
   static int occ = -1;
   if (occ < 0) {
+    // large D needs more than the default 48 KB of dynamic shared memory
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
     int o = 0;
     VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, GRAD>, NT_PAIR, smem));
     occ = o > 0 ? o : 1;
