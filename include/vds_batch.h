@@ -1,0 +1,62 @@
+/*
+ * vds_batch.h -- C ABI of the batched form of the VDS hot path: many
+ * independent particle ensembles of uneven size (one per macroscopic grid
+ * point of a micro-macro solver, the coupling the paper motivates in Sec. 1
+ * and Sec. 2.1) advanced together.  Not in the paper's experiments; each
+ * ensemble follows exactly the single-ensemble definitions of vds.h.
+ *
+ * Layout: the ensembles' particles are concatenated, ensemble e occupying
+ * rows [off_e, off_e + N_e) of one device array q_all (sum N_e) x D, with
+ * off_e = N_0 + ... + N_{e-1}.  Every ensemble has its own bandwidth h_e and
+ * velocity gradient kappa_e; the other parameters (springs, kBT, zeta, dt,
+ * scheme, tolerances) are shared.  Same status codes as vds.h.
+ *
+ * Work distribution: one persistent kernel per pair pass pops work items
+ * (e, i-tile) from a queue in longest-processing-time order -- cost N_e
+ * descending, then e ascending, then tile ascending -- with an atomic
+ * counter; an item covers all j of its ensemble, so every particle's sums are
+ * formed by one CTA in a fixed order and the results do not depend on the
+ * schedule.
+ */
+#ifndef VDS_BATCH_H
+#define VDS_BATCH_H
+
+#include "vds.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vds_batch vds_batch;
+
+/* Set up a batch of E ensembles: sizes (host, E ints, each >= 1), h (host,
+ * E doubles > 0), kappa (host, E x s x s doubles, row-major per ensemble),
+ * shared parameters p (p->h and p->kappa are ignored).  D = p->nb * p->s.
+ * The batch owns its device workspace. */
+VDS_API int vds_batch_create(vds_ctx *ctx, int E, const int *sizes, int D, const vds_params *p,
+                             const double *h, const double *kappa, vds_batch **out);
+VDS_API void vds_batch_free(vds_batch *b);
+/* Total particle count and tile size (particles per work item). */
+VDS_API int vds_batch_info(const vds_batch *b, long *total, int *tile, int *n_items);
+/* Work items in queue order: items[2k] = ensemble, items[2k+1] = tile
+ * (host, 2 * n_items ints). */
+VDS_API int vds_batch_queue(const vds_batch *b, int *items, int n_items);
+
+/* Per-ensemble energies E_e (host, E doubles, may be NULL), gradients g_all
+ * (device, total x D, may be NULL) and densities rho_all (device, total, may
+ * be NULL) of vds_energy_grad for every ensemble. */
+VDS_API int vds_batch_energy_grad(vds_ctx *ctx, vds_batch *b, const float *q_all, double *E,
+                                  float *g_all, float *rho_all);
+/* Advance every ensemble by nsteps steps of p->scheme (as vds_step).
+ * Implicit steps run all ensembles' minimisers in lockstep rounds (one
+ * persistent pair pass per round, each ensemble in its own state: gradient
+ * and new direction, or line-search trial), one CUDA graph per round,
+ * replayed until every ensemble has converged.  iters_out (host,
+ * nsteps x E ints, may be NULL) receives gradient evaluations per ensemble
+ * and step; status of the first failing ensemble is returned. */
+VDS_API int vds_batch_step(vds_ctx *ctx, vds_batch *b, float *q_all, int nsteps, int *iters_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VDS_BATCH_H */

@@ -86,6 +86,12 @@ _SIGS = {
     "pod_project": ([_vp, _vp, _vp, _i, _i, _vp], _i),
     "pod_lift": ([_vp, _vp, _vp, _i, _i, _vp], _i),
     "pod_free": ([_vp], None),
+    "vds_batch_create": ([_vp, _i, _ip, _i, _pp, _dp, _dp, ctypes.POINTER(_vp)], _i),
+    "vds_batch_free": ([_vp], None),
+    "vds_batch_info": ([_vp, ctypes.POINTER(_l), _ip, _ip], _i),
+    "vds_batch_queue": ([_vp, _ip, _i], _i),
+    "vds_batch_energy_grad": ([_vp, _vp, _vp, _dp, _vp, _vp], _i),
+    "vds_batch_step": ([_vp, _vp, _vp, _i, _ip], _i),
     "pod_brownian": ([_vp, _vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "pod_step": ([_vp, _vp, _vp, _i, _i, _pp, _i, _i, _i], _i),
 }
@@ -224,6 +230,54 @@ class Context:
     def pod_step(self, basis: "PodBasis", P, N, D, p: VdsParams, nsteps=1, refresh_every=1, mode=2):
         _check(lib.pod_step(self.h, basis.h, _ptr(P), int(N), int(D), ctypes.byref(p), int(nsteps),
                             int(refresh_every), int(mode)))
+
+
+class Batch:
+    """Owns a vds_batch (include/vds_batch.h)."""
+
+    def __init__(self, ctx: "Context", sizes, D, p: VdsParams, h, kappa):
+        sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        self.E = len(sizes)
+        self.ctx = ctx
+        out = _vp()
+        _check(lib.vds_batch_create(ctx.h, self.E, sizes.ctypes.data_as(_ip), int(D), ctypes.byref(p),
+                                    h.ctypes.data_as(_dp), kappa.ctypes.data_as(_dp), ctypes.byref(out)))
+        self.h = out
+
+    def info(self):
+        tot, tile, n = ctypes.c_long(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.vds_batch_info(self.h, ctypes.byref(tot), ctypes.byref(tile), ctypes.byref(n)))
+        return dict(total=tot.value, tile=tile.value, n_items=n.value)
+
+    def queue(self):
+        n = self.info()["n_items"]
+        buf = (ctypes.c_int * (2 * n))()
+        _check(lib.vds_batch_queue(self.h, buf, n))
+        return np.array(buf[:], dtype=np.int32).reshape(n, 2)
+
+    def energy_grad(self, q_all, g=None, rho=None, want_energy=True):
+        E = (ctypes.c_double * self.E)()
+        _check(lib.vds_batch_energy_grad(self.ctx.h, self.h, _ptr(q_all), E if want_energy else None,
+                                         _ptr(g), _ptr(rho)))
+        return np.array(E[:]) if want_energy else None
+
+    def step(self, q_all, nsteps=1, want_iters=False):
+        it = (ctypes.c_int * max(1, nsteps * self.E))() if want_iters else None
+        _check(lib.vds_batch_step(self.ctx.h, self.h, _ptr(q_all), int(nsteps), it))
+        return np.array(it[:nsteps * self.E]).reshape(nsteps, self.E) if want_iters else None
+
+    def free(self):
+        if self.h:
+            lib.vds_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class PodBasis:

@@ -1,0 +1,135 @@
+"""GPU parity of the batched ensembles (include/vds_batch.h): the work queue
+is bit-identical to the oracle's longest-processing-time order; every
+ensemble's density, energy, gradient, explicit and implicit steps match the
+FP64 oracle run on that ensemble alone (same tolerances as the single path);
+and an ensemble's results are bit-identical whether it runs alone or inside
+a larger batch (the schedule does not change any sum)."""
+import numpy as np
+import pytest
+
+from paper_2603_12550_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def vds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_12550_gb300 import build
+    build.build()
+    from paper_2603_12550_gb300 import vds as v
+    return v
+
+
+@pytest.fixture(scope="module")
+def ctx(vds):
+    c = vds.Context(0)
+    yield c
+    c.close()
+
+
+SIZES = [37, 1, 129, 600, 2, 513, 300, 1030]
+NB, S = 2, 3
+D = NB * S
+
+
+def _ensembles(seed=0):
+    rng = np.random.default_rng(seed)
+    qs = [inputs.equilibrium_cloud(n, NB, S, seed=100 + e) for e, n in enumerate(SIZES)]
+    h = rng.uniform(0.5, 1.0, len(SIZES))
+    rates = 10.0 ** rng.uniform(-1, 1, len(SIZES))
+    kap = np.stack([inputs.shear_kappa(S, r) for r in rates])
+    return qs, h, kap
+
+
+def _batch(vds, ctx, sizes, h, kap, **kw):
+    p = vds.params(NB, S, **kw)
+    return vds.Batch(ctx, sizes, D, p, h, kap)
+
+
+def test_queue_is_lpt_order(orc, vds, ctx):
+    qs, h, kap = _ensembles()
+    b = _batch(vds, ctx, SIZES, h, kap)
+    tile = b.info()["tile"]
+    np.testing.assert_array_equal(b.queue(), orc.work_queue(SIZES, tile))
+
+
+def test_batched_energy_grad_matches_oracle(orc, vds, ctx):
+    qs, h, kap = _ensembles()
+    b = _batch(vds, ctx, SIZES, h, kap)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    g = torch.empty_like(q_all)
+    rho = torch.empty(q_all.shape[0], device="cuda")
+    E = b.energy_grad(q_all, g=g, rho=rho)
+    g, rho = g.cpu().numpy(), rho.cpu().numpy()
+    off = 0
+    for e, q in enumerate(qs):
+        n = q.shape[0]
+        po = orc.params(NB, S, h=h[e])
+        E_o, g_o, rho_o = orc.energy_grad(q.astype(np.float64), po)
+        assert np.max(np.abs(rho[off:off + n] - rho_o) / rho_o) <= 1e-5
+        assert abs(E[e] - E_o) <= 1e-5 * (1 + abs(E_o))
+        assert np.max(np.abs(g[off:off + n] - g_o)) <= 1e-5 * max(np.max(np.abs(g_o)), 1e-30)
+        off += n
+
+
+def test_ensemble_alone_is_bit_identical(vds, ctx):
+    qs, h, kap = _ensembles()
+    b = _batch(vds, ctx, SIZES, h, kap)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    g = torch.empty_like(q_all)
+    b.energy_grad(q_all, g=g)
+    off = np.concatenate([[0], np.cumsum(SIZES)])
+    for e in (3, 7):
+        b1 = _batch(vds, ctx, [SIZES[e]], h[e:e + 1], kap[e:e + 1])
+        q1 = torch.from_numpy(qs[e]).cuda()
+        g1 = torch.empty_like(q1)
+        b1.energy_grad(q1, g=g1)
+        assert torch.equal(g1, g[off[e]:off[e + 1]])
+
+
+def test_batched_explicit_steps_match_oracle(orc, vds, ctx):
+    qs, h, kap = _ensembles(1)
+    b = _batch(vds, ctx, SIZES, h, kap, dt=0.005, scheme=0)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    b.step(q_all, 4)
+    q_all = q_all.cpu().numpy()
+    off = 0
+    for e, q in enumerate(qs):
+        n = q.shape[0]
+        po = orc.params(NB, S, h=h[e], dt=0.005, kappa=kap[e])
+        q_o = orc.explicit_steps(q.astype(np.float64), po, 4)
+        assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o))
+        off += n
+
+
+def test_batched_implicit_steps_match_oracle(orc, vds, ctx):
+    qs, h, kap = _ensembles(2)
+    b = _batch(vds, ctx, SIZES, h, kap, dt=0.01, scheme=1, tol=1e-6, jfloor=1e-9, max_iter=50)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    its = b.step(q_all, 2, want_iters=True)
+    q_all = q_all.cpu().numpy()
+    off = 0
+    for e, q in enumerate(qs):
+        n = q.shape[0]
+        po = orc.params(NB, S, h=h[e], dt=0.01, kappa=kap[e], tol=1e-10)
+        q_o, it_o, _ = orc.implicit_steps(q.astype(np.float64), po, 2)
+        assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o))
+        assert np.all(its[:, e] >= 1)
+        off += n
+
+
+def test_batched_implicit_matches_single_ensemble_path(vds, ctx):
+    qs, h, kap = _ensembles(3)
+    b = _batch(vds, ctx, SIZES, h, kap, dt=0.01, scheme=1, tol=1e-6, jfloor=1e-9)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    b.step(q_all, 1)
+    off = np.concatenate([[0], np.cumsum(SIZES)])
+    for e in (0, 5, 7):
+        q1 = torch.from_numpy(qs[e]).cuda()
+        ctx.vds_step(q1, vds.params(NB, S, h=h[e], dt=0.01, kappa=kap[e], scheme=1, tol=1e-6, jfloor=1e-9), 1)
+        ref = q1.cpu().numpy()
+        got = q_all[off[e]:off[e + 1]].cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
