@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary measurements (implicit step, POD, batched)")
     return ap.parse_args()
 
 
@@ -188,6 +190,102 @@ def run_reference(a, wl, rank):
     print(json.dumps(line), flush=True)
 
 
+def _extras(ctx, vds, inputs, torch, wl, h, stream):
+    """Secondary rows on the same GPU: implicit steps of the 4-bead workload,
+    POD build and reduced-order steps, batched vs per-ensemble implicit steps."""
+    out = {}
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
+    D = nb * s
+    kap = inputs.shear_kappa(s, wl["rate"])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, r
+
+    # implicit steps (minimiser) on the 4-bead workload
+    q = torch.from_numpy(inputs.equilibrium_cloud(N, nb, s, H=wl["H"], seed=wl["seed"])).cuda()
+    pi = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"], kappa=kap,
+                    scheme=1, tol=1e-6, jfloor=1e-9)
+    ctx.vds_step(q, pi, 1)
+    sec, its = timed(lambda: ctx.vds_step(q, pi, 3, want_iters=True))
+    out["implicit_step"] = {"workload": "chain4_n65536_d9", "steps_per_s": 3 / sec,
+                            "gradient_evaluations_per_step": its, "tol": 1e-6}
+
+    # POD: 200 snapshots every 5 explicit steps, basis at 99.99 % energy (r <= 64),
+    # then the reduced steps (mode 2 refresh every 60 steps = 0.3 time units)
+    pe = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"], kappa=kap)
+    q = torch.from_numpy(inputs.equilibrium_cloud(N, nb, s, H=wl["H"], seed=wl["seed"])).cuda()
+    S = 200
+    X = torch.empty((S * nb, N * s), dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    for l in range(S):
+        qv = q.view(N, nb, s)
+        for k in range(nb):
+            X[l * nb + k].copy_(qv[:, k, :].reshape(-1))
+        ctx.vds_step(q, pe, 5)
+    torch.cuda.synchronize()
+    snap_s = time.perf_counter() - t0
+    sec, (basis, r) = timed(lambda: ctx.pod_build(X, N * s, S * nb, s, energy=0.9999, r_max=64, kappa=kap))
+    P = torch.empty((r, nb), device="cuda")
+    ctx.pod_project(basis, q, P)
+    ctx.pod_step(basis, P, N, D, pe, nsteps=60, refresh_every=60, mode=2)
+    sec2, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=240, refresh_every=60, mode=2))
+    sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
+    out["pod"] = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
+                  "eigenvalues_top": basis.eigenvalues()[:8].tolist(),
+                  "mode2_steps_per_s": 240 / sec2, "mode2_refresh_every": 60,
+                  "mode1_galerkin_steps_per_s": 3 / sec3, "snapshot_run_s": snap_s}
+    del X
+    basis.free()
+
+    # batched: 512 ensembles, 3-bead chains (D = 6), N_e = round(2^U(10,14)),
+    # shear rates 10^U(-1,1), dt = 0.005, implicit steps
+    bnb, bs = 2, 3
+    sizes, rates = inputs.ensemble_sizes(512, seed=0)
+    qs = [inputs.equilibrium_cloud(int(n), bnb, bs, seed=1000 + e) for e, n in enumerate(sizes)]
+    q_all0 = torch.from_numpy(np.concatenate(qs)).cuda()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    hs = np.array([ctx.vds_bandwidth(q_all0[off[e]:off[e + 1]], 0) for e in range(len(sizes))])
+    kaps = np.stack([inputs.shear_kappa(bs, r_) for r_ in rates])
+    pb = vds.params(bnb, bs, kBT=1.0, zeta=4.0, dt=0.005, scheme=1, tol=1e-6, jfloor=1e-9)
+    batch = vds.Batch(ctx, sizes, bnb * bs, pb, hs, kaps)
+    q_all = q_all0.clone()
+    batch.step(q_all, 1)
+    q_all = q_all0.clone()
+    sec_b, its_b = timed(lambda: batch.step(q_all, 2, want_iters=True))
+    # per-ensemble path: vds_step on each ensemble in turn, same parameters
+    q_pe = q_all0.clone()
+    views = [q_pe[off[e]:off[e + 1]] for e in range(len(sizes))]
+    ps = [vds.params(bnb, bs, kBT=1.0, zeta=4.0, h=hs[e], dt=0.005, kappa=kaps[e], scheme=1, tol=1e-6,
+                     jfloor=1e-9) for e in range(len(sizes))]
+    for e in range(8):
+        ctx.vds_step(views[e].clone(), ps[e], 1)
+
+    def per_ensemble():
+        for e in range(len(sizes)):
+            ctx.vds_step(views[e], ps[e], 1)
+    sec_p, _ = timed(lambda: [per_ensemble() for _ in range(2)])
+    # equal stress: both paths advanced the same ensembles by two steps
+    dev = 0.0
+    for e in range(0, len(sizes), 16):
+        pe_ = vds.params(bnb, bs, h=hs[e])
+        t1, _ = ctx.vds_stress(q_all[off[e]:off[e + 1]], pe_)
+        t2, _ = ctx.vds_stress(views[e], pe_)
+        dev = max(dev, float(np.linalg.norm(t1 - t2) / np.linalg.norm(t2)))
+    out["batched"] = {"ensembles": len(sizes), "d": bnb * bs, "total_particles": int(sizes.sum()),
+                      "pairs_per_pass": float((sizes.astype(np.float64) ** 2).sum()),
+                      "batched_steps_per_s": 2 / sec_b, "per_ensemble_steps_per_s": 2 / sec_p,
+                      "speedup": sec_p / sec_b,
+                      "mean_gradient_evaluations": float(np.mean(its_b)),
+                      "stress_rel_diff_batched_vs_per_ensemble": dev,
+                      "note": "one step advances all 512 ensembles by dt (implicit, tol 1e-6)"}
+    batch.free()
+    return out
+
+
 def main():
     a = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -308,6 +406,10 @@ def main():
                              "achieved": ops_dens / t_dens / 1e12,
                              "frac": ops_dens / t_dens / 1e12 / peak_tops}}
 
+    extras = None
+    if not a.no_extras:
+        extras = _extras(ctx, vds, inputs, torch, wl, h, stream)
+
     cpu = None
     if not a.no_cpu_baseline:
         rate, n, secs, cores = _oracle_rate(wl)
@@ -322,7 +424,7 @@ def main():
             "config": _config(wl, h),
             "pair_interactions_per_s": value * N * N,
             "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
-            "cpu_baseline": cpu}
+            "cpu_baseline": cpu, "extras": extras}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

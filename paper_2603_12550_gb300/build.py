@@ -77,6 +77,12 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, out)
+    for old in glob.glob(os.path.join(BUILD, "libvds_gb300_*.so")):
+        if old != out:
+            try:
+                os.remove(old)
+            except OSError:
+                pass
     for o in objs:
         try:
             os.remove(o)
