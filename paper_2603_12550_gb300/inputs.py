@@ -97,3 +97,24 @@ WORKLOADS = {
                              zeta=4.0, h=None, dt=0.005, rate=1.0, spring=0,
                              b=50.0, scheme=0, steps=1000, seed=0),
 }
+
+
+def mlp_init(widths=(9, 256, 256, 256, 9), seed: int = 0, scale: float = 1.0):
+    """Seeded initial parameters of an MLP with the given layer widths:
+    W_l (out x in) ~ N(0, scale^2 / in), b_l = 0.  Returns a list of (W, b)
+    in FP32 (the draws; no arithmetic of the method)."""
+    rng = np.random.default_rng(seed)
+    layers = []
+    for fan_in, fan_out in zip(widths[:-1], widths[1:]):
+        W = rng.standard_normal((fan_out, fan_in)) * (scale / math.sqrt(fan_in))
+        layers.append((W.astype(np.float32), np.zeros(fan_out, dtype=np.float32)))
+    return layers
+
+
+def dsm_batch(X: np.ndarray, batch: int, seed: int):
+    """A training batch for denoising score matching: `batch` rows drawn with
+    replacement from X (n x D) and standard normal noise of the same shape."""
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, X.shape[0], batch)
+    eps = rng.standard_normal((batch, X.shape[1])).astype(np.float32)
+    return X[idx].astype(np.float32), eps

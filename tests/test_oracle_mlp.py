@@ -1,0 +1,94 @@
+"""Pins of the FP64 oracle of the score surrogate (oracle/mlp.py) against
+things other than itself: central finite differences, a zero-weight closed
+form, the Gaussian minimiser of the denoising score-matching loss, the Adam
+closed form of the first step, and training to the Gaussian score."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_2603_12550_gb300 import inputs
+
+
+def test_silu_and_derivative():
+    z = np.linspace(-6, 6, 101)
+    np.testing.assert_allclose(mlp.silu(z), z * (1 / (1 + np.exp(-z))), rtol=1e-15)
+    fd = (mlp.silu(z + 1e-6) - mlp.silu(z - 1e-6)) / 2e-6
+    np.testing.assert_allclose(mlp.silu_grad(z), fd, rtol=1e-7, atol=1e-9)
+
+
+def test_backprop_matches_finite_differences():
+    layers = mlp.as64(inputs.mlp_init((9, 16, 16, 16, 9), seed=3))
+    rng = np.random.default_rng(1)
+    layers = [(W, rng.standard_normal(b.shape) * 0.1) for W, b in layers]
+    x = rng.standard_normal((32, 9))
+    eps = rng.standard_normal((32, 9))
+    sigma = 0.7
+    _, grads = mlp.dsm_grad(layers, x, eps, sigma)
+    for l in range(4):
+        for which in (0, 1):
+            P = layers[l][which]
+            for _ in range(3):
+                idx = tuple(rng.integers(0, n) for n in P.shape)
+                up = [(W.copy(), b.copy()) for W, b in layers]
+                dn = [(W.copy(), b.copy()) for W, b in layers]
+                up[l][which][idx] += 1e-6
+                dn[l][which][idx] -= 1e-6
+                fd = (mlp.dsm_loss(up, x, eps, sigma) - mlp.dsm_loss(dn, x, eps, sigma)) / 2e-6
+                g = grads[l][which][idx]
+                assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (l, which, idx, fd, g)
+
+
+def test_zero_weights_closed_form():
+    # all weights and hidden biases zero: s = b4 for every input,
+    # L = mean |b4 + eps/sigma|^2, dL/db4 = 2 mean(b4 + eps/sigma), all else 0.
+    layers = [(np.zeros((8, 9)), np.zeros(8)), (np.zeros((8, 8)), np.zeros(8)),
+              (np.zeros((9, 8)), np.array([0.3, -0.2, 0.1, 0, 0.5, 0, 0, -1, 2.0]))]
+    rng = np.random.default_rng(2)
+    x, eps, sigma = rng.standard_normal((50, 9)), rng.standard_normal((50, 9)), 0.5
+    loss, grads = mlp.dsm_grad(layers, x, eps, sigma)
+    b4 = layers[-1][1]
+    assert loss == pytest.approx(np.mean(np.sum((b4 + eps / sigma) ** 2, axis=1)), rel=1e-14)
+    np.testing.assert_allclose(grads[-1][1], 2 * np.mean(b4 + eps / sigma, axis=0), rtol=1e-13)
+    for l in range(2):
+        assert np.all(grads[l][0] == 0) and np.all(grads[l][1] == 0)
+    assert np.all(grads[-1][0] == 0)
+
+
+def test_dsm_loss_is_minimised_by_smoothed_gaussian_score():
+    # data N(0, s0^2 I): the DSM minimiser among s = a x is a = -1/(s0^2 + sigma^2)
+    rng = np.random.default_rng(4)
+    s0, sigma = 1.3, 0.6
+    x = rng.standard_normal((200000, 9)) * s0
+    eps = rng.standard_normal(x.shape)
+    a_star = -1 / (s0 ** 2 + sigma ** 2)
+    la = [mlp.dsm_loss_of_score(lambda z, a=a: a * z, x, eps, sigma)
+          for a in (a_star * 0.9, a_star, a_star * 1.1)]
+    assert la[1] < la[0] and la[1] < la[2]
+
+
+def test_adam_first_step_closed_form():
+    layers = [(np.array([[1.0, -2.0]]), np.array([0.5]))]
+    grads = [(np.array([[0.3, -0.04]]), np.array([2.0]))]
+    m, v = mlp.adam_init(layers)
+    out, _, _ = mlp.adam_step(layers, grads, m, v, 1, lr=0.1, eps=1e-8)
+    # first step: m_hat = g, v_hat = g^2 -> p - lr g / (|g| + eps)
+    np.testing.assert_allclose(out[0][0], layers[0][0] - 0.1 * grads[0][0] / (np.abs(grads[0][0]) + 1e-8))
+    np.testing.assert_allclose(out[0][1], layers[0][1] - 0.1 * grads[0][1] / (np.abs(grads[0][1]) + 1e-8))
+
+
+def test_training_reaches_gaussian_score():
+    # a small network trained by the oracle's DSM + Adam learns
+    # s(x) = -x / (s0^2 + sigma^2) on Gaussian data
+    s0, sigma = 1.0, 0.5
+    rng = np.random.default_rng(5)
+    data = (rng.standard_normal((20000, 3)) * s0).astype(np.float32)
+    layers = mlp.as64(inputs.mlp_init((3, 32, 32, 3), seed=0))
+    m, v = mlp.adam_init(layers)
+    for t in range(1, 1201):
+        x, eps = inputs.dsm_batch(data, 256, seed=t)
+        _, g = mlp.dsm_grad(layers, x, eps, sigma)
+        layers, m, v = mlp.adam_step(layers, g, m, v, t, lr=3e-3)
+    z = rng.standard_normal((500, 3)) * 0.8
+    s, _ = mlp.forward(layers, z)
+    target = -z / (s0 ** 2 + sigma ** 2)
+    assert np.linalg.norm(s - target) / np.linalg.norm(target) < 0.15
