@@ -1,0 +1,713 @@
+// mlp.cu -- learned score surrogate s_theta ~ grad ln f (include/vds_score.h):
+// an MLP D -> W -> W -> W -> D with SiLU hidden layers, BF16 weights and
+// activations, FP32 accumulation, trained by denoising score matching with
+// Adam; forward and backward GEMMs on the 5th-generation tensor cores.
+//
+// GEMM (k_gemm_tn): C[M x N] = A[M x K] . B[N x K]^T, A and B row-major BF16
+// (K contiguous).  One CTA per 128-row tile (and per K split), 4 warps.  K is
+// consumed in chunks of 64: all threads copy the A (128 x 64) and B (N x 64)
+// chunks into shared memory in the canonical K-major layout without swizzle
+// (8-row x 16-byte core matrices; 128 B between core matrices along K, 1024 B
+// between 8-row groups), one thread issues four tcgen05.mma (M=128, N, K=16,
+// kind::f16 with BF16 inputs) accumulating in tensor memory and commits them
+// to an mbarrier; two chunk buffers alternate.  The epilogue reads the
+// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows) and
+// applies the layer's bias/activation, writing row-major and, where the
+// backward pass needs it, transposed copies.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/vds_score.h"
+#include "vds_internal.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int GM = 128;   // rows per CTA tile
+constexpr int KC = 64;    // K per chunk
+constexpr int TMEM_COLS = 256;
+
+// ------------------------------------------------------------ tcgen05 glue
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  // K-major, no swizzle: LBO = 128 B (next core matrix along K),
+  // SBO = 1024 B (next 8-row group), descriptor version 1
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  // D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 = 1, 10-12 = 1), K-major
+  // A and B, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float s = 1.f / (1.f + expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+enum { EPI_F32 = 0, EPI_SILU = 1, EPI_DSILU = 2 };
+
+struct Epi {
+  int mode;
+  int rows;          // valid rows of C
+  int ncols;         // valid columns written
+  int ldc;           // row stride of outf / h / zf
+  long long split_stride;  // element offset of a K split's output (EPI_F32)
+  const float *bias;       // per column (may be null)
+  float *outf;             // EPI_F32 output, or FP32 copy (z for SILU, dz for DSILU)
+  bf16 *h;                 // BF16 row-major output
+  bf16 *ht;                // BF16 transposed output (may be null)
+  int ldt;                 // row stride of ht
+  const float *zin;        // pre-activation for DSILU (stride ldc)
+};
+
+// K-major canonical layout store of a rows x 64 chunk
+__device__ __forceinline__ void load_chunk(uint8_t *dst, const bf16 *__restrict__ src, int ld, int row0,
+                                           int nvalid, int rows_tile, int k0) {
+  for (int idx = threadIdx.x; idx < rows_tile * 8; idx += blockDim.x) {
+    const int r = idx >> 3, c = idx & 7;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r < nvalid) v = *reinterpret_cast<const uint4 *>(src + (size_t)(row0 + r) * ld + k0 + c * 8);
+    *reinterpret_cast<uint4 *>(dst + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+  }
+}
+
+__global__ void __launch_bounds__(128)
+    k_gemm_tn(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int N, int Ksplit,
+              Epi ep, int *err) {
+  extern __shared__ __align__(1024) uint8_t gsm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * GM;
+  const int kbase = blockIdx.y * Ksplit;
+  // shared memory: [A chunk 0: 16 KB][B chunk 0: 32 KB][A chunk 1][B chunk 1]
+  uint8_t *abuf[2] = {gsm, gsm + 16384 + 32768};
+  uint8_t *bbuf[2] = {gsm + 16384, gsm + 2 * 16384 + 32768};
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t idesc = idesc_bf16(GM, N);
+  const int nch = Ksplit / KC;
+  const int avalid = min(GM, ep.rows - m0);
+  bool ok = true;
+  for (int ch = 0; ch < nch && ok; ++ch) {
+    const int b = ch & 1;
+    if (ch >= 2) {
+      const bool got = mbar_wait_bounded(&bars[b], (uint32_t)(((ch - 2) >> 1) & 1), VDS_WAIT_LIMIT_NS);
+      if (__syncthreads_or(!got)) {
+        ok = false;
+        break;
+      }
+    }
+    load_chunk(abuf[b], A, lda, m0, avalid, GM, kbase + ch * KC);
+    load_chunk(bbuf[b], B, ldb, 0, N, N, kbase + ch * KC);
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(abuf[b]), b0 = smem_u32(bbuf[b]);
+#pragma unroll
+      for (int s = 0; s < KC / 16; ++s)
+        tc_mma(tmem, sdesc(a0 + s * 256), sdesc(b0 + s * 256), idesc, (ch > 0 || s > 0) ? 1 : 0);
+      tc_commit(&bars[b]);
+    }
+  }
+  if (ok && nch > 0) {
+    const int last = nch - 1;
+    const bool got = mbar_wait_bounded(&bars[last & 1], (uint32_t)((last >> 1) & 1), VDS_WAIT_LIMIT_NS);
+    if (__syncthreads_or(!got)) ok = false;
+  }
+  tc_fence_after();
+  if (!ok) {
+    if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
+  } else {
+    const int row = m0 + warp * 32 + lane;
+    const bool vrow = row < ep.rows;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (!vrow) continue;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int col = c0 + j;
+        if (col >= ep.ncols) continue;
+        float a = __uint_as_float(v[j]);
+        if (ep.mode == EPI_F32) {
+          if (ep.bias) a += ep.bias[col];
+          ep.outf[(long long)blockIdx.y * ep.split_stride + (size_t)row * ep.ldc + col] = a;
+        } else if (ep.mode == EPI_SILU) {
+          const float z = a + (ep.bias ? ep.bias[col] : 0.f);
+          if (ep.outf) ep.outf[(size_t)row * ep.ldc + col] = z;
+          const bf16 hv = __float2bfloat16_rn(silu_f(z));
+          ep.h[(size_t)row * ep.ldc + col] = hv;
+          if (ep.ht) ep.ht[(size_t)col * ep.ldt + row] = hv;
+        } else {
+          const float dz = a * dsilu_f(ep.zin[(size_t)row * ep.ldc + col]);
+          if (ep.outf) ep.outf[(size_t)row * ep.ldc + col] = dz;
+          const bf16 hv = __float2bfloat16_rn(dz);
+          ep.h[(size_t)row * ep.ldc + col] = hv;
+          if (ep.ht) ep.ht[(size_t)col * ep.ldt + row] = hv;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+constexpr size_t GEMM_SMEM = 2 * (16384 + 32768);
+
+// ------------------------------------------------------------ small kernels
+
+// A0 = bf16(x + sigma eps) padded to Dp columns (and its transpose)
+__global__ void k_input(const float *__restrict__ x, const float *__restrict__ eps, float sigma, int M, int D,
+                        int Dp, bf16 *__restrict__ a0, bf16 *__restrict__ a0t, int ldt) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)M * Dp) return;
+  const int m = (int)(idx / Dp), k = (int)(idx - (long)m * Dp);
+  float v = 0.f;
+  if (k < D) {
+    v = x[(size_t)m * D + k];
+    if (eps) v += sigma * eps[(size_t)m * D + k];
+  }
+  const bf16 b = __float2bfloat16_rn(v);
+  a0[idx] = b;
+  if (a0t) a0t[(size_t)k * ldt + m] = b;
+}
+
+// dS = (2/M)(s + eps/sigma) (first D columns), padded BF16 copies; loss terms
+__global__ void k_dsm_out(const float *__restrict__ S, int ldS, const float *__restrict__ eps, float sigma, int M,
+                          int D, float *__restrict__ dSf, int Op, bf16 *__restrict__ dSb, int ldb,
+                          bf16 *__restrict__ dSt, int ldt, double *__restrict__ lossp) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (m < M) {
+    for (int k = 0; k < ldb; ++k) {
+      float g = 0.f;
+      if (k < D) {
+        const float r = S[(size_t)m * ldS + k] + eps[(size_t)m * D + k] / sigma;
+        l += (double)r * r;
+        g = 2.f * r / (float)M;
+      }
+      if (k < Op) {
+        dSf[(size_t)m * Op + k] = g;
+        dSt[(size_t)k * ldt + m] = __float2bfloat16_rn(g);
+      }
+      dSb[(size_t)m * ldb + k] = __float2bfloat16_rn(g);
+    }
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = l;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lossp[blockIdx.x] = sh[0];
+}
+
+// column sums of an M x n FP32 matrix in a fixed order -> out[n]
+__global__ void k_colsum(const float *__restrict__ X, int M, int n, int ld, float *__restrict__ out) {
+  const int col = blockIdx.x;
+  double a = 0.0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) a += X[(size_t)m * ld + col];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && col < n) out[col] = (float)sh[0];
+}
+
+// out[i] = sum over splits of part[s * stride + i]
+__global__ void k_split_reduce(const float *__restrict__ part, int splits, long long stride, long long n,
+                               float *__restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a = 0.f;
+  for (int s = 0; s < splits; ++s) a += part[s * stride + i];
+  out[i] = a;
+}
+
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, long long n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copy of a rows x cols FP32 matrix and (optionally) its transpose
+// padded to tcols columns (zeros beyond rows).
+__global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 *__restrict__ Wb,
+                          bf16 *__restrict__ Wt, int tcols) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < (long)rows * cols) {
+    const int r = (int)(idx / cols), c = (int)(idx - (long)r * cols);
+    const bf16 b = __float2bfloat16_rn(W[idx]);
+    Wb[idx] = b;
+    if (Wt) Wt[(size_t)c * tcols + r] = b;
+  }
+  if (Wt && idx < (long)cols * tcols) {
+    const int c = (int)(idx / tcols), r = (int)(idx - (long)c * tcols);
+    if (r >= rows) Wt[idx] = __float2bfloat16_rn(0.f);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+
+struct vds_score {
+  int device = 0, D = 0, W = 0, Dp = 64, Op = 16;
+  long long off[8] = {};  // W1 b1 W2 b2 W3 b3 W4 b4 in the flat padded parameter vector
+  long long np = 0;
+  float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+  bf16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w4b = nullptr;
+  bf16 *w2t = nullptr, *w3t = nullptr, *w4t = nullptr;  // transposes (w4t: W x 64, K padded)
+  int t = 0;
+  int mcap = 0;
+  // activations for up to mcap rows
+  bf16 *a0 = nullptr, *a0t = nullptr, *h[3] = {}, *ht[3] = {}, *dzb[2] = {}, *dzt[2] = {}, *dsb = nullptr,
+       *dst = nullptr;
+  float *z[3] = {}, *dzf[2] = {}, *sf = nullptr, *dsf = nullptr, *part = nullptr;
+  double *lossp = nullptr, *h_loss = nullptr;
+};
+
+namespace {
+
+struct Dev {
+  int prev = -1, dev;
+  explicit Dev(int d) : dev(d) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Dev() {
+    if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  }
+};
+
+int gemm(vds_ctx *c, const bf16 *A, int lda, const bf16 *B, int ldb, int rows, int N, int K, int splits,
+         const Epi &ep) {
+  static bool attr = false;
+  if (!attr) {
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM));
+    attr = true;
+  }
+  if (N % 16 != 0 || N < 16 || N > 256 || K % (KC * splits) != 0) return VDS_EARG;
+  dim3 grid((rows + GM - 1) / GM, splits);
+  k_gemm_tn<<<grid, 128, GEMM_SMEM, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+Epi epi_f32(int rows, int ncols, int ldc, const float *bias, float *out, long long split_stride = 0) {
+  Epi e;
+  memset(&e, 0, sizeof(e));
+  e.mode = EPI_F32;
+  e.rows = rows;
+  e.ncols = ncols;
+  e.ldc = ldc;
+  e.bias = bias;
+  e.outf = out;
+  e.split_stride = split_stride;
+  return e;
+}
+
+Epi epi_act(int mode, int rows, int ncols, int ldc, const float *bias, float *outf, bf16 *h, bf16 *ht, int ldt,
+            const float *zin) {
+  Epi e;
+  memset(&e, 0, sizeof(e));
+  e.mode = mode;
+  e.rows = rows;
+  e.ncols = ncols;
+  e.ldc = ldc;
+  e.bias = bias;
+  e.outf = outf;
+  e.h = h;
+  e.ht = ht;
+  e.ldt = ldt;
+  e.zin = zin;
+  return e;
+}
+
+void free_acts(vds_score *s) {
+  void *ptrs[] = {s->a0, s->a0t, s->h[0], s->h[1], s->h[2], s->ht[0], s->ht[1], s->ht[2], s->dzb[0], s->dzb[1],
+                  s->dzt[0], s->dzt[1], s->dsb, s->dst, s->z[0], s->z[1], s->z[2], s->dzf[0], s->dzf[1], s->sf,
+                  s->dsf, s->part, s->lossp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  s->a0 = s->a0t = s->dsb = s->dst = nullptr;
+  for (int k = 0; k < 3; ++k) s->h[k] = s->ht[k] = nullptr, s->z[k] = nullptr;
+  for (int k = 0; k < 2; ++k) s->dzb[k] = s->dzt[k] = nullptr, s->dzf[k] = nullptr;
+  s->sf = s->dsf = s->part = nullptr;
+  s->lossp = nullptr;
+  s->mcap = 0;
+}
+
+int ensure_acts(vds_score *s, int M) {
+  if (M <= s->mcap) return VDS_OK;
+  free_acts(s);
+  const int Mc = (M + 127) / 128 * 128;
+  const size_t W = s->W;
+  cudaError_t ce = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (ce == cudaSuccess) ce = cudaMalloc(p, bytes);
+  };
+  A((void **)&s->a0, sizeof(bf16) * Mc * s->Dp);
+  A((void **)&s->a0t, sizeof(bf16) * Mc * s->Dp);
+  for (int k = 0; k < 3; ++k) {
+    A((void **)&s->h[k], sizeof(bf16) * Mc * W);
+    A((void **)&s->ht[k], sizeof(bf16) * Mc * W);
+    A((void **)&s->z[k], sizeof(float) * Mc * W);
+  }
+  for (int k = 0; k < 2; ++k) {
+    A((void **)&s->dzb[k], sizeof(bf16) * Mc * W);
+    A((void **)&s->dzt[k], sizeof(bf16) * Mc * W);
+    A((void **)&s->dzf[k], sizeof(float) * Mc * W);
+  }
+  A((void **)&s->dsb, sizeof(bf16) * Mc * 64);
+  A((void **)&s->dst, sizeof(bf16) * Mc * s->Op);
+  A((void **)&s->sf, sizeof(float) * Mc * s->Op);
+  A((void **)&s->dsf, sizeof(float) * Mc * s->Op);
+  A((void **)&s->part, sizeof(float) * 64 * W * W);
+  A((void **)&s->lossp, sizeof(double) * (Mc / 256 + 1));
+  if (ce != cudaSuccess) {
+    vds_last_cuda_error(ce);
+    free_acts(s);
+    return ce == cudaErrorMemoryAllocation ? VDS_ENOMEM : VDS_ECUDA;
+  }
+  s->mcap = Mc;
+  return VDS_OK;
+}
+
+int refresh_bf16(vds_ctx *c, vds_score *s) {
+  const int W = s->W;
+  auto conv = [&](const float *src, int rows, int cols, bf16 *dst, bf16 *dt, int tcols) -> int {
+    const long n = (long)rows * cols > (long)cols * tcols ? (long)rows * cols : (long)cols * tcols;
+    k_to_bf16<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(src, rows, cols, dst, dt, tcols);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    return VDS_OK;
+  };
+  VDS_TRY(conv(s->p + s->off[0], W, s->Dp, s->w1b, nullptr, 0));
+  VDS_TRY(conv(s->p + s->off[2], W, W, s->w2b, s->w2t, W));
+  VDS_TRY(conv(s->p + s->off[4], W, W, s->w3b, s->w3t, W));
+  VDS_TRY(conv(s->p + s->off[6], s->Op, W, s->w4b, s->w4t, 64));
+  return VDS_OK;
+}
+
+// forward for M rows (A0 built); train keeps Z/H^T for the backward pass
+int forward(vds_ctx *c, vds_score *s, int M, bool train, float *out, int ldo, int ncols_out) {
+  const int W = s->W;
+  const float *b1 = s->p + s->off[1], *b2 = s->p + s->off[3], *b3 = s->p + s->off[5], *b4 = s->p + s->off[7];
+  const int Mc = s->mcap;
+  VDS_TRY(gemm(c, s->a0, s->Dp, s->w1b, s->Dp, M, W, s->Dp, 1,
+               epi_act(EPI_SILU, M, W, W, b1, train ? s->z[0] : nullptr, s->h[0], train ? s->ht[0] : nullptr, Mc,
+                       nullptr)));
+  VDS_TRY(gemm(c, s->h[0], W, s->w2b, W, M, W, W, 1,
+               epi_act(EPI_SILU, M, W, W, b2, train ? s->z[1] : nullptr, s->h[1], train ? s->ht[1] : nullptr, Mc,
+                       nullptr)));
+  VDS_TRY(gemm(c, s->h[1], W, s->w3b, W, M, W, W, 1,
+               epi_act(EPI_SILU, M, W, W, b3, train ? s->z[2] : nullptr, s->h[2], train ? s->ht[2] : nullptr, Mc,
+                       nullptr)));
+  VDS_TRY(gemm(c, s->h[2], W, s->w4b, W, M, s->Op, W, 1, epi_f32(M, ncols_out, ldo, b4, out)));
+  return VDS_OK;
+}
+
+// loss and gradients (flat padded vector s->g) for a batch of M rows
+int loss_grad(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma, double *loss) {
+  const int W = s->W, Mc = s->mcap;
+  k_input<<<(unsigned)(((long)M * s->Dp + 255) / 256), 256, 0, c->stream>>>(x, eps, (float)sigma, M, s->D, s->Dp,
+                                                                           s->a0, s->a0t, Mc);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_TRY(forward(c, s, M, true, s->sf, s->Op, s->Op));
+  const int nb = (M + 255) / 256;
+  k_dsm_out<<<nb, 256, 0, c->stream>>>(s->sf, s->Op, eps, (float)sigma, M, s->D, s->dsf, s->Op, s->dsb, 64,
+                                       s->dst, Mc, s->lossp);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  // split-K over the batch for the weight gradients
+  int splits = M / KC;
+  while (splits > 64 || (M % (KC * splits)) != 0) --splits;
+  if (splits < 1) splits = 1;
+  auto wgrad = [&](const bf16 *At, int rows, const bf16 *Bt, int N, float *dst) -> int {
+    const long long stride = (long long)rows * N;
+    VDS_TRY(gemm(c, At, Mc, Bt, Mc, rows, N, M, splits, epi_f32(rows, N, N, nullptr, s->part, stride)));
+    k_split_reduce<<<(unsigned)((stride + 255) / 256), 256, 0, c->stream>>>(s->part, splits, stride, stride, dst);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    return VDS_OK;
+  };
+  auto bgrad = [&](const float *X, int n, int ld, float *dst) -> int {
+    k_colsum<<<n, 256, 0, c->stream>>>(X, M, n, ld, dst);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    return VDS_OK;
+  };
+  // layer 4
+  VDS_TRY(wgrad(s->dst, s->Op, s->ht[2], W, s->g + s->off[6]));
+  VDS_TRY(bgrad(s->dsf, s->Op, s->Op, s->g + s->off[7]));
+  // dZ3 = (dS W4) * silu'(Z3)
+  VDS_TRY(gemm(c, s->dsb, 64, s->w4t, 64, M, W, 64, 1,
+               epi_act(EPI_DSILU, M, W, W, nullptr, s->dzf[0], s->dzb[0], s->dzt[0], Mc, s->z[2])));
+  VDS_TRY(wgrad(s->dzt[0], W, s->ht[1], W, s->g + s->off[4]));
+  VDS_TRY(bgrad(s->dzf[0], W, W, s->g + s->off[5]));
+  // dZ2 = (dZ3 W3) * silu'(Z2)
+  VDS_TRY(gemm(c, s->dzb[0], W, s->w3t, W, M, W, W, 1,
+               epi_act(EPI_DSILU, M, W, W, nullptr, s->dzf[1], s->dzb[1], s->dzt[1], Mc, s->z[1])));
+  VDS_TRY(wgrad(s->dzt[1], W, s->ht[0], W, s->g + s->off[2]));
+  VDS_TRY(bgrad(s->dzf[1], W, W, s->g + s->off[3]));
+  // dZ1 = (dZ2 W2) * silu'(Z1)
+  VDS_TRY(gemm(c, s->dzb[1], W, s->w2t, W, M, W, W, 1,
+               epi_act(EPI_DSILU, M, W, W, nullptr, s->dzf[0], s->dzb[0], s->dzt[0], Mc, s->z[0])));
+  VDS_TRY(wgrad(s->dzt[0], W, s->a0t, s->Dp, s->g + s->off[0]));
+  VDS_TRY(bgrad(s->dzf[0], W, W, s->g + s->off[1]));
+  if (loss) {
+    std::vector<double> lp(nb);
+    VDS_CUDA_TRY(cudaMemcpyAsync(lp.data(), s->lossp, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream));
+    VDS_TRY(vds_sync_status(c));
+    double a = 0.0;
+    for (int k = 0; k < nb; ++k) a += lp[k];
+    *loss = a / (double)M;
+  }
+  return VDS_OK;
+}
+
+// flat unpadded parameter layout: W1 (W x D), b1 (W), W2 (W x W), b2, W3, b3,
+// W4 (D x W), b4 (D)
+long long flat_count(int D, int W) { return (long long)W * D + W + 2LL * (W * W + W) + (long long)D * W + D; }
+
+void pad_params(const vds_score *s, const float *in, std::vector<float> &out) {
+  const int D = s->D, W = s->W;
+  out.assign(s->np, 0.f);
+  long long k = 0;
+  for (int r = 0; r < W; ++r)
+    for (int cc = 0; cc < D; ++cc) out[s->off[0] + (long long)r * s->Dp + cc] = in[k++];
+  for (int r = 0; r < W; ++r) out[s->off[1] + r] = in[k++];
+  for (int l = 0; l < 2; ++l) {
+    for (long long e = 0; e < (long long)W * W; ++e) out[s->off[2 + 2 * l] + e] = in[k++];
+    for (int r = 0; r < W; ++r) out[s->off[3 + 2 * l] + r] = in[k++];
+  }
+  for (int r = 0; r < D; ++r)
+    for (int cc = 0; cc < W; ++cc) out[s->off[6] + (long long)r * W + cc] = in[k++];
+  for (int r = 0; r < D; ++r) out[s->off[7] + r] = in[k++];
+}
+
+void unpad_params(const vds_score *s, const std::vector<float> &in, float *out) {
+  const int D = s->D, W = s->W;
+  long long k = 0;
+  for (int r = 0; r < W; ++r)
+    for (int cc = 0; cc < D; ++cc) out[k++] = in[s->off[0] + (long long)r * s->Dp + cc];
+  for (int r = 0; r < W; ++r) out[k++] = in[s->off[1] + r];
+  for (int l = 0; l < 2; ++l) {
+    for (long long e = 0; e < (long long)W * W; ++e) out[k++] = in[s->off[2 + 2 * l] + e];
+    for (int r = 0; r < W; ++r) out[k++] = in[s->off[3 + 2 * l] + r];
+  }
+  for (int r = 0; r < D; ++r)
+    for (int cc = 0; cc < W; ++cc) out[k++] = in[s->off[6] + (long long)r * W + cc];
+  for (int r = 0; r < D; ++r) out[k++] = in[s->off[7] + r];
+}
+
+}  // namespace
+
+extern "C" {
+
+int vds_score_create(vds_ctx *c, int D, int width, const float *params, vds_score **out) {
+  if (!c || !out || !params || D < 1 || D > 16 || width != 256) return VDS_EARG;
+  *out = nullptr;
+  Dev dg(c->device);
+  vds_score *s = new vds_score();
+  s->device = c->device;
+  s->D = D;
+  s->W = width;
+  const int W = width;
+  long long o = 0;
+  s->off[0] = o; o += (long long)W * s->Dp;
+  s->off[1] = o; o += W;
+  s->off[2] = o; o += (long long)W * W;
+  s->off[3] = o; o += W;
+  s->off[4] = o; o += (long long)W * W;
+  s->off[5] = o; o += W;
+  s->off[6] = o; o += (long long)s->Op * W;
+  s->off[7] = o; o += s->Op;
+  s->np = o;
+  cudaError_t ce = cudaSuccess;
+  auto A = [&](void **p, size_t bytes) {
+    if (ce == cudaSuccess) ce = cudaMalloc(p, bytes);
+  };
+  A((void **)&s->p, sizeof(float) * o);
+  A((void **)&s->m, sizeof(float) * o);
+  A((void **)&s->v, sizeof(float) * o);
+  A((void **)&s->g, sizeof(float) * o);
+  A((void **)&s->w1b, sizeof(bf16) * W * s->Dp);
+  A((void **)&s->w2b, sizeof(bf16) * W * W);
+  A((void **)&s->w3b, sizeof(bf16) * W * W);
+  A((void **)&s->w4b, sizeof(bf16) * s->Op * W);
+  A((void **)&s->w2t, sizeof(bf16) * W * W);
+  A((void **)&s->w3t, sizeof(bf16) * W * W);
+  A((void **)&s->w4t, sizeof(bf16) * W * 64);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->m, 0, sizeof(float) * o, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->v, 0, sizeof(float) * o, c->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->g, 0, sizeof(float) * o, c->stream);
+  if (ce != cudaSuccess) {
+    vds_last_cuda_error(ce);
+    vds_score_free(s);
+    return ce == cudaErrorMemoryAllocation ? VDS_ENOMEM : VDS_ECUDA;
+  }
+  int st = vds_score_set_params(c, s, params);
+  if (st != VDS_OK) {
+    vds_score_free(s);
+    return st;
+  }
+  *out = s;
+  return VDS_OK;
+}
+
+void vds_score_free(vds_score *s) {
+  if (!s) return;
+  Dev dg(s->device);
+  free_acts(s);
+  void *ptrs[] = {s->p, s->m, s->v, s->g, s->w1b, s->w2b, s->w3b, s->w4b, s->w2t, s->w3t, s->w4t};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+long vds_score_param_count(int D, int width) { return (long)flat_count(D, width); }
+
+int vds_score_set_params(vds_ctx *c, vds_score *s, const float *params) {
+  if (!c || !s || !params) return VDS_EARG;
+  Dev dg(c->device);
+  std::vector<float> pad;
+  pad_params(s, params, pad);
+  VDS_CUDA_TRY(cudaMemcpyAsync(s->p, pad.data(), sizeof(float) * s->np, cudaMemcpyHostToDevice, c->stream));
+  VDS_CUDA_TRY(cudaMemsetAsync(s->m, 0, sizeof(float) * s->np, c->stream));
+  VDS_CUDA_TRY(cudaMemsetAsync(s->v, 0, sizeof(float) * s->np, c->stream));
+  s->t = 0;
+  VDS_TRY(refresh_bf16(c, s));
+  return vds_sync_status(c);
+}
+
+int vds_score_get_params(vds_ctx *c, const vds_score *s, float *params) {
+  if (!c || !s || !params) return VDS_EARG;
+  Dev dg(c->device);
+  std::vector<float> pad(s->np);
+  VDS_CUDA_TRY(cudaMemcpyAsync(pad.data(), s->p, sizeof(float) * s->np, cudaMemcpyDeviceToHost, c->stream));
+  VDS_TRY(vds_sync_status(c));
+  unpad_params(s, pad, params);
+  return VDS_OK;
+}
+
+int vds_score_eval(vds_ctx *c, vds_score *s, const float *x, int N, float *out) {
+  if (!c || !s || !x || !out || N < 1) return VDS_EARG;
+  Dev dg(c->device);
+  const int chunk = 65536;
+  VDS_TRY(ensure_acts(s, N < chunk ? N : chunk));
+  for (int n0 = 0; n0 < N; n0 += chunk) {
+    const int M = (N - n0) < chunk ? (N - n0) : chunk;
+    k_input<<<(unsigned)(((long)M * s->Dp + 255) / 256), 256, 0, c->stream>>>(x + (size_t)n0 * s->D, nullptr,
+                                                                             0.f, M, s->D, s->Dp, s->a0, nullptr, 0);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    VDS_TRY(forward(c, s, M, false, out + (size_t)n0 * s->D, s->D, s->D));
+  }
+  return VDS_OK;
+}
+
+int vds_score_loss_grad(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma,
+                        double *loss, float *grads) {
+  if (!c || !s || !x || !eps || M < 128 || M % 128 != 0 || !(sigma > 0.0)) return VDS_EARG;
+  Dev dg(c->device);
+  VDS_TRY(ensure_acts(s, M));
+  VDS_TRY(loss_grad(c, s, x, eps, M, sigma, loss));
+  if (grads) {
+    std::vector<float> pad(s->np);
+    VDS_CUDA_TRY(cudaMemcpyAsync(pad.data(), s->g, sizeof(float) * s->np, cudaMemcpyDeviceToHost, c->stream));
+    VDS_TRY(vds_sync_status(c));
+    unpad_params(s, pad, grads);
+  }
+  return vds_sync_status(c);
+}
+
+int vds_score_train(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma, double lr,
+                    double *loss) {
+  if (!c || !s || !x || !eps || M < 128 || M % 128 != 0 || !(sigma > 0.0) || !(lr > 0.0)) return VDS_EARG;
+  Dev dg(c->device);
+  VDS_TRY(ensure_acts(s, M));
+  VDS_TRY(loss_grad(c, s, x, eps, M, sigma, loss));
+  s->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)s->t), c2 = 1.f - powf(b2, (float)s->t);
+  k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, c->stream>>>(s->p, s->m, s->v, s->g, s->np, (float)lr, b1, b2,
+                                                                1e-8f, c1, c2);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_TRY(refresh_bf16(c, s));
+  return loss ? vds_sync_status(c) : VDS_OK;
+}
+
+}  // extern "C"

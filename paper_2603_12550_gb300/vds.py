@@ -92,6 +92,14 @@ _SIGS = {
     "vds_batch_queue": ([_vp, _ip, _i], _i),
     "vds_batch_energy_grad": ([_vp, _vp, _vp, _dp, _vp, _vp], _i),
     "vds_batch_step": ([_vp, _vp, _vp, _i, _ip], _i),
+    "vds_score_param_count": ([_i, _i], _l),
+    "vds_score_create": ([_vp, _i, _i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)], _i),
+    "vds_score_free": ([_vp], None),
+    "vds_score_set_params": ([_vp, _vp, ctypes.POINTER(ctypes.c_float)], _i),
+    "vds_score_get_params": ([_vp, _vp, ctypes.POINTER(ctypes.c_float)], _i),
+    "vds_score_eval": ([_vp, _vp, _vp, _i, _vp], _i),
+    "vds_score_loss_grad": ([_vp, _vp, _vp, _vp, _i, _d, _dp, ctypes.POINTER(ctypes.c_float)], _i),
+    "vds_score_train": ([_vp, _vp, _vp, _vp, _i, _d, _d, _dp], _i),
     "pod_brownian": ([_vp, _vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "pod_step": ([_vp, _vp, _vp, _i, _i, _pp, _i, _i, _i], _i),
 }
@@ -271,6 +279,75 @@ class Batch:
     def free(self):
         if self.h:
             lib.vds_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def flatten_layers(layers):
+    """[(W, b)] -> flat FP32 parameter vector in the order of vds_score.h."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                           for W, b in layers]).astype(np.float32)
+
+
+def unflatten(flat, D, width=256):
+    shapes = [(width, D), (width, width), (width, width), (D, width)]
+    out, k = [], 0
+    for r, cc in shapes:
+        W = flat[k:k + r * cc].reshape(r, cc)
+        k += r * cc
+        b = flat[k:k + r]
+        k += r
+        out.append((W, b))
+    return out
+
+
+class Score:
+    """Owns a vds_score network (include/vds_score.h)."""
+
+    def __init__(self, ctx: "Context", D, layers, width=256):
+        self.ctx, self.D, self.width = ctx, int(D), int(width)
+        flat = flatten_layers(layers)
+        n = lib.vds_score_param_count(self.D, self.width)
+        assert flat.size == n, (flat.size, n)
+        out = _vp()
+        _check(lib.vds_score_create(ctx.h, self.D, self.width,
+                                    flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(out)))
+        self.h = out
+        self.n = n
+
+    def params(self):
+        buf = np.empty(self.n, dtype=np.float32)
+        _check(lib.vds_score_get_params(self.ctx.h, self.h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return unflatten(buf, self.D, self.width)
+
+    def set_params(self, layers):
+        flat = flatten_layers(layers)
+        _check(lib.vds_score_set_params(self.ctx.h, self.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def eval(self, x, out):
+        _check(lib.vds_score_eval(self.ctx.h, self.h, _ptr(x), int(x.shape[0]), _ptr(out)))
+
+    def loss_grad(self, x, eps, sigma):
+        loss = ctypes.c_double()
+        g = np.empty(self.n, dtype=np.float32)
+        _check(lib.vds_score_loss_grad(self.ctx.h, self.h, _ptr(x), _ptr(eps), int(x.shape[0]), float(sigma),
+                                       ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, unflatten(g, self.D, self.width)
+
+    def train_step(self, x, eps, sigma, lr, want_loss=True):
+        loss = ctypes.c_double()
+        _check(lib.vds_score_train(self.ctx.h, self.h, _ptr(x), _ptr(eps), int(x.shape[0]), float(sigma),
+                                   float(lr), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def free(self):
+        if self.h:
+            lib.vds_score_free(self.h)
             self.h = None
 
     def __del__(self):
