@@ -63,6 +63,24 @@ VDS_API int pod_brownian(vds_ctx *ctx, const pod_basis *b, const float *P, int N
 VDS_API int pod_step(vds_ctx *ctx, const pod_basis *b, float *P, int N, int D,
                      const vds_params *p, int nsteps, int refresh_every, int mode);
 
+/* Reduced-order stepping with the learned score surrogate (include/
+ * vds_score.h; not in the paper): as pod_step mode 1 but with the O(N^2)
+ * entropy gradient S replaced by the network's score at the lifted state,
+ * mean-centred over the particles (the exact S sums to zero):
+ *   Pdot = Phi^T [kappa q~ - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi(q~))].
+ * Every check_every steps (0: never) the exact S is evaluated (full density
+ * and gradient passes) and compared on check_n particles (every
+ * (N/check_n)-th) by ||s - mean s - S|| / ||S||; above check_tol that step
+ * uses the exact S (fallback).  check_err (host, may be NULL) receives the
+ * largest relative error seen, fallbacks (host, may be NULL) their number. */
+#ifndef VDS_SCORE_TYPEDEF
+#define VDS_SCORE_TYPEDEF
+typedef struct vds_score vds_score;
+#endif
+VDS_API int pod_step_score(vds_ctx *ctx, const pod_basis *b, vds_score *score, float *P, int N,
+                           int D, const vds_params *p, int nsteps, int check_every, int check_n,
+                           double check_tol, double *check_err, int *fallbacks);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,10 @@
 extern "C" {
 #endif
 
+#ifndef VDS_SCORE_TYPEDEF
+#define VDS_SCORE_TYPEDEF
 typedef struct vds_score vds_score;
+#endif
 
 VDS_API long vds_score_param_count(int D, int width);
 /* Create a network with input/output dimension D (<= 16), width 256, from

@@ -413,6 +413,24 @@ def velocity(q, p: OrParams):
     return v.reshape(N, D)
 
 
+def score_rhs(P, Phi, p: OrParams, layers):
+    """Reduced RHS with the learned score in place of the entropy gradient:
+    Pdot = U^T [kappa q~ - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi)],
+    q~ = U P, s = s_theta(q~) (FP64 forward of the given network), the mean
+    taken over particles."""
+    from . import mlp
+    q = lift(Phi, P, p.s, p.nb)
+    N, D = q.shape
+    s, _ = mlp.forward(mlp.as64(layers), q)
+    s = s - s.mean(axis=0)
+    g = p.kBT * s + spring_grad(q, p)
+    A = rouse(p.nb)
+    kap = np.array(p.kappa[:p.s * p.s]).reshape(p.s, p.s)
+    qb, gb = q.reshape(N, p.nb, p.s), g.reshape(N, p.nb, p.s)
+    v = np.einsum("ab,Ikb->Ika", kap, qb) - np.einsum("kj,Ija->Ika", A, gb) / p.zeta
+    return project(Phi, v.reshape(N, D), p.s, p.nb)
+
+
 def galerkin_rhs(P, Phi, p: OrParams):
     """Mode i: Pdot = U^T v(U P) (Eq. model_DymRepParPod at the lifted state)."""
     q = lift(Phi, P, p.s, p.nb)

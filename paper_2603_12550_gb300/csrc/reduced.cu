@@ -18,6 +18,7 @@
 // tall-skinny Grams.
 #include <math.h>
 
+#include "../../include/vds_score.h"
 #include "pair.cuh"
 #include "pod_internal.cuh"
 
@@ -175,6 +176,113 @@ __global__ void k_combine_xb(const double *__restrict__ G1, const double *__rest
   if (o < n) XB[o] = scale * (G1[o] + G2[o]);
 }
 
+// column means of an N x D matrix (one block per column, fixed order)
+__global__ void k_colmean(const float *__restrict__ s, int N, int D, double *__restrict__ mean) {
+  __shared__ double sh[256];
+  const int col = blockIdx.x;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += (double)s[(size_t)i * D + col];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) mean[col] = sh[0] / (double)N;
+}
+
+// particle velocity with the entropy gradient replaced by the surrogate
+// (mean-centred): v = kappa q - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi)
+template <int D>
+__global__ void k_score_vel(KParams kp, const float *__restrict__ q, const float *__restrict__ sc,
+                            const double *__restrict__ smean, float *__restrict__ v, int *err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kp.N) return;
+  double y[D], g[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[a] = (double)q[(size_t)i * D + a];
+  double f[8];
+  for (int k = 0; k < kp.nb; ++k) {
+    double n2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a / kp.s == k) n2 += y[a] * y[a];
+    if (kp.spring == 0) {
+      f[k] = kp.H[k];
+    } else {
+      const double x = 1.0 - n2 / kp.b;
+      if (!(x > 0.0)) vds_flag(err, VDS_EDOMAIN);
+      f[k] = x > 0.0 ? kp.H[k] / x : 0.0;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    g[a] = kp.kBT * ((double)sc[(size_t)i * D + a] - (smean ? smean[a] : 0.0)) + f[a / kp.s] * y[a];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int k = a / kp.s, al = a - k * kp.s;
+    double vv = 0.0, m = 0.0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      const int kb = b / kp.s, be = b - kb * kp.s;
+      if (kb == k) vv += kp.kappa[al * kp.s + be] * y[b];
+      if (be == al) m += rA(k, kb) * g[b];
+    }
+    v[(size_t)i * D + a] = (float)(vv - m / kp.zeta);
+  }
+}
+
+// sums over the checked particles (every stride-th) of |s - mean s - S|^2 and |S|^2
+__global__ void k_check_err(const float *__restrict__ sc, const double *__restrict__ smean,
+                            const float *__restrict__ S, int N, int D, int stride, double *__restrict__ out) {
+  __shared__ double sh[2][256];
+  double e = 0.0, n = 0.0;
+  for (int r = threadIdx.x; (long)r * stride < N; r += blockDim.x) {
+    const long i = (long)r * stride;
+    for (int a = 0; a < D; ++a) {
+      const double d = (double)sc[i * D + a] - smean[a] - (double)S[i * D + a];
+      e += d * d;
+      n += (double)S[i * D + a] * S[i * D + a];
+    }
+  }
+  sh[0][threadIdx.x] = e;
+  sh[1][threadIdx.x] = n;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + o];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+  }
+}
+
+template <int D>
+int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean,
+                   float *v) {
+  k_score_vel<D><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp, q, sc, smean, v, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean, float *v) {
+  switch (kp.D) {
+    case 2: return score_vel_impl<2>(c, kp, q, sc, smean, v);
+    case 3: return score_vel_impl<3>(c, kp, q, sc, smean, v);
+    case 4: return score_vel_impl<4>(c, kp, q, sc, smean, v);
+    case 6: return score_vel_impl<6>(c, kp, q, sc, smean, v);
+    case 8: return score_vel_impl<8>(c, kp, q, sc, smean, v);
+    case 9: return score_vel_impl<9>(c, kp, q, sc, smean, v);
+    case 12: return score_vel_impl<12>(c, kp, q, sc, smean, v);
+    default: return VDS_EARG;
+  }
+}
+
 template <int D, int S>
 int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
   dim3 grid((N + RF_NT - 1) / RF_NT, (b->r + RT - 1) / RT);
@@ -307,6 +415,70 @@ int pod_step(vds_ctx *c, const pod_basis *b, float *P, int N, int D, const vds_p
       ++c->launches;
     }
   }
+  return vds_sync_status(c);
+}
+
+int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int N, int D, const vds_params *p,
+                   int nsteps, int check_every, int check_n, double check_tol, double *check_err,
+                   int *fallbacks) {
+  if (!c || !P || !sc || nsteps < 0 || check_every < 0 || (check_every > 0 && check_n < 1)) return VDS_EARG;
+  VDS_TRY(check(p, b, N, D));
+  if (!(p->dt > 0.0)) return VDS_EARG;
+  if (D != 2 && D != 3 && D != 4 && D != 6 && D != 8 && D != 9 && D != 12) return VDS_EARG;
+  if (check_err) *check_err = 0.0;
+  if (fallbacks) *fallbacks = 0;
+  if (nsteps == 0) return VDS_OK;
+  Dev dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  vds_params pS = *p;  // exact entropy gradient alone: kBT = 1, no springs
+  pS.kBT = 1.0;
+  pS.spring = 0;
+  for (int j = 0; j < 8; ++j) pS.H[j] = 0.0;
+  const KParams kS = make_kparams(&pS, N, D);
+  const int r = b->r, nb = p->nb, n = r * nb;
+  const size_t nd = (size_t)N * D;
+  VDS_TRY(vds_ensure(c, c->vecs, 4 * nd * sizeof(float)));
+  float *qt = (float *)c->vecs.ptr, *sbuf = qt + nd, *Sx = sbuf + nd, *vel = Sx + nd;
+  VDS_TRY(vds_ensure(c, c->ubuf, (2 * 512 + 64) * sizeof(double)));
+  double *Pd = (double *)c->ubuf.ptr, *Pdot = Pd + 512, *smean = Pdot + 512, *errs = smean + 32;
+  k_f2d<<<(n + 255) / 256, 256, 0, c->stream>>>(P, Pd, n);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  const int stride = check_n >= N ? 1 : N / check_n;
+  double worst = 0.0;
+  int nfall = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
+    VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
+    k_colmean<<<D, 256, 0, c->stream>>>(sbuf, N, D, smean);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    bool exact = false;
+    if (check_every > 0 && step % check_every == 0) {
+      VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
+      VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr));
+      VDS_TRY(pass_grad(c, kS, GM_OUT, Sx, qt, nullptr, nullptr, nullptr, nullptr));
+      k_check_err<<<1, 256, 0, c->stream>>>(sbuf, smean, Sx, N, D, stride, errs);
+      VDS_CUDA_TRY(cudaGetLastError());
+      ++c->launches;
+      double h_err[2];
+      VDS_CUDA_TRY(cudaMemcpyAsync(h_err, errs, sizeof(h_err), cudaMemcpyDeviceToHost, c->stream));
+      VDS_TRY(vds_sync_status(c));
+      const double rel = h_err[1] > 0.0 ? sqrt(h_err[0] / h_err[1]) : 0.0;
+      if (rel > worst) worst = rel;
+      if (!(rel <= check_tol)) {
+        exact = true;
+        ++nfall;
+      }
+    }
+    VDS_TRY(score_vel(c, kp, qt, exact ? Sx : sbuf, exact ? nullptr : smean, vel));
+    VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
+    k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+  }
+  if (check_err) *check_err = worst;
+  if (fallbacks) *fallbacks = nfall;
   return vds_sync_status(c);
 }
 

@@ -100,6 +100,7 @@ _SIGS = {
     "vds_score_eval": ([_vp, _vp, _vp, _i, _vp], _i),
     "vds_score_loss_grad": ([_vp, _vp, _vp, _vp, _i, _d, _dp, ctypes.POINTER(ctypes.c_float)], _i),
     "vds_score_train": ([_vp, _vp, _vp, _vp, _i, _d, _d, _dp], _i),
+    "pod_step_score": ([_vp, _vp, _vp, _vp, _i, _i, _pp, _i, _i, _i, _d, _dp, _ip], _i),
     "pod_brownian": ([_vp, _vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "pod_step": ([_vp, _vp, _vp, _i, _i, _pp, _i, _i, _i], _i),
 }
@@ -234,6 +235,14 @@ class Context:
         b2 = (ctypes.c_double * (r * r))()
         _check(lib.pod_brownian(self.h, basis.h, _ptr(P), int(N), int(D), ctypes.byref(p), b1, b2))
         return np.array(b1[:]).reshape(r, r), np.array(b2[:]).reshape(r, r)
+
+    def pod_step_score(self, basis: "PodBasis", score: "Score", P, N, D, p: VdsParams, nsteps=1,
+                       check_every=20, check_n=4096, check_tol=0.25):
+        err, nf = ctypes.c_double(), ctypes.c_int()
+        _check(lib.pod_step_score(self.h, basis.h, score.h, _ptr(P), int(N), int(D), ctypes.byref(p),
+                                  int(nsteps), int(check_every), int(check_n), float(check_tol),
+                                  ctypes.byref(err), ctypes.byref(nf)))
+        return err.value, nf.value
 
     def pod_step(self, basis: "PodBasis", P, N, D, p: VdsParams, nsteps=1, refresh_every=1, mode=2):
         _check(lib.pod_step(self.h, basis.h, _ptr(P), int(N), int(D), ctypes.byref(p), int(nsteps),

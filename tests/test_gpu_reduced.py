@@ -105,3 +105,38 @@ def test_mode2_rejects_fene(vds, ctx, setup):
     pf = vds.params(S["nb"], S["s"], h=0.9, dt=0.005, spring=1, b=50.0)
     with pytest.raises(vds.VdsError):
         ctx.pod_step(S["basis"], P, S["N"], S["nb"] * S["s"], pf, nsteps=1, mode=2)
+
+
+def _score_net(vds, ctx, seed=11):
+    from paper_2603_12550_gb300 import inputs as inp
+    layers = inp.mlp_init((9, 256, 256, 256, 9), seed=seed, scale=0.5)
+    return layers, vds.Score(ctx, 9, layers)
+
+
+def test_score_mode_matches_oracle(orc, vds, ctx, setup):
+    # the surrogate reduced step (no checks) against the FP64 oracle with the
+    # same network weights; BF16 network: 1e-2 relative on P
+    S = setup
+    layers, net = _score_net(vds, ctx)
+    P = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    D = S["nb"] * S["s"]
+    ctx.pod_step_score(S["basis"], net, P, S["N"], D, S["pg"], nsteps=3, check_every=0)
+    Po = S["P0"].astype(np.float32).astype(np.float64)
+    for _ in range(3):
+        Po = Po + S["po"].dt * orc.score_rhs(Po, S["Phi"], S["po"], layers)
+    assert _rel(P.cpu().numpy(), Po) <= 1e-2
+
+
+def test_score_check_falls_back_to_exact(vds, ctx, setup):
+    # with a zero tolerance every checked step uses the exact entropy gradient,
+    # which is the Galerkin step
+    S = setup
+    _, net = _score_net(vds, ctx)
+    D = S["nb"] * S["s"]
+    P1 = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    P2 = P1.clone()
+    err, nf = ctx.pod_step_score(S["basis"], net, P1, S["N"], D, S["pg"], nsteps=3, check_every=1,
+                                 check_n=100, check_tol=0.0)
+    assert nf == 3 and err > 0.0
+    ctx.pod_step(S["basis"], P2, S["N"], D, S["pg"], nsteps=3, mode=1)
+    assert _rel(P1.cpu().numpy(), P2.cpu().numpy()) <= 1e-5
