@@ -35,15 +35,27 @@ VDS_API int vds_score_set_params(vds_ctx *ctx, vds_score *s, const float *params
 VDS_API int vds_score_get_params(vds_ctx *ctx, const vds_score *s, float *params);
 /* out (device, N x D) = s_theta(x) for x (device, N x D). */
 VDS_API int vds_score_eval(vds_ctx *ctx, vds_score *s, const float *x, int N, float *out);
-/* Denoising score-matching loss on a batch (device x, eps: M x D, M a
- * multiple of 128): L = (1/M) sum_m |s_theta(x_m + sigma eps_m) + eps_m/sigma|^2
- * and its gradient (host, flat as the parameters, may be NULL); *loss host. */
-VDS_API int vds_score_loss_grad(vds_ctx *ctx, vds_score *s, const float *x, const float *eps, int M,
-                                double sigma, double *loss, float *grads);
+/* Denoising score-matching loss on a batch of M rows (M a multiple of 128):
+ * L = (1/M) sum_m |s_theta(x_m + sigma eps_m) + eps_m/sigma|^2 and its
+ * gradient (host, flat as the parameters, may be NULL); *loss host.  The
+ * batch rows are x[rows[m]] when rows (device, M ints) is given, else x[m]
+ * (x device, rows x D); eps device M x D. */
+VDS_API int vds_score_loss_grad(vds_ctx *ctx, vds_score *s, const float *x, const int *rows,
+                                const float *eps, int M, double sigma, double *loss, float *grads);
 /* One Adam step (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on the
  * gradient of the DSM loss of the batch; *loss (host, may be NULL). */
-VDS_API int vds_score_train(vds_ctx *ctx, vds_score *s, const float *x, const float *eps, int M,
-                            double sigma, double lr, double *loss);
+VDS_API int vds_score_train(vds_ctx *ctx, vds_score *s, const float *x, const int *rows,
+                            const float *eps, int M, double sigma, double lr, double *loss);
+
+/* Supervised fit to given target scores (e.g. the exact VDS entropy gradient
+ * of the same particles, which carries the second, 1/rho_J term of
+ * Eq. model_DymRepPar that the denoising objective does not see):
+ *   L = (1/M) sum_m |s_theta(x_m) - t_m|^2,
+ * rows as in vds_score_loss_grad (t_m = target[rows[m]] when rows is given).
+ * lr > 0 takes one Adam step; grads (host, may be NULL) as in
+ * vds_score_loss_grad; *loss host (may be NULL). */
+VDS_API int vds_score_fit(vds_ctx *ctx, vds_score *s, const float *x, const int *rows,
+                          const float *target, int M, double lr, double *loss, float *grads);
 
 #ifdef __cplusplus
 }

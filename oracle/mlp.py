@@ -94,3 +94,21 @@ def adam_step(layers, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         mo.append((res[0][1], res[1][1]))
         vo.append((res[0][2], res[1][2]))
     return out, mo, vo
+
+
+def fit_grad(layers, x, target):
+    """(loss, grads) of the supervised fit L = (1/B) sum_b |s_theta(x_b) - t_b|^2."""
+    x = np.asarray(x, dtype=np.float64)
+    s, cache = forward(layers, x)
+    B = x.shape[0]
+    r = s - np.asarray(target, dtype=np.float64)
+    loss = np.mean(np.sum(r * r, axis=1))
+    d = 2.0 * r / B
+    grads = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        h_in, z = cache[l]
+        if l < len(layers) - 1:
+            d = d * silu_grad(z)
+        grads[l] = (d.T @ h_in, d.sum(axis=0))
+        d = d @ layers[l][0]
+    return loss, grads

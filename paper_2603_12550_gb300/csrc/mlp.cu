@@ -214,14 +214,14 @@ constexpr size_t GEMM_SMEM = 2 * (16384 + 32768);
 // ------------------------------------------------------------ small kernels
 
 // A0 = bf16(x + sigma eps) padded to Dp columns (and its transpose)
-__global__ void k_input(const float *__restrict__ x, const float *__restrict__ eps, float sigma, int M, int D,
-                        int Dp, bf16 *__restrict__ a0, bf16 *__restrict__ a0t, int ldt) {
+__global__ void k_input(const float *__restrict__ x, const int *__restrict__ rows, const float *__restrict__ eps,
+                        float sigma, int M, int D, int Dp, bf16 *__restrict__ a0, bf16 *__restrict__ a0t, int ldt) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long)M * Dp) return;
   const int m = (int)(idx / Dp), k = (int)(idx - (long)m * Dp);
   float v = 0.f;
   if (k < D) {
-    v = x[(size_t)m * D + k];
+    v = x[(size_t)(rows ? rows[m] : m) * D + k];
     if (eps) v += sigma * eps[(size_t)m * D + k];
   }
   const bf16 b = __float2bfloat16_rn(v);
@@ -240,6 +240,39 @@ __global__ void k_dsm_out(const float *__restrict__ S, int ldS, const float *__r
       float g = 0.f;
       if (k < D) {
         const float r = S[(size_t)m * ldS + k] + eps[(size_t)m * D + k] / sigma;
+        l += (double)r * r;
+        g = 2.f * r / (float)M;
+      }
+      if (k < Op) {
+        dSf[(size_t)m * Op + k] = g;
+        dSt[(size_t)k * ldt + m] = __float2bfloat16_rn(g);
+      }
+      dSb[(size_t)m * ldb + k] = __float2bfloat16_rn(g);
+    }
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = l;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lossp[blockIdx.x] = sh[0];
+}
+
+// regression: dS = (2/M)(s - t), t = target[rows[m]] (or target[m])
+__global__ void k_fit_out(const float *__restrict__ S, int ldS, const float *__restrict__ target,
+                          const int *__restrict__ rows, int M, int D, float *__restrict__ dSf, int Op,
+                          bf16 *__restrict__ dSb, int ldb, bf16 *__restrict__ dSt, int ldt,
+                          double *__restrict__ lossp) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double l = 0.0;
+  if (m < M) {
+    const size_t tr = (size_t)(rows ? rows[m] : m) * D;
+    for (int k = 0; k < ldb; ++k) {
+      float g = 0.f;
+      if (k < D) {
+        const float r = S[(size_t)m * ldS + k] - target[tr + k];
         l += (double)r * r;
         g = 2.f * r / (float)M;
       }
@@ -478,16 +511,22 @@ int forward(vds_ctx *c, vds_score *s, int M, bool train, float *out, int ldo, in
 }
 
 // loss and gradients (flat padded vector s->g) for a batch of M rows
-int loss_grad(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma, double *loss) {
+int loss_grad(vds_ctx *c, vds_score *s, const float *x, const int *rows, const float *eps, int M, double sigma,
+              double *loss, const float *target = nullptr) {
   const int W = s->W, Mc = s->mcap;
-  k_input<<<(unsigned)(((long)M * s->Dp + 255) / 256), 256, 0, c->stream>>>(x, eps, (float)sigma, M, s->D, s->Dp,
-                                                                           s->a0, s->a0t, Mc);
+  k_input<<<(unsigned)(((long)M * s->Dp + 255) / 256), 256, 0, c->stream>>>(x, rows, target ? nullptr : eps,
+                                                                           (float)sigma, M, s->D, s->Dp, s->a0,
+                                                                           s->a0t, Mc);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   VDS_TRY(forward(c, s, M, true, s->sf, s->Op, s->Op));
   const int nb = (M + 255) / 256;
-  k_dsm_out<<<nb, 256, 0, c->stream>>>(s->sf, s->Op, eps, (float)sigma, M, s->D, s->dsf, s->Op, s->dsb, 64,
-                                       s->dst, Mc, s->lossp);
+  if (target)
+    k_fit_out<<<nb, 256, 0, c->stream>>>(s->sf, s->Op, target, rows, M, s->D, s->dsf, s->Op, s->dsb, 64, s->dst,
+                                         Mc, s->lossp);
+  else
+    k_dsm_out<<<nb, 256, 0, c->stream>>>(s->sf, s->Op, eps, (float)sigma, M, s->D, s->dsf, s->Op, s->dsb, 64,
+                                         s->dst, Mc, s->lossp);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   // split-K over the batch for the weight gradients
@@ -670,7 +709,8 @@ int vds_score_eval(vds_ctx *c, vds_score *s, const float *x, int N, float *out) 
   for (int n0 = 0; n0 < N; n0 += chunk) {
     const int M = (N - n0) < chunk ? (N - n0) : chunk;
     k_input<<<(unsigned)(((long)M * s->Dp + 255) / 256), 256, 0, c->stream>>>(x + (size_t)n0 * s->D, nullptr,
-                                                                             0.f, M, s->D, s->Dp, s->a0, nullptr, 0);
+                                                                             nullptr, 0.f, M, s->D, s->Dp, s->a0,
+                                                                             nullptr, 0);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
     VDS_TRY(forward(c, s, M, false, out + (size_t)n0 * s->D, s->D, s->D));
@@ -678,12 +718,12 @@ int vds_score_eval(vds_ctx *c, vds_score *s, const float *x, int N, float *out) 
   return VDS_OK;
 }
 
-int vds_score_loss_grad(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma,
-                        double *loss, float *grads) {
+int vds_score_loss_grad(vds_ctx *c, vds_score *s, const float *x, const int *rows, const float *eps, int M,
+                        double sigma, double *loss, float *grads) {
   if (!c || !s || !x || !eps || M < 128 || M % 128 != 0 || !(sigma > 0.0)) return VDS_EARG;
   Dev dg(c->device);
   VDS_TRY(ensure_acts(s, M));
-  VDS_TRY(loss_grad(c, s, x, eps, M, sigma, loss));
+  VDS_TRY(loss_grad(c, s, x, rows, eps, M, sigma, loss));
   if (grads) {
     std::vector<float> pad(s->np);
     VDS_CUDA_TRY(cudaMemcpyAsync(pad.data(), s->g, sizeof(float) * s->np, cudaMemcpyDeviceToHost, c->stream));
@@ -693,12 +733,12 @@ int vds_score_loss_grad(vds_ctx *c, vds_score *s, const float *x, const float *e
   return vds_sync_status(c);
 }
 
-int vds_score_train(vds_ctx *c, vds_score *s, const float *x, const float *eps, int M, double sigma, double lr,
-                    double *loss) {
+int vds_score_train(vds_ctx *c, vds_score *s, const float *x, const int *rows, const float *eps, int M,
+                    double sigma, double lr, double *loss) {
   if (!c || !s || !x || !eps || M < 128 || M % 128 != 0 || !(sigma > 0.0) || !(lr > 0.0)) return VDS_EARG;
   Dev dg(c->device);
   VDS_TRY(ensure_acts(s, M));
-  VDS_TRY(loss_grad(c, s, x, eps, M, sigma, loss));
+  VDS_TRY(loss_grad(c, s, x, rows, eps, M, sigma, loss));
   s->t += 1;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)s->t), c2 = 1.f - powf(b2, (float)s->t);
@@ -707,6 +747,31 @@ int vds_score_train(vds_ctx *c, vds_score *s, const float *x, const float *eps, 
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   VDS_TRY(refresh_bf16(c, s));
+  return loss ? vds_sync_status(c) : VDS_OK;
+}
+
+int vds_score_fit(vds_ctx *c, vds_score *s, const float *x, const int *rows, const float *target, int M, double lr,
+                  double *loss, float *grads) {
+  if (!c || !s || !x || !target || M < 128 || M % 128 != 0 || !(lr >= 0.0)) return VDS_EARG;
+  Dev dg(c->device);
+  VDS_TRY(ensure_acts(s, M));
+  VDS_TRY(loss_grad(c, s, x, rows, nullptr, M, 1.0, loss, target));
+  if (grads) {
+    std::vector<float> pad(s->np);
+    VDS_CUDA_TRY(cudaMemcpyAsync(pad.data(), s->g, sizeof(float) * s->np, cudaMemcpyDeviceToHost, c->stream));
+    VDS_TRY(vds_sync_status(c));
+    unpad_params(s, pad, grads);
+  }
+  if (lr > 0.0) {
+    s->t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)s->t), c2 = 1.f - powf(b2, (float)s->t);
+    k_adam<<<(unsigned)((s->np + 255) / 256), 256, 0, c->stream>>>(s->p, s->m, s->v, s->g, s->np, (float)lr, b1,
+                                                                  b2, 1e-8f, c1, c2);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    VDS_TRY(refresh_bf16(c, s));
+  }
   return loss ? vds_sync_status(c) : VDS_OK;
 }
 

@@ -118,3 +118,11 @@ def dsm_batch(X: np.ndarray, batch: int, seed: int):
     idx = rng.integers(0, X.shape[0], batch)
     eps = rng.standard_normal((batch, X.shape[1])).astype(np.float32)
     return X[idx].astype(np.float32), eps
+
+
+def dsm_rows(n_pool: int, batch: int, D: int, seed: int):
+    """Row indices (batch, with replacement, int32) into a pool of n_pool
+    configurations and standard normal noise (batch x D, FP32)."""
+    rng = np.random.default_rng(seed)
+    return (rng.integers(0, n_pool, batch).astype(np.int32),
+            rng.standard_normal((batch, D)).astype(np.float32))

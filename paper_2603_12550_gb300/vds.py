@@ -98,8 +98,9 @@ _SIGS = {
     "vds_score_set_params": ([_vp, _vp, ctypes.POINTER(ctypes.c_float)], _i),
     "vds_score_get_params": ([_vp, _vp, ctypes.POINTER(ctypes.c_float)], _i),
     "vds_score_eval": ([_vp, _vp, _vp, _i, _vp], _i),
-    "vds_score_loss_grad": ([_vp, _vp, _vp, _vp, _i, _d, _dp, ctypes.POINTER(ctypes.c_float)], _i),
-    "vds_score_train": ([_vp, _vp, _vp, _vp, _i, _d, _d, _dp], _i),
+    "vds_score_loss_grad": ([_vp, _vp, _vp, _vp, _vp, _i, _d, _dp, ctypes.POINTER(ctypes.c_float)], _i),
+    "vds_score_train": ([_vp, _vp, _vp, _vp, _vp, _i, _d, _d, _dp], _i),
+    "vds_score_fit": ([_vp, _vp, _vp, _vp, _vp, _i, _d, _dp, ctypes.POINTER(ctypes.c_float)], _i),
     "pod_step_score": ([_vp, _vp, _vp, _vp, _i, _i, _pp, _i, _i, _i, _d, _dp, _ip], _i),
     "pod_brownian": ([_vp, _vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "pod_step": ([_vp, _vp, _vp, _i, _i, _pp, _i, _i, _i], _i),
@@ -341,18 +342,30 @@ class Score:
     def eval(self, x, out):
         _check(lib.vds_score_eval(self.ctx.h, self.h, _ptr(x), int(x.shape[0]), _ptr(out)))
 
-    def loss_grad(self, x, eps, sigma):
+    def loss_grad(self, x, eps, sigma, rows=None):
         loss = ctypes.c_double()
         g = np.empty(self.n, dtype=np.float32)
-        _check(lib.vds_score_loss_grad(self.ctx.h, self.h, _ptr(x), _ptr(eps), int(x.shape[0]), float(sigma),
+        M = int(eps.shape[0])
+        _check(lib.vds_score_loss_grad(self.ctx.h, self.h, _ptr(x), _ptr(rows), _ptr(eps), M, float(sigma),
                                        ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return loss.value, unflatten(g, self.D, self.width)
 
-    def train_step(self, x, eps, sigma, lr, want_loss=True):
+    def train_step(self, x, eps, sigma, lr, want_loss=True, rows=None):
         loss = ctypes.c_double()
-        _check(lib.vds_score_train(self.ctx.h, self.h, _ptr(x), _ptr(eps), int(x.shape[0]), float(sigma),
+        M = int(eps.shape[0])
+        _check(lib.vds_score_train(self.ctx.h, self.h, _ptr(x), _ptr(rows), _ptr(eps), M, float(sigma),
                                    float(lr), ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def fit_step(self, x, target, lr, rows=None, M=None, want_loss=True, want_grads=False):
+        loss = ctypes.c_double()
+        M = int(M if M is not None else (rows.shape[0] if rows is not None else x.shape[0]))
+        g = np.empty(self.n, dtype=np.float32) if want_grads else None
+        _check(lib.vds_score_fit(self.ctx.h, self.h, _ptr(x), _ptr(rows), _ptr(target), M, float(lr),
+                                 ctypes.byref(loss) if want_loss else None,
+                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grads else None))
+        out = loss.value if want_loss else None
+        return (out, unflatten(g, self.D, self.width)) if want_grads else out
 
     def free(self):
         if self.h:

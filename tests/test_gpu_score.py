@@ -96,3 +96,34 @@ def test_gpu_training_learns_the_gaussian_score(vds, ctx):
     net.eval(torch.from_numpy(z).cuda(), out)
     target = -z / (s0 ** 2 + sigma ** 2)
     assert _rel(out.cpu().numpy(), target) < 0.15
+
+
+def test_row_gather_equals_gathered_batch(vds, ctx):
+    # training batches drawn as rows of a device pool give the same loss and
+    # gradients as the gathered rows passed directly
+    layers = _layers(9)
+    net = vds.Score(ctx, 9, layers)
+    pool = np.random.default_rng(9).standard_normal((3000, 9)).astype(np.float32)
+    rows, eps = inputs.dsm_rows(3000, 256, 9, seed=1)
+    l1, g1 = net.loss_grad(torch.from_numpy(pool).cuda(), torch.from_numpy(eps).cuda(), 0.7,
+                           rows=torch.from_numpy(rows).cuda())
+    l2, g2 = net.loss_grad(torch.from_numpy(pool[rows]).cuda(), torch.from_numpy(eps).cuda(), 0.7)
+    assert l1 == l2
+    for (a, b), (c, d) in zip(g1, g2):
+        assert np.array_equal(a, c) and np.array_equal(b, d)
+
+
+def test_fit_gradients_match_oracle(vds, ctx):
+    layers = _layers(12)
+    net = vds.Score(ctx, 9, layers)
+    rng = np.random.default_rng(13)
+    pool = rng.standard_normal((2000, 9)).astype(np.float32)
+    tgt = (-0.6 * pool + 0.1 * rng.standard_normal(pool.shape)).astype(np.float32)
+    rows = rng.integers(0, 2000, 384).astype(np.int32)
+    loss, grads = net.fit_step(torch.from_numpy(pool).cuda(), torch.from_numpy(tgt).cuda(), 0.0,
+                               rows=torch.from_numpy(rows).cuda(), want_grads=True)
+    loss_o, grads_o = mlp.fit_grad(mlp.as64(layers), pool[rows], tgt[rows])
+    assert abs(loss - loss_o) <= 2e-2 * loss_o
+    for (gW, gb), (oW, ob) in zip(grads, grads_o):
+        assert _rel(gW, oW) <= 5e-2
+        assert _rel(gb, ob) <= 5e-2

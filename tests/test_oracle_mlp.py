@@ -92,3 +92,20 @@ def test_training_reaches_gaussian_score():
     s, _ = mlp.forward(layers, z)
     target = -z / (s0 ** 2 + sigma ** 2)
     assert np.linalg.norm(s - target) / np.linalg.norm(target) < 0.15
+
+
+def test_fit_gradient_matches_finite_differences():
+    layers = mlp.as64(inputs.mlp_init((4, 8, 8, 4), seed=2))
+    rng = np.random.default_rng(3)
+    x, t = rng.standard_normal((20, 4)), rng.standard_normal((20, 4))
+    loss, grads = mlp.fit_grad(layers, x, t)
+    s, _ = mlp.forward(layers, x)
+    assert loss == pytest.approx(np.mean(np.sum((s - t) ** 2, axis=1)), rel=1e-14)
+    for l in range(3):
+        idx = (1, 2)
+        up = [(W.copy(), b.copy()) for W, b in layers]
+        dn = [(W.copy(), b.copy()) for W, b in layers]
+        up[l][0][idx] += 1e-6
+        dn[l][0][idx] -= 1e-6
+        fd = (mlp.fit_grad(up, x, t)[0] - mlp.fit_grad(dn, x, t)[0]) / 2e-6
+        assert abs(fd - grads[l][0][idx]) <= 1e-6 * max(1.0, abs(fd))
