@@ -29,7 +29,7 @@ namespace {
 
 constexpr int GM = 128;   // rows per CTA tile
 constexpr int KC = 64;    // K per chunk
-constexpr int TMEM_COLS = 256;
+constexpr int TMEM_COLS = 128;
 
 // ------------------------------------------------------------ tcgen05 glue
 
@@ -98,30 +98,48 @@ struct Epi {
   const float *zin;        // pre-activation for DSILU (stride ldc)
 };
 
-// K-major canonical layout store of a rows x 64 chunk
-__device__ __forceinline__ void load_chunk(uint8_t *dst, const bf16 *__restrict__ src, int ld, int row0,
-                                           int nvalid, int rows_tile, int k0) {
+constexpr int GBN = 128;   // columns of C per CTA
+constexpr int GST = 4;     // pipeline stages (K chunks in flight)
+constexpr int GSTAGE = GM * KC * 2 + GBN * KC * 2;  // bytes per stage (A 16 KB + B <= 16 KB)
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Asynchronous copy of a rows_tile x 64 chunk (rows beyond nvalid zero-filled)
+// into the K-major canonical layout: byte offset of element (r, k) is
+// (r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2.  Consecutive lanes take
+// consecutive rows inside an 8-row group, so one warp writes 512 contiguous
+// bytes (no bank conflicts).
+__device__ __forceinline__ void load_chunk_async(uint32_t dst, const bf16 *__restrict__ src, int ld, int row0,
+                                                 int nvalid, int rows_tile, int k0) {
   for (int idx = threadIdx.x; idx < rows_tile * 8; idx += blockDim.x) {
-    const int r = idx >> 3, c = idx & 7;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (r < nvalid) v = *reinterpret_cast<const uint4 *>(src + (size_t)(row0 + r) * ld + k0 + c * 8);
-    *reinterpret_cast<uint4 *>(dst + (r >> 3) * 1024 + c * 128 + (r & 7) * 16) = v;
+    const int r8 = idx & 7, c = (idx >> 3) & 7, g = idx >> 6;
+    const int r = g * 8 + r8;
+    const bool ok = r < nvalid;
+    const bf16 *p = src + (size_t)(row0 + (ok ? r : 0)) * ld + k0 + c * 8;
+    cp_async16(dst + g * 1024 + c * 128 + r8 * 16, p, ok);
   }
 }
 
+// C tile [128 rows x BN cols] = A[m0:, K-split] . B[n0:n0+BN, K-split]^T
 __global__ void __launch_bounds__(128)
     k_gemm_tn(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int N, int Ksplit,
               Epi ep, int *err) {
   extern __shared__ __align__(1024) uint8_t gsm[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[GST];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * GM;
   const int kbase = blockIdx.y * Ksplit;
-  // shared memory: [A chunk 0: 16 KB][B chunk 0: 32 KB][A chunk 1][B chunk 1]
-  uint8_t *abuf[2] = {gsm, gsm + 16384 + 32768};
-  uint8_t *bbuf[2] = {gsm + 16384, gsm + 2 * 16384 + 32768};
-
+  const int n0 = blockIdx.z * GBN;
+  const int BN = min(GBN, N - n0);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(TMEM_COLS)
@@ -129,44 +147,55 @@ __global__ void __launch_bounds__(128)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int k = 0; k < GST; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = idesc_bf16(GM, N);
+  const uint32_t idesc = idesc_bf16(GM, BN);
   const int nch = Ksplit / KC;
   const int avalid = min(GM, ep.rows - m0);
-  bool ok = true;
-  for (int ch = 0; ch < nch && ok; ++ch) {
-    const int b = ch & 1;
-    if (ch >= 2) {
-      const bool got = mbar_wait_bounded(&bars[b], (uint32_t)(((ch - 2) >> 1) & 1), VDS_WAIT_LIMIT_NS);
-      if (__syncthreads_or(!got)) {
-        ok = false;
-        break;
-      }
+  const uint32_t sbase = smem_u32(gsm);
+  auto issue_loads = [&](int ch) {
+    if (ch < nch) {
+      const uint32_t st = sbase + (ch % GST) * GSTAGE;
+      load_chunk_async(st, A, lda, m0, avalid, GM, kbase + ch * KC);
+      load_chunk_async(st + GM * KC * 2, B, ldb, n0, BN, BN, kbase + ch * KC);
     }
-    load_chunk(abuf[b], A, lda, m0, avalid, GM, kbase + ch * KC);
-    load_chunk(bbuf[b], B, ldb, 0, N, N, kbase + ch * KC);
+    cp_async_commit();
+  };
+  for (int ch = 0; ch < GST - 1; ++ch) issue_loads(ch);
+  bool ok = true;
+  for (int ch = 0; ch < nch; ++ch) {
+    cp_async_wait<GST - 2>();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = smem_u32(abuf[b]), b0 = smem_u32(bbuf[b]);
+      const uint32_t a0 = sbase + (ch % GST) * GSTAGE, b0 = a0 + GM * KC * 2;
 #pragma unroll
-      for (int s = 0; s < KC / 16; ++s)
-        tc_mma(tmem, sdesc(a0 + s * 256), sdesc(b0 + s * 256), idesc, (ch > 0 || s > 0) ? 1 : 0);
-      tc_commit(&bars[b]);
+      for (int k = 0; k < KC / 16; ++k)
+        tc_mma(tmem, sdesc(a0 + k * 256), sdesc(b0 + k * 256), idesc, (ch > 0 || k > 0) ? 1 : 0);
+      tc_commit(&bars[ch % GST]);
     }
+    // the stage refilled next was read by the MMAs of chunk ch-1
+    if (ch >= 1 && ch + GST - 1 < nch) {
+      const int pc = ch - 1;
+      const bool got = mbar_wait_bounded(&bars[pc % GST], (uint32_t)((pc / GST) & 1), VDS_WAIT_LIMIT_NS);
+      if (__syncthreads_or(!got)) {
+        ok = false;
+        break;
+      }
+    }
+    issue_loads(ch + GST - 1);
   }
+  cp_async_wait<0>();
   if (ok && nch > 0) {
     const int last = nch - 1;
-    const bool got = mbar_wait_bounded(&bars[last & 1], (uint32_t)((last >> 1) & 1), VDS_WAIT_LIMIT_NS);
+    const bool got = mbar_wait_bounded(&bars[last % GST], (uint32_t)((last / GST) & 1), VDS_WAIT_LIMIT_NS);
     if (__syncthreads_or(!got)) ok = false;
   }
   tc_fence_after();
@@ -175,13 +204,13 @@ __global__ void __launch_bounds__(128)
   } else {
     const int row = m0 + warp * 32 + lane;
     const bool vrow = row < ep.rows;
-    for (int c0 = 0; c0 < N; c0 += 16) {
+    for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t v[16];
       tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (!vrow) continue;
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const int col = c0 + j;
+        const int col = n0 + c0 + j;
         if (col >= ep.ncols) continue;
         float a = __uint_as_float(v[j]);
         if (ep.mode == EPI_F32) {
@@ -209,7 +238,7 @@ __global__ void __launch_bounds__(128)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-constexpr size_t GEMM_SMEM = 2 * (16384 + 32768);
+constexpr size_t GEMM_SMEM = (size_t)GST * GSTAGE;
 
 // ------------------------------------------------------------ small kernels
 
@@ -298,10 +327,10 @@ __global__ void k_colsum(const float *__restrict__ X, int M, int n, int ld, floa
   const int col = blockIdx.x;
   double a = 0.0;
   for (int m = threadIdx.x; m < M; m += blockDim.x) a += X[(size_t)m * ld + col];
-  __shared__ double sh[256];
+  __shared__ double sh[512];
   sh[threadIdx.x] = a;
   __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
+  for (int o = 256; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
@@ -389,7 +418,7 @@ int gemm(vds_ctx *c, const bf16 *A, int lda, const bf16 *B, int ldb, int rows, i
     attr = true;
   }
   if (N % 16 != 0 || N < 16 || N > 256 || K % (KC * splits) != 0) return VDS_EARG;
-  dim3 grid((rows + GM - 1) / GM, splits);
+  dim3 grid((rows + GM - 1) / GM, splits, (N + GBN - 1) / GBN);
   k_gemm_tn<<<grid, 128, GEMM_SMEM, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
@@ -542,7 +571,7 @@ int loss_grad(vds_ctx *c, vds_score *s, const float *x, const int *rows, const f
     return VDS_OK;
   };
   auto bgrad = [&](const float *X, int n, int ld, float *dst) -> int {
-    k_colsum<<<n, 256, 0, c->stream>>>(X, M, n, ld, dst);
+    k_colsum<<<n, 512, 0, c->stream>>>(X, M, n, ld, dst);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
     return VDS_OK;

@@ -525,14 +525,24 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// one block per output: strided partial sums over the CTA partials, then a
+// fixed-order tree (deterministic)
 __global__ void k_project_reduce2(const double *__restrict__ part, int nblk, int n, double *__restrict__ pd,
                                   float *__restrict__ pf) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n) return;
+  __shared__ double sh[256];
+  const int o = blockIdx.x;
   double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * n + o];
-  if (pd) pd[o] = v;
-  if (pf) pf[o] = (float)v;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += part[(size_t)b * n + o];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (pd) pd[o] = sh[0];
+    if (pf) pf[o] = (float)sh[0];
+  }
 }
 
 __global__ void k_project_reduce(const double *__restrict__ part, int nblk, int n, float *__restrict__ p) {
@@ -600,7 +610,7 @@ int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D
   const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
   k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->gbuf.ptr);
   VDS_CUDA_TRY(cudaGetLastError());
-  k_project_reduce2<<<(n + 255) / 256, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, nblk, n, pd, pf);
+  k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, nblk, n, pd, pf);
   VDS_CUDA_TRY(cudaGetLastError());
   c->launches += 2;
   return VDS_OK;
@@ -857,7 +867,7 @@ int pod_project(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, fl
   if (st == VDS_OK) {
     const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
     k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->red.ptr);
-    k_project_reduce<<<(n + 255) / 256, 256, 0, c->stream>>>((const double *)c->red.ptr, nblk, n, p);
+    k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->red.ptr, nblk, n, nullptr, p);
     c->launches += 2;
     if (cudaGetLastError() != cudaSuccess) st = VDS_ECUDA;
   }

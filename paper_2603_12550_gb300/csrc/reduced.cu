@@ -176,19 +176,27 @@ __global__ void k_combine_xb(const double *__restrict__ G1, const double *__rest
   if (o < n) XB[o] = scale * (G1[o] + G2[o]);
 }
 
-// column means of an N x D matrix (one block per column, fixed order)
-__global__ void k_colmean(const float *__restrict__ s, int N, int D, double *__restrict__ mean) {
+// column means of an N x D matrix: CM_BLK blocks of partial sums per column,
+// then one block per column combining them in a fixed order
+constexpr int CM_BLK = 64;
+__global__ void k_colmean_part(const float *__restrict__ s, int N, int D, double *__restrict__ part) {
   __shared__ double sh[256];
-  const int col = blockIdx.x;
+  const int col = blockIdx.x, b = blockIdx.y;
   double a = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) a += (double)s[(size_t)i * D + col];
+  for (int i = b * 256 + threadIdx.x; i < N; i += 256 * CM_BLK) a += (double)s[(size_t)i * D + col];
   sh[threadIdx.x] = a;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) mean[col] = sh[0] / (double)N;
+  if (threadIdx.x == 0) part[col * CM_BLK + b] = sh[0];
+}
+__global__ void k_colmean(const double *__restrict__ part, int N, double *__restrict__ mean) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0;
+  for (int b = 0; b < CM_BLK; ++b) a += part[blockIdx.x * CM_BLK + b];
+  mean[blockIdx.x] = a / (double)N;
 }
 
 // particle velocity with the entropy gradient replaced by the surrogate
@@ -439,8 +447,9 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   const size_t nd = (size_t)N * D;
   VDS_TRY(vds_ensure(c, c->vecs, 4 * nd * sizeof(float)));
   float *qt = (float *)c->vecs.ptr, *sbuf = qt + nd, *Sx = sbuf + nd, *vel = Sx + nd;
-  VDS_TRY(vds_ensure(c, c->ubuf, (2 * 512 + 64) * sizeof(double)));
-  double *Pd = (double *)c->ubuf.ptr, *Pdot = Pd + 512, *smean = Pdot + 512, *errs = smean + 32;
+  VDS_TRY(vds_ensure(c, c->ubuf, (2 * 512 + 64 + 16 * CM_BLK) * sizeof(double)));
+  double *Pd = (double *)c->ubuf.ptr, *Pdot = Pd + 512, *smean = Pdot + 512, *errs = smean + 32,
+         *cpart = errs + 32;
   k_f2d<<<(n + 255) / 256, 256, 0, c->stream>>>(P, Pd, n);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
@@ -450,9 +459,10 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   for (int step = 0; step < nsteps; ++step) {
     VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
     VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
-    k_colmean<<<D, 256, 0, c->stream>>>(sbuf, N, D, smean);
+    k_colmean_part<<<dim3(D, CM_BLK), 256, 0, c->stream>>>(sbuf, N, D, cpart);
+    k_colmean<<<D, 32, 0, c->stream>>>(cpart, N, smean);
     VDS_CUDA_TRY(cudaGetLastError());
-    ++c->launches;
+    c->launches += 2;
     bool exact = false;
     if (check_every > 0 && step % check_every == 0) {
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
