@@ -25,7 +25,8 @@ namespace {
 constexpr size_t kHeadBytes = 8192;  // err | tickets | scalars | reduction slots
 constexpr size_t kErrOff = 0, kTicketOff = 256, kScalOff = 512, kRedOff = 512 + SC_COUNT * 8;
 constexpr int kMaxDP = 20;           // Rec<16>::DP
-constexpr size_t kRecBytes = (size_t)((VDS_NOALLOC_MAX_N + 127) / 128 * 128) * kMaxDP * sizeof(float);
+constexpr size_t kRecBytes =
+    (size_t)((VDS_NOALLOC_MAX_N + vds_pair::TJ - 1) / vds_pair::TJ * vds_pair::TJ) * kMaxDP * sizeof(float);
 constexpr size_t kPartBytes = (size_t)4 << 20;
 constexpr size_t kScratchBytes = kHeadBytes + kRecBytes + kPartBytes;
 static_assert(kRedOff + (VDS_NOALLOC_MAX_N / 256 + 1) * 4 * 8 <= kHeadBytes, "head layout");

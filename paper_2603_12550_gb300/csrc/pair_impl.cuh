@@ -20,14 +20,32 @@
 
 namespace vds_pair {
 
-constexpr int NT_PAIR = 128;   // threads per CTA
-constexpr int TJ = 128;        // records per j-tile (= j-chunk)
-constexpr int NSTAGE = 3;      // shared-memory ring depth
+// Tile shape (overridable at build time for tuning sweeps).
+#ifndef VDS_PAIR_NT
+#define VDS_PAIR_NT 256
+#endif
+#ifndef VDS_PAIR_TJ
+#define VDS_PAIR_TJ 256
+#endif
+#ifndef VDS_PAIR_NSTAGE
+#define VDS_PAIR_NSTAGE 3
+#endif
+#ifndef VDS_PAIR_RI_DENS
+#define VDS_PAIR_RI_DENS 4
+#endif
+#ifndef VDS_PAIR_RI_GRAD_LARGE_D
+#define VDS_PAIR_RI_GRAD_LARGE_D 4
+#endif
+constexpr int NT_PAIR = VDS_PAIR_NT;     // threads per CTA
+constexpr int TJ = VDS_PAIR_TJ;          // records per j-tile (= j-chunk)
+constexpr int NSTAGE = VDS_PAIR_NSTAGE;  // shared-memory ring depth
 
 template <int D>
 struct PairCfg {
-  static constexpr int RI_DENS = 4;
-  static constexpr int RI_GRAD = (D <= 6) ? 4 : 2;
+  static constexpr int RI_DENS = VDS_PAIR_RI_DENS;
+  // (chosen by a sweep on GB300 at N=65536, D=9; large D keeps 2 to stay
+  // within 255 registers)
+  static constexpr int RI_GRAD = (D <= 6) ? 4 : (D <= 9 ? VDS_PAIR_RI_GRAD_LARGE_D : 2);
 };
 
 // ------------------------------------------------------------- pair kernel
