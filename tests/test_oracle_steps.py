@@ -157,3 +157,14 @@ def test_dumbbell_shear_moments_near_oldroyd_b(orc):
     exact = np.array([[1 + 2 * (lam * gdot) ** 2, lam * gdot, 0], [lam * gdot, 1, 0], [0, 0, 1]])
     assert np.all(np.abs(qq - exact) <= 0.2 * np.abs(exact) + 0.01), qq
     assert np.all(qq[[0, 0, 1, 2], [0, 1, 1, 2]] < exact[[0, 0, 1, 2], [0, 1, 1, 2]])
+
+
+def test_dumbbell_moment_equation_reaches_oldroyd_b():
+    # the steady state of the exact moment equation is the Oldroyd-B closed
+    # form (lambda = zeta / 4H = 1), and at t = 0 it is the equilibrium start
+    from closed_forms import dumbbell_cov_exact
+    for rate in (0.1, 1.0, 10.0):
+        C = dumbbell_cov_exact(rate, 200.0)
+        ex = np.array([[1 + 2 * rate ** 2, rate, 0], [rate, 1, 0], [0, 0, 1]])
+        np.testing.assert_allclose(C, ex, rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(dumbbell_cov_exact(rate, 0.0), np.eye(3), atol=1e-15)
