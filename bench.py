@@ -228,15 +228,22 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
         ctx.vds_step(q, pe, 5)
     torch.cuda.synchronize()
     snap_s = time.perf_counter() - t0
+    ctx.vds_timing(True)
     sec, (basis, r) = timed(lambda: ctx.pod_build(X, N * s, S * nb, s, energy=0.9999, r_max=64, kappa=kap))
+    ph_ms, _, _ = ctx.vds_timing_read()
     P = torch.empty((r, nb), device="cuda")
     ctx.pod_project(basis, q, P)
     ctx.pod_step(basis, P, N, D, pe, nsteps=60, refresh_every=60, mode=2)
+    ctx.vds_timing(True)
     sec2, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=240, refresh_every=60, mode=2))
+    rf_ms, rf_n, _ = ctx.vds_timing_read()
+    ctx.vds_timing(False)
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
     out["pod"] = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
+                  "build_phases_ms": {"gram": ph_ms[4], "eigensolve": ph_ms[5], "basis": ph_ms[6]},
                   "eigenvalues_top": basis.eigenvalues()[:8].tolist(),
                   "mode2_steps_per_s": 240 / sec2, "mode2_refresh_every": 60,
+                  "mode2_refresh_ms": rf_ms[3] / max(1, rf_n[3]), "mode2_refreshes": rf_n[3],
                   "mode1_galerkin_steps_per_s": 3 / sec3, "snapshot_run_s": snap_s}
     del X
     basis.free()
@@ -252,6 +259,7 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
     kaps = np.stack([inputs.shear_kappa(bs, r_) for r_ in rates])
     pb = vds.params(bnb, bs, kBT=1.0, zeta=4.0, dt=0.005, scheme=1, tol=1e-6, jfloor=1e-9)
     batch = vds.Batch(ctx, sizes, bnb * bs, pb, hs, kaps)
+    cfg, cfg_ms = batch.autotune(q_all0, reps=2)
     q_all = q_all0.clone()
     batch.step(q_all, 1)
     q_all = q_all0.clone()
@@ -281,6 +289,8 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
                       "speedup": sec_p / sec_b,
                       "mean_gradient_evaluations": float(np.mean(its_b)),
                       "stress_rel_diff_batched_vs_per_ensemble": dev,
+                      "autotune": {"config": cfg, "tile": batch.info()["tile"],
+                                   "pair_passes_ms_per_config": cfg_ms},
                       "note": "one step advances all 512 ensembles by dt (implicit, tol 1e-6)"}
     batch.free()
     return out
@@ -301,11 +311,12 @@ def _extras_surrogate(ctx, vds, inputs, torch, wl, h):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, r
 
+    # training snapshots span the run's horizon (t in [0, 1], every 10 steps)
     pool = []
     for k, rate in enumerate((0.5, 1.0, 2.0)):
         q = torch.from_numpy(inputs.equilibrium_cloud(N, nb, s, H=wl["H"], seed=100 + k)).cuda()
         p = vds.params(nb, s, H=wl["H"], h=h, dt=wl["dt"], kappa=inputs.shear_kappa(s, rate))
-        for _ in range(7):
+        for _ in range(21):
             pool.append(q.clone())
             ctx.vds_step(q, p, 10)
     pool = torch.cat(pool)

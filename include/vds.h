@@ -152,13 +152,17 @@ VDS_API int vds_energy_grad_noalloc(const float *q, int N, int D, const vds_para
 
 /* Instrumentation (no counterpart in the paper; used to report a kernel's
  * achieved rate).  vds_timing(ctx, 1) clears the counters and starts
- * recording the device duration of every pair-pass launch on the context
- * stream (CUDA events around the launch); vds_timing(ctx, 0) stops.  The
+ * recording the device duration of every pair-pass launch and POD phase on
+ * the context stream (CUDA events around it); vds_timing(ctx, 0) stops.  The
  * library's total kernel-launch count is cleared by either call.
- * vds_timing_read synchronises and returns, per pass kind (0 density,
- * 1 gradient, 2 bandwidth, 3 POD refresh), the summed milliseconds ms[4] and
- * launch counts launches[4] (host arrays, may be NULL), and the number of
- * kernels launched since the last vds_timing call. */
+ * vds_timing_read synchronises and returns, per kind, the summed milliseconds
+ * ms[VDS_TIMING_KINDS] and event-pair counts launches[VDS_TIMING_KINDS] (host
+ * arrays of that length, may be NULL), and the number of kernels launched
+ * since the last vds_timing call.  Kinds: 0 density pass, 1 gradient pass,
+ * 2 bandwidth selection, 3 POD refresh pass (X^B), 4 POD Gram X^T X, 5 POD
+ * eigensolve (Jacobi sweeps, sort and rank rule), 6 POD basis (Phi, Cholesky-QR,
+ * sign fix, X^H). */
+#define VDS_TIMING_KINDS 7
 VDS_API int vds_timing(vds_ctx *ctx, int enable);
 VDS_API int vds_timing_read(vds_ctx *ctx, double *ms, long *launches, long *total_launches);
 

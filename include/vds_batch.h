@@ -56,6 +56,28 @@ VDS_API int vds_batch_energy_grad(vds_ctx *ctx, vds_batch *b, const float *q_all
  * and step; status of the first failing ensemble is returned. */
 VDS_API int vds_batch_step(vds_ctx *ctx, vds_batch *b, float *q_all, int nsteps, int *iters_out);
 
+/* Tile autotuner (no counterpart in the paper).  The batched pair kernel has
+ * VDS_BATCH_CONFIGS candidate shapes: config k runs 128 << (k >> 1) threads
+ * per CTA with 2 << (k & 1) particles per thread, so a work item's i-tile is
+ * 256, 512, 512 or 1024 particles.  The j-tiles and the order of every sum
+ * are the same in all of them, so results are bit-identical across configs;
+ * only the queue (its items follow the tile) and the speed change.  A batch
+ * starts in config 1 for D <= 6 and config 0 otherwise.
+ *
+ * vds_batch_autotune times one density and one gradient pass of every
+ * candidate on the batch's particles q_all (device, total x D; reps >= 1
+ * timed repetitions each, the fastest kept), selects the fastest candidate,
+ * rebuilds the work queue for its tile and returns its index in config
+ * (host, may be NULL) and each candidate's milliseconds in ms (host,
+ * VDS_BATCH_CONFIGS doubles, may be NULL).  Synchronises.
+ * vds_batch_set_config selects a candidate directly; vds_batch_get_config
+ * reads the current one.  Either invalidates the captured implicit round. */
+#define VDS_BATCH_CONFIGS 4
+VDS_API int vds_batch_autotune(vds_ctx *ctx, vds_batch *b, const float *q_all, int reps, int *config,
+                               double *ms);
+VDS_API int vds_batch_set_config(vds_ctx *ctx, vds_batch *b, int config);
+VDS_API int vds_batch_get_config(const vds_batch *b, int *config);
+
 #ifdef __cplusplus
 }
 #endif

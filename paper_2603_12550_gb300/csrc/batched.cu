@@ -28,15 +28,17 @@
 
 namespace {
 
-constexpr int BNT = 128;  // threads per pair CTA
 constexpr int BTJ = 128;  // records per j-tile
 constexpr int BNS = 3;    // ring stages
 constexpr int RNT = 256;  // threads of the per-ensemble reduction
 
-template <int D>
-struct BCfg {
-  static constexpr int RI = (D <= 6) ? 4 : 2;
-};
+// Candidate pair-kernel shapes of the tile autotuner (vds_batch_autotune):
+// threads per CTA and particles per thread; the i-tile of a work item is
+// their product.  j-tiles and summation order are the same in every shape.
+constexpr int kCfgNT[VDS_BATCH_CONFIGS] = {128, 128, 256, 256};
+constexpr int kCfgRI[VDS_BATCH_CONFIGS] = {2, 4, 2, 4};
+constexpr int kMinTile = 256;  // smallest i-tile over the candidates
+inline int default_config(int D) { return D <= 6 ? 1 : 0; }
 
 struct EParam {
   float c;
@@ -60,13 +62,13 @@ struct BState {
 
 // ------------------------------------------------------------ pair kernel
 
-template <int D, int RI, bool GRAD>
+template <int D, int RI, int NT, bool GRAD>
 __device__ __forceinline__ bool bitem(float *tiles, uint64_t *full, const float *__restrict__ recE, int Ne,
                                       int t, long long gtile, double *__restrict__ outE) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
   constexpr int TILE = BTJ * DP;
-  constexpr int TI = BNT * RI;
+  constexpr int TI = NT * RI;
   const int tid = threadIdx.x;
   const int ntile = (Ne + BTJ - 1) / BTJ;
   if (tid == 0) {
@@ -80,7 +82,7 @@ __device__ __forceinline__ bool bitem(float *tiles, uint64_t *full, const float 
   float xi[RI][D], wi[RI], sum[RI][ACC], cmp[RI][ACC];
 #pragma unroll
   for (int k = 0; k < RI; ++k) {
-    int i = t * TI + tid + k * BNT;
+    int i = t * TI + tid + k * NT;
     i = i < Ne ? i : Ne - 1;
     const float *r = recE + (size_t)i * DP;
 #pragma unroll
@@ -158,7 +160,7 @@ __device__ __forceinline__ bool bitem(float *tiles, uint64_t *full, const float 
   }
 #pragma unroll
   for (int k = 0; k < RI; ++k) {
-    const int i = t * TI + tid + k * BNT;
+    const int i = t * TI + tid + k * NT;
     if (i < Ne)
 #pragma unroll
       for (int a = 0; a < ACC; ++a) outE[(size_t)i * D + a] = (double)sum[k][a] - (double)cmp[k][a];
@@ -168,8 +170,8 @@ __device__ __forceinline__ bool bitem(float *tiles, uint64_t *full, const float 
 
 // mode 0: density for every item; 1: gradient for every item; 2: by the
 // ensemble's minimiser state (trial -> density, direction -> gradient).
-template <int D, int RI>
-__global__ void __launch_bounds__(BNT)
+template <int D, int RI, int NT>
+__global__ void __launch_bounds__(NT)
     k_bpair(const float *__restrict__ rec, const long long *__restrict__ off, const int *__restrict__ sizes,
             const int2 *__restrict__ queue, int nitems, unsigned *counter, int mode,
             const BState *__restrict__ st, double *__restrict__ acc_out, int *err) {
@@ -201,8 +203,8 @@ __global__ void __launch_bounds__(BNT)
     }
     const int Ne = sizes[e];
     const long long base = off[e];
-    const bool ok = grad ? bitem<D, RI, true>(tiles, full, rec + base * DP, Ne, t, gtile, acc_out + base * D)
-                         : bitem<D, RI, false>(tiles, full, rec + base * DP, Ne, t, gtile, acc_out + base * D);
+    const bool ok = grad ? bitem<D, RI, NT, true>(tiles, full, rec + base * DP, Ne, t, gtile, acc_out + base * D)
+                         : bitem<D, RI, NT, false>(tiles, full, rec + base * DP, Ne, t, gtile, acc_out + base * D);
     if (!ok) {
       if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
       return;
@@ -559,7 +561,7 @@ __global__ void k_binit(int E, BState *st) {
 // ------------------------------------------------------------------ host
 
 struct vds_batch {
-  int device = 0, E = 0, D = 0, tile = 0, nitems = 0, grid = 0, scheme = 0;
+  int device = 0, E = 0, D = 0, tile = 0, nitems = 0, grid = 0, scheme = 0, cfg = 0, max_items = 0;
   long total = 0;
   BCommon cm;
   std::vector<int> sizes;
@@ -582,14 +584,24 @@ struct vds_batch {
 
 namespace {
 
+template <int D, int RI, int NT>
+int b_launch_cfg(vds_ctx *c, vds_batch *b, int mode) {
+  k_bpair<D, RI, NT><<<b->grid, NT, b->smem, c->stream>>>(b->rec, b->d_off, b->d_sizes, b->d_queue, b->nitems,
+                                                           b->d_counter, mode, b->d_st, b->acc, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  return VDS_OK;
+}
+
 template <int D>
 int b_launch_pair(vds_ctx *c, vds_batch *b, int mode) {
-  constexpr int RI = BCfg<D>::RI;
   VDS_CUDA_TRY(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), c->stream));
   VDS_TRY(vds_time_begin(c, mode == 1 ? PK_GRADIENT : PK_DENSITY));
-  k_bpair<D, RI><<<b->grid, BNT, b->smem, c->stream>>>(b->rec, b->d_off, b->d_sizes, b->d_queue, b->nitems,
-                                                       b->d_counter, mode, b->d_st, b->acc, c->err);
-  VDS_CUDA_TRY(cudaGetLastError());
+  switch (b->cfg) {
+    case 0: VDS_TRY((b_launch_cfg<D, kCfgRI[0], kCfgNT[0]>(c, b, mode))); break;
+    case 1: VDS_TRY((b_launch_cfg<D, kCfgRI[1], kCfgNT[1]>(c, b, mode))); break;
+    case 2: VDS_TRY((b_launch_cfg<D, kCfgRI[2], kCfgNT[2]>(c, b, mode))); break;
+    default: VDS_TRY((b_launch_cfg<D, kCfgRI[3], kCfgNT[3]>(c, b, mode))); break;
+  }
   VDS_TRY(vds_time_end(c, mode == 1 ? PK_GRADIENT : PK_DENSITY));
   ++c->launches;
   return VDS_OK;
@@ -622,15 +634,89 @@ int b_reduce(vds_ctx *c, vds_batch *b, int mode) {
   return VDS_OK;
 }
 
+#define VDS_BATCH_D(D, CALL)     \
+  switch (D) {                   \
+    case 2: return CALL(2);      \
+    case 3: return CALL(3);      \
+    case 4: return CALL(4);      \
+    case 6: return CALL(6);      \
+    case 8: return CALL(8);      \
+    case 9: return CALL(9);      \
+    case 12: return CALL(12);    \
+    default: return VDS_EARG;    \
+  }
+
+template <int D, int RI, int NT>
+int b_setup_cfg(vds_ctx *c, vds_batch *b) {
+  b->tile = NT * RI;
+  b->smem = (size_t)BNS * BTJ * Rec<D>::DP * sizeof(float);
+  VDS_CUDA_TRY(cudaFuncSetAttribute(k_bpair<D, RI, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+  int occ = 0;
+  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpair<D, RI, NT>, NT, b->smem));
+  b->grid = c->num_sms * (occ > 0 ? occ : 1);
+  return VDS_OK;
+}
+
+// Select pair-kernel shape b->cfg: i-tile, shared memory, grid (resident CTAs
+// on every SM, at most one per work item) and the work queue for that tile.
 template <int D>
 int b_setup_kernel(vds_ctx *c, vds_batch *b) {
-  constexpr int RI = BCfg<D>::RI;
-  b->tile = BNT * RI;
-  b->smem = (size_t)BNS * BTJ * Rec<D>::DP * sizeof(float);
-  VDS_CUDA_TRY(cudaFuncSetAttribute(k_bpair<D, RI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
-  int occ = 0;
-  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bpair<D, RI>, BNT, b->smem));
-  b->grid = c->num_sms * (occ > 0 ? occ : 1);
+  switch (b->cfg) {
+    case 0: VDS_TRY((b_setup_cfg<D, kCfgRI[0], kCfgNT[0]>(c, b))); break;
+    case 1: VDS_TRY((b_setup_cfg<D, kCfgRI[1], kCfgNT[1]>(c, b))); break;
+    case 2: VDS_TRY((b_setup_cfg<D, kCfgRI[2], kCfgNT[2]>(c, b))); break;
+    default: VDS_TRY((b_setup_cfg<D, kCfgRI[3], kCfgNT[3]>(c, b))); break;
+  }
+  return VDS_OK;
+}
+
+// Work queue in longest-processing-time order for the current tile: cost N_e
+// descending, then ensemble, then tile ascending.
+void b_build_queue(vds_batch *b) {
+  struct It {
+    int n, e, t;
+  };
+  std::vector<It> its;
+  for (int e = 0; e < b->E; ++e)
+    for (int t = 0; t < (b->sizes[e] + b->tile - 1) / b->tile; ++t) its.push_back({b->sizes[e], e, t});
+  std::sort(its.begin(), its.end(), [](const It &a, const It &bb) {
+    if (a.n != bb.n) return a.n > bb.n;
+    if (a.e != bb.e) return a.e < bb.e;
+    return a.t < bb.t;
+  });
+  b->nitems = (int)its.size();
+  b->items.resize(2 * its.size());
+  for (size_t k = 0; k < its.size(); ++k) {
+    b->items[2 * k] = its[k].e;
+    b->items[2 * k + 1] = its[k].t;
+  }
+  if (b->grid > b->nitems) b->grid = b->nitems;
+}
+
+void b_drop_graph(vds_batch *b) {
+  if (b->round_exec) cudaGraphExecDestroy(b->round_exec);
+  if (b->round_graph) cudaGraphDestroy(b->round_graph);
+  b->round_exec = nullptr;
+  b->round_graph = nullptr;
+  b->graph_stream = nullptr;
+  b->graph_q = nullptr;
+}
+
+// Switch to shape cfg: kernel setup, queue, upload; the round graph is
+// captured again at the next implicit step.
+int b_apply_config(vds_ctx *c, vds_batch *b, int cfg) {
+  b->cfg = cfg;
+  int st;
+#define SETUP(DD) b_setup_kernel<DD>(c, b)
+  st = [&]() -> int { VDS_BATCH_D(b->D, SETUP) }();
+#undef SETUP
+  VDS_TRY(st);
+  b_build_queue(b);
+  if (b->nitems > b->max_items) return VDS_EARG;
+  VDS_CUDA_TRY(cudaMemcpyAsync(b->d_queue, b->items.data(), sizeof(int2) * b->nitems, cudaMemcpyHostToDevice,
+                               c->stream));
+  VDS_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  b_drop_graph(b);
   return VDS_OK;
 }
 
@@ -737,17 +823,49 @@ int b_step(vds_ctx *c, vds_batch *b, float *q, int nsteps, int *iters_out, int s
   return VDS_OK;
 }
 
-#define VDS_BATCH_D(D, CALL)     \
-  switch (D) {                   \
-    case 2: return CALL(2);      \
-    case 3: return CALL(3);      \
-    case 4: return CALL(4);      \
-    case 6: return CALL(6);      \
-    case 8: return CALL(8);      \
-    case 9: return CALL(9);      \
-    case 12: return CALL(12);    \
-    default: return VDS_EARG;    \
+template <int D>
+int b_autotune(vds_ctx *c, vds_batch *b, const float *q, int reps, int *best_cfg, double *ms_out) {
+  // records of q with w = 1/rho, from one density pass in the current shape
+  VDS_TRY(b_prep<D>(c, b, 0, (float *)q));
+  VDS_TRY(b_launch_pair<D>(c, b, 0));
+  VDS_TRY(b_fin<D>(c, b, 0, 0, (float *)q, nullptr));
+  VDS_TRY(vds_sync_status(c));
+  struct Ev {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Ev() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  VDS_CUDA_TRY(cudaEventCreate(&ev.e[0]));
+  VDS_CUDA_TRY(cudaEventCreate(&ev.e[1]));
+  double best = 1e300;
+  int bi = b->cfg;
+  for (int k = 0; k < VDS_BATCH_CONFIGS; ++k) {
+    VDS_TRY(b_apply_config(c, b, k));
+    VDS_TRY(b_launch_pair<D>(c, b, 0));  // warm-up
+    VDS_TRY(b_launch_pair<D>(c, b, 1));
+    double tmin = 1e300;
+    for (int r = 0; r < reps; ++r) {
+      VDS_CUDA_TRY(cudaEventRecord(ev.e[0], c->stream));
+      VDS_TRY(b_launch_pair<D>(c, b, 0));
+      VDS_TRY(b_launch_pair<D>(c, b, 1));
+      VDS_CUDA_TRY(cudaEventRecord(ev.e[1], c->stream));
+      VDS_TRY(vds_sync_status(c));
+      float ms = 0.f;
+      VDS_CUDA_TRY(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
+      if (ms < tmin) tmin = ms;
+    }
+    if (ms_out) ms_out[k] = tmin;
+    if (tmin < best) {
+      best = tmin;
+      bi = k;
+    }
   }
+  VDS_TRY(b_apply_config(c, b, bi));
+  if (best_cfg) *best_cfg = bi;
+  return VDS_OK;
+}
 
 struct Dev {
   int prev = -1, dev;
@@ -767,8 +885,7 @@ extern "C" {
 void vds_batch_free(vds_batch *b) {
   if (!b) return;
   Dev dg(b->device);
-  if (b->round_exec) cudaGraphExecDestroy(b->round_exec);
-  if (b->round_graph) cudaGraphDestroy(b->round_graph);
+  b_drop_graph(b);
   void *ptrs[] = {b->d_off, b->d_sizes, b->d_ens, b->d_active, b->d_queue, b->d_counter, b->d_ep, b->d_st,
                   b->rec, b->qs, b->dA, b->dB, b->dir, b->acc, b->contrib, b->eout};
   for (void *p : ptrs)
@@ -812,33 +929,8 @@ int vds_batch_create(vds_ctx *c, int E, const int *sizes, int D, const vds_param
     tot += sizes[e];
   }
   b->total = tot;
-  int st;
-#define SETUP(DD) b_setup_kernel<DD>(c, b)
-  st = [&]() -> int { VDS_BATCH_D(D, SETUP) }();
-#undef SETUP
-  if (st != VDS_OK) {
-    vds_batch_free(b);
-    return st;
-  }
-  // work queue in longest-processing-time order
-  struct It {
-    int n, e, t;
-  };
-  std::vector<It> its;
-  for (int e = 0; e < E; ++e)
-    for (int t = 0; t < (sizes[e] + b->tile - 1) / b->tile; ++t) its.push_back({sizes[e], e, t});
-  std::sort(its.begin(), its.end(), [](const It &a, const It &bb) {
-    if (a.n != bb.n) return a.n > bb.n;
-    if (a.e != bb.e) return a.e < bb.e;
-    return a.t < bb.t;
-  });
-  b->nitems = (int)its.size();
-  b->items.resize(2 * its.size());
-  for (size_t k = 0; k < its.size(); ++k) {
-    b->items[2 * k] = its[k].e;
-    b->items[2 * k + 1] = its[k].t;
-  }
-  if (b->grid > b->nitems) b->grid = b->nitems;
+  b->max_items = 0;
+  for (int e = 0; e < E; ++e) b->max_items += (sizes[e] + kMinTile - 1) / kMinTile;
   std::vector<int> ens(tot);
   for (int e = 0; e < E; ++e)
     for (int k = 0; k < sizes[e]; ++k) ens[b->off[e] + k] = e;
@@ -862,7 +954,7 @@ int vds_batch_create(vds_ctx *c, int E, const int *sizes, int D, const vds_param
   A((void **)&b->d_sizes, sizeof(int) * E);
   A((void **)&b->d_ens, sizeof(int) * tot);
   A((void **)&b->d_active, sizeof(int));
-  A((void **)&b->d_queue, sizeof(int2) * b->nitems);
+  A((void **)&b->d_queue, sizeof(int2) * b->max_items);
   A((void **)&b->d_counter, sizeof(unsigned));
   A((void **)&b->d_ep, sizeof(EParam) * E);
   A((void **)&b->d_st, sizeof(BState) * E);
@@ -878,13 +970,16 @@ int vds_batch_create(vds_ctx *c, int E, const int *sizes, int D, const vds_param
   if (ce == cudaSuccess) ce = cudaMemcpy(b->d_off, b->off.data(), sizeof(long long) * E, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(b->d_sizes, sizes, sizeof(int) * E, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(b->d_ens, ens.data(), sizeof(int) * tot, cudaMemcpyHostToDevice);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpy(b->d_queue, b->items.data(), sizeof(int2) * b->nitems, cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemcpy(b->d_ep, ep.data(), sizeof(EParam) * E, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {
     vds_last_cuda_error(ce);
     vds_batch_free(b);
     return ce == cudaErrorMemoryAllocation ? VDS_ENOMEM : VDS_ECUDA;
+  }
+  const int st = b_apply_config(c, b, default_config(D));
+  if (st != VDS_OK) {
+    vds_batch_free(b);
+    return st;
   }
   *out = b;
   return VDS_OK;
@@ -902,6 +997,26 @@ int vds_batch_queue(const vds_batch *b, int *items, int n_items) {
   if (!b || !items || n_items < b->nitems) return VDS_EARG;
   memcpy(items, b->items.data(), sizeof(int) * 2 * b->nitems);
   return VDS_OK;
+}
+
+int vds_batch_set_config(vds_ctx *c, vds_batch *b, int config) {
+  if (!c || !b || config < 0 || config >= VDS_BATCH_CONFIGS || b->device != c->device) return VDS_EARG;
+  Dev dg(c->device);
+  return b_apply_config(c, b, config);
+}
+
+int vds_batch_get_config(const vds_batch *b, int *config) {
+  if (!b || !config) return VDS_EARG;
+  *config = b->cfg;
+  return VDS_OK;
+}
+
+int vds_batch_autotune(vds_ctx *c, vds_batch *b, const float *q, int reps, int *config, double *ms) {
+  if (!c || !b || !q || reps < 1 || b->device != c->device) return VDS_EARG;
+  Dev dg(c->device);
+#define CALL(DD) b_autotune<DD>(c, b, q, reps, config, ms)
+  VDS_BATCH_D(b->D, CALL)
+#undef CALL
 }
 
 int vds_batch_energy_grad(vds_ctx *c, vds_batch *b, const float *q, double *E, float *g, float *rho) {

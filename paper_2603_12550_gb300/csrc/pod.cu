@@ -672,10 +672,13 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   order = (int *)tb.p[3];
 
   // 1. Gram
+  VDS_TRY(vds_time_begin(c, PK_GRAM));
   k_gram_x<<<dim3(nbt * nbt, nks), 256, 0, c->stream>>>(X, Ns, M, nbt, kchunk, gpart);
   VDS_CUDA_TRY(cudaGetLastError());
   k_gram_reduce<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(gpart, M, nbt, nks, A0);
   VDS_CUDA_TRY(cudaGetLastError());
+  VDS_TRY(vds_time_end(c, PK_GRAM));
+  VDS_TRY(vds_time_begin(c, PK_EIGEN));
   k_identity<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(V0, M);
   VDS_CUDA_TRY(cudaGetLastError());
   c->launches += 3;
@@ -716,6 +719,7 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   k_eig_sort<<<1, 1024, 0, c->stream>>>(A0, V0, M, energy, r_max, r_fixed, lam_s, order, W, c->scal);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
+  VDS_TRY(vds_time_end(c, PK_EIGEN));
   VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
   VDS_TRY(vds_sync_status(c));
@@ -744,6 +748,7 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
       break;
     }
     // 4. basis
+    if ((st = vds_time_begin(c, PK_BASIS)) != VDS_OK) break;
     k_basis<<<dim3((unsigned)((Ns + 255) / 256), (ld + BT - 1) / BT), 256, 0, c->stream>>>(X, Ns, M, W, r,
                                                                                          ld, b->phi);
     if (cudaGetLastError() != cudaSuccess) {
@@ -803,6 +808,7 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
     }
     ++c->launches;
     if ((st = tsgram(c, b->phi, (const float *)tb.p[6], Ns, ld, r, tpart, nblk, rchunk, G)) != VDS_OK) break;
+    if ((st = vds_time_end(c, PK_BASIS)) != VDS_OK) break;
     if (cudaMemcpyAsync(b->xh, G, sizeof(double) * r * r, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaMemcpyAsync(b->lam, lam_s, sizeof(double) * M, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
       st = VDS_ECUDA;

@@ -17,5 +17,8 @@ struct pod_basis {
 int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *G);
 // P = Phi^T q (r x nb) into pd (FP64, may be NULL) and/or pf (FP32, may be NULL).
 int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf);
+// U1, U2 (Ns x ld, FP32) of the X^B refresh at the records in ctx->rec
+// (refresh.cu); time kind PK_REFRESH.
+int pod_refresh_dev(vds_ctx *c, const pod_basis *b, int N, int D, float *U1, float *U2);
 // q = Phi P from FP32 P (r x nb).
 int pod_lift_dev(vds_ctx *c, const pod_basis *b, const float *p, int N, int D, float *q);

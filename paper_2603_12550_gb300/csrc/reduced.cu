@@ -8,14 +8,10 @@
 //   with X^B1, X^B2 rebuilt every `refresh_every` steps at the lifted state
 //   ("mapping back and forth", Sec. 2.4, Sec. 3.2) and frozen in between.
 //
-// The refresh is a pair pass over the lifted particles that accumulates, for
-// each particle I and basis column t (RT columns per CTA),
-//   W1_(Ia)t = sum_K Z_IK Phi_(Ka)t,  W2_(Ia)t = sum_K Z_IK Phi_(Ka)t / rho_K,
-//   c_I = sum_K Z_IK / rho_K,
-// and writes U1 = Phi - W1 / rho_I and U2 = c Phi - W2, so that
-//   X^B1 = -(1/h^2) Phi^T U1,  X^B2 = -(1/h^2) Phi^T U2
-// (the row sum of Z is rho_I).  Both contractions are FP64-accumulated
-// tall-skinny Grams.
+// The refresh is a pair pass over the lifted particles (refresh.cu) that
+// writes U1 = Phi - W1 / rho_I and U2 = c Phi - W2 per particle, so that
+//   X^B1 = -(1/h^2) Phi^T U1,  X^B2 = -(1/h^2) Phi^T U2;
+// both contractions are FP64-accumulated tall-skinny Grams.
 #include <math.h>
 
 #include "../../include/vds_score.h"
@@ -23,89 +19,6 @@
 #include "pod_internal.cuh"
 
 namespace {
-
-constexpr int RF_NT = 128;  // threads (particles) per CTA
-constexpr int RF_TJ = 64;   // j records per shared-memory tile
-constexpr int RT = 8;       // basis columns per CTA
-
-template <int D, int S>
-__global__ void __launch_bounds__(RF_NT)
-    k_refresh(const float *__restrict__ rec, int N, const float *__restrict__ phi, int ld, int r,
-              float *__restrict__ U1, float *__restrict__ U2) {
-  constexpr int DP = Rec<D>::DP;
-  __shared__ __align__(16) float srec[RF_TJ * DP];
-  __shared__ float sphi[RF_TJ][S][RT];
-  const int tid = threadIdx.x;
-  const int i = blockIdx.x * RF_NT + tid;
-  const int t0 = blockIdx.y * RT;
-  const bool vi = i < N;
-  const int ic = vi ? i : N - 1;
-  float xi[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) xi[d] = rec[(size_t)ic * DP + d];
-  const float wi = rec[(size_t)ic * DP + D];
-  float W1[S][RT], W2[S][RT], cs = 0.f;
-#pragma unroll
-  for (int a = 0; a < S; ++a)
-#pragma unroll
-    for (int t = 0; t < RT; ++t) W1[a][t] = W2[a][t] = 0.f;
-
-  for (int jt = 0; jt < N; jt += RF_TJ) {
-    __syncthreads();
-    for (int e = tid; e < RF_TJ * DP; e += RF_NT) srec[e] = rec[(size_t)jt * DP + e];
-    for (int e = tid; e < RF_TJ * S * RT; e += RF_NT) {
-      const int j = e / (S * RT), rem = e - j * (S * RT), a = rem / RT, t = rem - a * RT;
-      const int J = jt + j;
-      sphi[j][a][t] = (J < N && t0 + t < r) ? phi[((size_t)J * S + a) * ld + t0 + t] : 0.f;
-    }
-    __syncthreads();
-    float a1[S][RT], a2[S][RT], ac = 0.f;
-#pragma unroll
-    for (int a = 0; a < S; ++a)
-#pragma unroll
-      for (int t = 0; t < RT; ++t) a1[a][t] = a2[a][t] = 0.f;
-#pragma unroll 2
-    for (int j = 0; j < RF_TJ; ++j) {
-      const float *rj = srec + j * DP;
-      float r2 = 0.f;
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const float dd = xi[d] - rj[d];
-        r2 = fmaf(dd, dd, r2);
-      }
-      const float K = ex2_approx(-r2);
-      const float kw = K * rj[D];
-      ac += kw;
-#pragma unroll
-      for (int a = 0; a < S; ++a)
-#pragma unroll
-        for (int t = 0; t < RT; ++t) {
-          const float f = sphi[j][a][t];
-          a1[a][t] = fmaf(K, f, a1[a][t]);
-          a2[a][t] = fmaf(kw, f, a2[a][t]);
-        }
-    }
-    cs += ac;
-#pragma unroll
-    for (int a = 0; a < S; ++a)
-#pragma unroll
-      for (int t = 0; t < RT; ++t) {
-        W1[a][t] += a1[a][t];
-        W2[a][t] += a2[a][t];
-      }
-  }
-  if (!vi) return;
-#pragma unroll
-  for (int a = 0; a < S; ++a)
-#pragma unroll
-    for (int t = 0; t < RT; ++t) {
-      if (t0 + t >= r) continue;
-      const size_t o = ((size_t)i * S + a) * ld + t0 + t;
-      const float f = phi[o];
-      U1[o] = f - W1[a][t] * wi;
-      U2[o] = cs * f - W2[a][t];
-    }
-}
 
 struct RedParams {
   double kBT, zeta, dt;
@@ -291,27 +204,6 @@ int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, co
   }
 }
 
-template <int D, int S>
-int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
-  dim3 grid((N + RF_NT - 1) / RF_NT, (b->r + RT - 1) / RT);
-  VDS_TRY(vds_time_begin(c, PK_REFRESH));
-  k_refresh<D, S><<<grid, RF_NT, 0, c->stream>>>((const float *)c->rec.ptr, N, b->phi, b->ld, b->r, U1, U2);
-  VDS_CUDA_TRY(cudaGetLastError());
-  VDS_TRY(vds_time_end(c, PK_REFRESH));
-  ++c->launches;
-  return VDS_OK;
-}
-
-int refresh_dispatch(vds_ctx *c, const pod_basis *b, int N, int D, float *U1, float *U2) {
-  const int s = b->s;
-#define RF(DD, SS) \
-  if (D == DD && s == SS) return refresh_impl<DD, SS>(c, b, N, U1, U2);
-  RF(2, 2) RF(3, 3) RF(4, 2) RF(6, 2) RF(6, 3) RF(8, 2) RF(9, 3) RF(10, 2) RF(12, 2) RF(12, 3)
-  RF(14, 2) RF(15, 3) RF(16, 2)
-#undef RF
-  return VDS_EARG;
-}
-
 int check(const vds_params *p, const pod_basis *b, int N, int D) {
   if (!p || !b || N < 1 || D < 2 || D > VDS_MAXD) return VDS_EARG;
   if (p->s != b->s || p->nb * p->s != D || (long)N * b->s != b->Ns || p->nb > 8) return VDS_EARG;
@@ -339,7 +231,7 @@ int brownian_dev(vds_ctx *c, const pod_basis *b, const float *P, int N, int D, c
   VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
   VDS_TRY(pass_prep(c, kp, qt, nullptr, nullptr, 0.f, nullptr));
   VDS_TRY(pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr));
-  VDS_TRY(refresh_dispatch(c, b, N, D, U1, U2));
+  VDS_TRY(pod_refresh_dev(c, b, N, D, U1, U2));
   VDS_TRY(pod_tsgram(c, b->phi, U1, b->Ns, b->ld, b->r, G1));
   VDS_TRY(pod_tsgram(c, b->phi, U2, b->Ns, b->ld, b->r, G2));
   return VDS_OK;

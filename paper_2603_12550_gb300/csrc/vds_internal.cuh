@@ -159,8 +159,18 @@ struct DevBuf {
   size_t cap = 0;
 };
 
-// Optional instrumentation of pair-pass launches (vds_timing).
-enum { PK_DENSITY = 0, PK_GRADIENT = 1, PK_BANDWIDTH = 2, PK_REFRESH = 3, PK_COUNT = 4 };
+// Optional instrumentation of pair-pass launches and POD phases (vds_timing).
+enum {
+  PK_DENSITY = 0,
+  PK_GRADIENT = 1,
+  PK_BANDWIDTH = 2,
+  PK_REFRESH = 3,
+  PK_GRAM = 4,
+  PK_EIGEN = 5,
+  PK_BASIS = 6,
+  PK_COUNT = 7
+};
+static_assert(PK_COUNT == VDS_TIMING_KINDS, "timing kinds");
 struct TimingPool {
   bool on = false;
   cudaEvent_t ev[PK_COUNT][2][256] = {};

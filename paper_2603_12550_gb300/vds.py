@@ -17,6 +17,8 @@ from . import build as _build
 VDS_OK, VDS_EARG, VDS_ECUDA, VDS_EDOMAIN, VDS_ENOCONV = 0, -1, -2, -3, -4
 VDS_ENAN, VDS_ETIMEOUT, VDS_ENOMEM, VDS_ESURROGATE, VDS_ESIZE = -5, -6, -7, -8, -9
 VDS_NOALLOC_MAX_N = 8192
+BATCH_CONFIGS = 4  # pair-kernel shapes of the batched tile autotuner
+TIMING_KINDS = 7  # density, gradient, bandwidth, refresh, POD Gram, POD eigensolve, POD basis
 
 
 class VdsError(RuntimeError):
@@ -92,6 +94,9 @@ _SIGS = {
     "vds_batch_queue": ([_vp, _ip, _i], _i),
     "vds_batch_energy_grad": ([_vp, _vp, _vp, _dp, _vp, _vp], _i),
     "vds_batch_step": ([_vp, _vp, _vp, _i, _ip], _i),
+    "vds_batch_autotune": ([_vp, _vp, _vp, _i, _ip, _dp], _i),
+    "vds_batch_set_config": ([_vp, _vp, _i], _i),
+    "vds_batch_get_config": ([_vp, _ip], _i),
     "vds_score_param_count": ([_i, _i], _l),
     "vds_score_create": ([_vp, _i, _i, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(_vp)], _i),
     "vds_score_free": ([_vp], None),
@@ -178,8 +183,8 @@ class Context:
         _check(lib.vds_timing(self.h, 1 if enable else 0))
 
     def vds_timing_read(self):
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_long * 4)()
+        ms = (ctypes.c_double * TIMING_KINDS)()
+        n = (ctypes.c_long * TIMING_KINDS)()
         tot = ctypes.c_long()
         _check(lib.vds_timing_read(self.h, ms, n, ctypes.byref(tot)))
         return list(ms), list(n), tot.value
@@ -280,6 +285,22 @@ class Batch:
         _check(lib.vds_batch_energy_grad(self.ctx.h, self.h, _ptr(q_all), E if want_energy else None,
                                          _ptr(g), _ptr(rho)))
         return np.array(E[:]) if want_energy else None
+
+    def autotune(self, q_all, reps=3):
+        """Times every pair-kernel shape on q_all, keeps the fastest; returns
+        (config, milliseconds per config)."""
+        cfg = ctypes.c_int()
+        ms = (ctypes.c_double * BATCH_CONFIGS)()
+        _check(lib.vds_batch_autotune(self.ctx.h, self.h, _ptr(q_all), int(reps), ctypes.byref(cfg), ms))
+        return cfg.value, list(ms)
+
+    def set_config(self, config):
+        _check(lib.vds_batch_set_config(self.ctx.h, self.h, int(config)))
+
+    def config(self):
+        cfg = ctypes.c_int()
+        _check(lib.vds_batch_get_config(self.h, ctypes.byref(cfg)))
+        return cfg.value
 
     def step(self, q_all, nsteps=1, want_iters=False):
         it = (ctypes.c_int * max(1, nsteps * self.E))() if want_iters else None

@@ -133,3 +133,41 @@ def test_batched_implicit_matches_single_ensemble_path(vds, ctx):
         ref = q1.cpu().numpy()
         got = q_all[off[e]:off[e + 1]].cpu().numpy()
         assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+def test_every_tile_shape_is_bit_identical(orc, vds, ctx):
+    # the autotuner's candidate shapes change threads per CTA and particles
+    # per thread, not the order of any sum: same bits, queue in LPT order for
+    # each shape's i-tile
+    qs, h, kap = _ensembles()
+    b = _batch(vds, ctx, SIZES, h, kap)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    ref_g = None
+    for cfg in range(vds.BATCH_CONFIGS):
+        b.set_config(cfg)
+        assert b.config() == cfg
+        np.testing.assert_array_equal(b.queue(), orc.work_queue(SIZES, b.info()["tile"]))
+        g = torch.empty_like(q_all)
+        rho = torch.empty(q_all.shape[0], device="cuda")
+        E = b.energy_grad(q_all, g=g, rho=rho)
+        if ref_g is None:
+            ref_g, ref_rho, ref_E = g, rho, E
+        else:
+            assert torch.equal(g, ref_g) and torch.equal(rho, ref_rho)
+            np.testing.assert_array_equal(E, ref_E)
+    with pytest.raises(vds.VdsError):
+        b.set_config(vds.BATCH_CONFIGS)
+
+
+def test_autotune_keeps_the_fastest_shape(vds, ctx):
+    qs, h, kap = _ensembles(4)
+    b = _batch(vds, ctx, SIZES, h, kap, dt=0.01, scheme=1, tol=1e-6, jfloor=1e-9)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    q_ref = q_all.clone()
+    b.step(q_ref, 1)  # default shape, round graph captured
+    cfg, ms = b.autotune(q_all, reps=2)
+    assert len(ms) == vds.BATCH_CONFIGS and all(m > 0 for m in ms)
+    assert cfg == int(np.argmin(ms)) and b.config() == cfg
+    # implicit step after the switch (graph captured again): same bits
+    b.step(q_all, 1)
+    assert torch.equal(q_all, q_ref)
