@@ -12,8 +12,9 @@
 // FMAs that follow dominate.  One CTA column chunk carries RT basis columns
 // (RT in {4, 8, 12, 16}, chosen at launch to cover r with the fewest wasted
 // columns), so for r <= 16 the kernel value is evaluated once per pair.
-// Sums run in FP32: per 64-record j-tile into registers, then into per-
-// particle totals (two-level summation).
+// Sums run in FP32: per 32-record j-tile into registers, then into per-
+// particle totals (two-level summation; a single running FP32 sum over all
+// N = 65536 terms loses about two more digits).
 #include <math.h>
 
 #include "pair.cuh"
@@ -21,16 +22,29 @@
 
 namespace {
 
-constexpr int RF_NT = 128;  // threads (particles) per CTA
-constexpr int RF_TJ = 64;   // j records per shared-memory tile
+constexpr int RF_NT = 64;   // threads (particles) per CTA
+constexpr int RF_TJ = 32;   // j records per shared-memory tile (divides the record padding)
 
+// Resident CTAs per SM: 8 (128 registers) when the per-tile partials fit,
+// else 6 (170 registers), or 5 (204) for the widest rows.
 template <int D, int S, int RT>
-__global__ void __launch_bounds__(RF_NT)
+struct RfOcc {
+  static constexpr int value = (2 * S * RT <= 72) ? 8 : (D + 2 * S * RT <= 105 ? 6 : 5);
+};
+
+// One thread per particle I, RT columns of one chunk.  Per j-tile the sums go
+// to register partials a1, a2; the per-particle totals live in shared memory
+// (thread-private columns), which keeps the register count at the occupancy
+// target.
+template <int D, int S, int RT>
+__global__ void __launch_bounds__(RF_NT, RfOcc<D, S, RT>::value)
     k_refresh(const float *__restrict__ rec, int N, const float *__restrict__ phi, int ld, int r,
               float *__restrict__ U1, float *__restrict__ U2) {
   constexpr int DP = Rec<D>::DP;
+  constexpr int NC = S * RT;
   __shared__ __align__(16) float srec[RF_TJ * DP];
   __shared__ __align__(16) float sphi[RF_TJ][S][RT];
+  __shared__ float W1s[NC][RF_NT], W2s[NC][RF_NT];
   const int tid = threadIdx.x;
   const int i = blockIdx.x * RF_NT + tid;
   const int t0 = blockIdx.y * RT;
@@ -40,22 +54,27 @@ __global__ void __launch_bounds__(RF_NT)
 #pragma unroll
   for (int d = 0; d < D; ++d) xi[d] = rec[(size_t)ic * DP + d];
   const float wi = rec[(size_t)ic * DP + D];
-  float W1[S][RT], W2[S][RT], cs = 0.f;
 #pragma unroll
-  for (int a = 0; a < S; ++a)
-#pragma unroll
-    for (int t = 0; t < RT; ++t) W1[a][t] = W2[a][t] = 0.f;
+  for (int k = 0; k < NC; ++k) W1s[k][tid] = W2s[k][tid] = 0.f;
+  float cs = 0.f;
 
   for (int jt = 0; jt < N; jt += RF_TJ) {
     __syncthreads();
-    for (int e = tid; e < RF_TJ * DP; e += RF_NT) srec[e] = rec[(size_t)jt * DP + e];
-    // basis rows of the tile: RT consecutive columns of row (J, a)
-    for (int e = tid; e < RF_TJ * S; e += RF_NT) {
-      const int J = jt + e / S, a = e - (e / S) * S;
-      float *dst = &sphi[e / S][a][0];
-      const float *src = phi + ((size_t)J * S + a) * ld + t0;
-#pragma unroll
-      for (int t = 0; t < RT; ++t) dst[t] = (J < N && t0 + t < r) ? src[t] : 0.f;
+    {
+      const float4 *src = reinterpret_cast<const float4 *>(rec + (size_t)jt * DP);
+      float4 *dst = reinterpret_cast<float4 *>(srec);
+      for (int e = tid; e < RF_TJ * DP / 4; e += RF_NT) dst[e] = src[e];
+    }
+    // basis rows of the tile: RT consecutive columns of row (J, a), as float4
+    // (ld and t0 are multiples of 4; columns r..ld-1 of Phi are zero)
+    for (int e = tid; e < RF_TJ * S * (RT / 4); e += RF_NT) {
+      const int row = e / (RT / 4), v = e - row * (RT / 4);
+      const int jj = row / S, a = row - jj * S;
+      const int J = jt + jj;
+      float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (J < N && t0 + 4 * v < ld)
+        f = *reinterpret_cast<const float4 *>(phi + ((size_t)J * S + a) * ld + t0 + 4 * v);
+      *reinterpret_cast<float4 *>(&sphi[jj][a][4 * v]) = f;
     }
     __syncthreads();
     float a1[S][RT], a2[S][RT], ac = 0.f;
@@ -89,8 +108,8 @@ __global__ void __launch_bounds__(RF_NT)
     for (int a = 0; a < S; ++a)
 #pragma unroll
       for (int t = 0; t < RT; ++t) {
-        W1[a][t] += a1[a][t];
-        W2[a][t] += a2[a][t];
+        W1s[a * RT + t][tid] += a1[a][t];
+        W2s[a * RT + t][tid] += a2[a][t];
       }
   }
   if (!vi) return;
@@ -101,8 +120,8 @@ __global__ void __launch_bounds__(RF_NT)
       if (t0 + t >= r) continue;
       const size_t o = ((size_t)i * S + a) * ld + t0 + t;
       const float f = phi[o];
-      U1[o] = f - W1[a][t] * wi;
-      U2[o] = cs * f - W2[a][t];
+      U1[o] = f - W1s[a * RT + t][tid] * wi;
+      U2[o] = cs * f - W2s[a * RT + t][tid];
     }
 }
 
