@@ -16,8 +16,10 @@ extern "C" {
 /* POD by the method of snapshots (Sec. 2.3, Sec. 3.1).
  * X: device, column-major (N s) x M snapshot matrix, one column per
  * (snapshot l, bond k) = q_k(t_l) flattened over rows (I, alpha).
- * C = X^T X (M x M, FP32 products with compensated sums, FP64 result);
- * C = V Lambda V^T by cyclic Jacobi in FP64; rank r = r_fixed if > 0, else
+ * C = X^T X (M x M) on the tensor cores: TF32 with one refinement step (each
+ * FP32 value split into two TF32 parts, three products per pair), FP32 sums
+ * over 512-row segments and FP64 across segments (relative error about 1e-7
+ * of max|C|); C = V Lambda V^T by cyclic Jacobi in FP64; rank r = r_fixed if > 0, else
  * the smallest r with sum_{i<=r} lambda_i >= energy * sum_i lambda_i,
  * capped at r_max (<= 64); Phi = X V_r Lambda_r^(-1/2), re-orthonormalised
  * by one Cholesky-QR pass; sign: the largest-magnitude entry of each column
@@ -27,6 +29,13 @@ extern "C" {
 VDS_API int pod_build(vds_ctx *ctx, const float *X, long Ns, int M, int s,
               double energy, int r_max, int r_fixed, const double *kappa,
               pod_basis **out, int *r);
+/* A basis supplied by the caller (one stored from an earlier pod_build, or
+ * computed elsewhere): phi device, (N s) x r row-major FP32 with orthonormal
+ * columns (not checked), 1 <= r <= 64; kappa (host, s x s) gives X^H as in
+ * pod_build.  The basis holds no eigenvalues (pod_eigenvalues copies none).
+ * *out receives a new basis owned by the caller (pod_free). */
+VDS_API int pod_load(vds_ctx *ctx, const float *phi, long Ns, int r, int s, const double *kappa,
+                     pod_basis **out);
 /* Basis accessors: Phi (device, (N s) x r row-major, leading dimension *ld),
  * eigenvalues (host copy, M values, descending), X^H (host, r x r). */
 VDS_API int pod_info(const pod_basis *b, int *r, int *ld, const float **phi_dev,

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/vds_score.h"
+#include "tcgen05.cuh"
 #include "vds_internal.cuh"
 
 typedef __nv_bfloat16 bf16;
@@ -30,51 +31,6 @@ namespace {
 constexpr int GM = 128;   // rows per CTA tile
 constexpr int KC = 64;    // K per chunk
 constexpr int TMEM_COLS = 128;
-
-// ------------------------------------------------------------ tcgen05 glue
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  // K-major, no swizzle: LBO = 128 B (next core matrix along K),
-  // SBO = 1024 B (next 8-row group), descriptor version 1
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
-         (1ull << 46);
-}
-
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  // D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9 = 1, 10-12 = 1), K-major
-  // A and B, N >> 3 at bits 17-22, M >> 4 at bits 24-28
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
@@ -101,16 +57,6 @@ struct Epi {
 constexpr int GBN = 128;   // columns of C per CTA
 constexpr int GST = 4;     // pipeline stages (K chunks in flight)
 constexpr int GSTAGE = GM * KC * 2 + GBN * KC * 2;  // bytes per stage (A 16 KB + B <= 16 KB)
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // Asynchronous copy of a rows_tile x 64 chunk (rows beyond nvalid zero-filled)
 // into the K-major canonical layout: byte offset of element (r, k) is
@@ -141,10 +87,7 @@ __global__ void __launch_bounds__(128)
   const int n0 = blockIdx.z * GBN;
   const int BN = min(GBN, N - n0);
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_alloc(&s_tmem, TMEM_COLS);
   }
   if (tid == 0) {
     for (int k = 0; k < GST; ++k) mbar_init(&bars[k], 1);
@@ -154,7 +97,7 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = idesc_bf16(GM, BN);
+  const uint32_t idesc = tc_idesc(TC_FMT_BF16, GM, BN);
   const int nch = Ksplit / KC;
   const int avalid = min(GM, ep.rows - m0);
   const uint32_t sbase = smem_u32(gsm);
@@ -178,7 +121,7 @@ __global__ void __launch_bounds__(128)
       const uint32_t a0 = sbase + (ch % GST) * GSTAGE, b0 = a0 + GM * KC * 2;
 #pragma unroll
       for (int k = 0; k < KC / 16; ++k)
-        tc_mma(tmem, sdesc(a0 + k * 256), sdesc(b0 + k * 256), idesc, (ch > 0 || k > 0) ? 1 : 0);
+        tc_mma_bf16(tmem, tc_sdesc(a0 + k * 256), tc_sdesc(b0 + k * 256), idesc, (ch > 0 || k > 0) ? 1 : 0);
       tc_commit(&bars[ch % GST]);
     }
     // the stage refilled next was read by the MMAs of chunk ch-1
@@ -235,7 +178,7 @@ __global__ void __launch_bounds__(128)
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    tc_dealloc(tmem, TMEM_COLS);
 }
 
 constexpr size_t GEMM_SMEM = (size_t)GST * GSTAGE;

@@ -2,12 +2,13 @@
 // project / lift maps of Eq. model_pq, for GB300 (sm_103a).
 //
 // pod_build:
-//   C = X^T X            FP32 snapshots, exact FP64 products and sums (the
-//                        upper-triangle 64x64 tiles, k split across CTAs,
-//                        partials combined in a fixed order)
+//   C = X^T X            tensor cores, TF32 with one refinement step
+//                        (3xTF32 split of every snapshot value) and FP64
+//                        sums across 512-row segments (gram_tc.cu)
 //   C = V Lambda V^T     two-sided cyclic Jacobi in FP64 with the round-robin
-//                        ordering: each round applies M/2 disjoint rotations
-//                        in one launch (block (a,b) of A' = R_a^T A_ab R_b)
+//                        ordering: each round computes its M/2 disjoint
+//                        rotations once, then applies them in one launch
+//                        (block (a,b) of A' = R_a^T A_ab R_b)
 //   r                    energy rule on the sorted eigenvalues (FP64 prefix
 //                        sums in descending order), or r_fixed
 //   Phi = X V_r Lambda_r^(-1/2)   FP64 accumulation, stored FP32
@@ -27,71 +28,6 @@ namespace {
 struct KappaArg {
   double k[9];
 };
-
-constexpr int GT = 64;   // Gram tile (columns)
-constexpr int GK = 32;   // Gram k-step
-
-// ------------------------------------------------------------------ Gram
-
-__global__ void __launch_bounds__(256)
-    k_gram_x(const float *__restrict__ X, long Ns, int M, int nbt, long kchunk,
-             double *__restrict__ part) {
-  const int bi = blockIdx.x / nbt, bj = blockIdx.x - (blockIdx.x / nbt) * nbt;
-  if (bi > bj) return;
-  const long k0 = (long)blockIdx.y * kchunk;
-  const long k1 = min(Ns, k0 + kchunk);
-  __shared__ float As[GK][GT + 1], Bs[GK][GT + 1];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (long kb = k0; kb < k1; kb += GK) {
-#pragma unroll
-    for (int u = 0; u < (GK * GT) / 256; ++u) {
-      const int e = tid + 256 * u, kk = e & (GK - 1), c = e / GK;
-      const long row = kb + kk;
-      const int ca = bi * GT + c, cb = bj * GT + c;
-      As[kk][c] = (row < k1 && ca < M) ? X[row + (long)ca * Ns] : 0.f;
-      Bs[kk][c] = (row < k1 && cb < M) ? X[row + (long)cb * Ns] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        a[i] = (double)As[kk][tx * 4 + i];
-        b[i] = (double)Bs[kk][ty * 4 + i];
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-  double *dst = part + ((size_t)blockIdx.y * nbt * nbt + blockIdx.x) * (GT * GT);
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) dst[(tx * 4 + i) * GT + ty * 4 + j] = acc[i][j];
-}
-
-// C (M x M, FP64) = sum over k-splits of the tile partials; symmetric fill.
-__global__ void k_gram_reduce(const double *__restrict__ part, int M, int nbt, int nks,
-                              double *__restrict__ C) {
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)M * M) return;
-  const int i = (int)(idx / M), j = (int)(idx - (long)(idx / M) * M);
-  const int ii = i <= j ? i : j, jj = i <= j ? j : i;
-  const int bi = ii / GT, bj = jj / GT;
-  const size_t off = (size_t)(bi * nbt + bj) * (GT * GT) + (ii - bi * GT) * GT + (jj - bj * GT);
-  double v = 0.0;
-  for (int k = 0; k < nks; ++k) v += part[(size_t)k * nbt * nbt * (GT * GT) + off];
-  C[idx] = v;
-}
 
 // ------------------------------------------------------------------ Jacobi
 
@@ -128,9 +64,24 @@ __device__ __forceinline__ void jac_rot(const double *A, int M, int p, int q, do
   s = t * c;
 }
 
+// The M/2 disjoint rotations of round `rnd`, computed once from the current A
+// (rot[a] = (c, s) for pair a of the round-robin ordering).
+__global__ void __launch_bounds__(256)
+    k_jacobi_rots(const double *__restrict__ A, int M, int Mp, int rnd, double2 *__restrict__ rot) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= Mp / 2) return;
+  int p, q;
+  jac_pair(a, rnd, Mp, p, q);
+  double c, s;
+  jac_rot(A, M, p, q, c, s);
+  rot[a] = make_double2(c, s);
+}
+
+// A2 = R^T A R on every 2x2 block (rows of pair a, columns of pair b) and
+// V2 = V R, with the rotations of the round from k_jacobi_rots.
 __global__ void __launch_bounds__(256)
     k_jacobi_round(const double *__restrict__ A, double *__restrict__ A2, const double *__restrict__ V,
-                   double *__restrict__ V2, int M, int Mp, int rnd) {
+                   double *__restrict__ V2, int M, int Mp, int rnd, const double2 *__restrict__ rot) {
   const int H = Mp / 2;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nA = (long)H * H;
@@ -139,9 +90,8 @@ __global__ void __launch_bounds__(256)
     int p, q, p2, q2;
     jac_pair(a, rnd, Mp, p, q);
     jac_pair(b, rnd, Mp, p2, q2);
-    double ca, sa, cb, sb;
-    jac_rot(A, M, p, q, ca, sa);
-    jac_rot(A, M, p2, q2, cb, sb);
+    const double2 ra = rot[a], rb = rot[b];
+    const double ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
     auto get = [&](int i, int j) -> double { return (i < M && j < M) ? A[(size_t)i * M + j] : 0.0; };
     const double x00 = get(p, p2), x01 = get(p, q2), x10 = get(q, p2), x11 = get(q, q2);
     const double t00 = ca * x00 - sa * x10, t01 = ca * x01 - sa * x11;
@@ -162,8 +112,8 @@ __global__ void __launch_bounds__(256)
     const int i = (int)(v / H), b = (int)(v - (long)(v / H) * H);
     int p2, q2;
     jac_pair(b, rnd, Mp, p2, q2);
-    double cb, sb;
-    jac_rot(A, M, p2, q2, cb, sb);
+    const double2 rb = rot[b];
+    const double cb = rb.x, sb = rb.y;
     if (q2 >= M) {
       if (p2 < M) V2[(size_t)i * M + p2] = V[(size_t)i * M + p2];
       return;
@@ -545,14 +495,6 @@ __global__ void k_project_reduce2(const double *__restrict__ part, int nblk, int
   }
 }
 
-__global__ void k_project_reduce(const double *__restrict__ part, int nblk, int n, float *__restrict__ p) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n) return;
-  double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * n + o];
-  p[o] = (float)v;
-}
-
 // q[I D + s k + a] = sum_t Phi[(I s + a), t] p[t nb + k]
 __global__ void __launch_bounds__(256)
     k_lift(const float *__restrict__ phi, int ld, int r, const float *__restrict__ p, int N, int D,
@@ -645,17 +587,10 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   } restore{prev, c->device};
 
   TmpBufs tb;
-  const int nbt = (M + GT - 1) / GT;
-  // k split: about four CTAs per SM over the upper-triangle tiles
-  const int ntiles = nbt * (nbt + 1) / 2;
-  int nks = (4 * c->num_sms + ntiles - 1) / ntiles;
-  long kchunk = (Ns + nks - 1) / nks;
-  kchunk = (kchunk + GK - 1) / GK * GK;
-  nks = (int)((Ns + kchunk - 1) / kchunk);
   const size_t MM = (size_t)M * M;
   double *gpart, *A0, *A1, *V0, *V1, *W, *lam_s, *G, *Linv;
   int *order;
-  VDS_CUDA_TRY(cudaMalloc(&tb.p[0], (size_t)nks * nbt * nbt * GT * GT * sizeof(double)));
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[0], pod_gram_tc_workspace(c, Ns, M)));
   gpart = (double *)tb.p[0];
   VDS_CUDA_TRY(cudaMalloc(&tb.p[1], 4 * MM * sizeof(double)));
   A0 = (double *)tb.p[1];
@@ -670,18 +605,17 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   Linv = G + 64 * 64;
   VDS_CUDA_TRY(cudaMalloc(&tb.p[3], (size_t)M * sizeof(int)));
   order = (int *)tb.p[3];
+  VDS_CUDA_TRY(cudaMalloc(&tb.p[7], (size_t)(M / 2 + 1) * sizeof(double2)));
+  double2 *rot = (double2 *)tb.p[7];
 
   // 1. Gram
   VDS_TRY(vds_time_begin(c, PK_GRAM));
-  k_gram_x<<<dim3(nbt * nbt, nks), 256, 0, c->stream>>>(X, Ns, M, nbt, kchunk, gpart);
-  VDS_CUDA_TRY(cudaGetLastError());
-  k_gram_reduce<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(gpart, M, nbt, nks, A0);
-  VDS_CUDA_TRY(cudaGetLastError());
+  VDS_TRY(pod_gram_tc(c, X, Ns, M, gpart, A0));
   VDS_TRY(vds_time_end(c, PK_GRAM));
   VDS_TRY(vds_time_begin(c, PK_EIGEN));
   k_identity<<<(unsigned)((MM + 255) / 256), 256, 0, c->stream>>>(V0, M);
   VDS_CUDA_TRY(cudaGetLastError());
-  c->launches += 3;
+  ++c->launches;
 
   // 2. cyclic Jacobi, round-robin ordering
   VDS_TRY(vds_ensure(c, c->red, 2 * 1024 * sizeof(double)));
@@ -691,20 +625,46 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   const unsigned nblk_round = (unsigned)((nthreads + 255) / 256);
   int offblk = (int)((MM + 255) / 256);
   if (offblk > 1024) offblk = 1024;
+  // One sweep (Mpe - 1 rounds, two launches each) is captured as a CUDA graph
+  // per starting buffer pair (the buffers swap once per round).
+  struct SweepGraphs {
+    cudaGraphExec_t g[2] = {nullptr, nullptr};
+    ~SweepGraphs() {
+      for (cudaGraphExec_t x : g)
+        if (x) cudaGraphExecDestroy(x);
+    }
+  } sg;
+  double *Ab[2] = {A0, A1}, *Vb[2] = {V0, V1};
+  auto capture = [&](int par) -> int {
+    cudaStream_t cap;
+    VDS_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int cur = par;
+    for (int rnd = 0; rnd < Mpe - 1 && e == cudaSuccess; ++rnd) {
+      k_jacobi_rots<<<(H + 255) / 256, 256, 0, cap>>>(Ab[cur], M, Mpe, rnd, rot);
+      k_jacobi_round<<<nblk_round, 256, 0, cap>>>(Ab[cur], Ab[cur ^ 1], Vb[cur], Vb[cur ^ 1], M, Mpe, rnd, rot);
+      e = cudaGetLastError();
+      cur ^= 1;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&sg.g[par], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      vds_last_cuda_error(e != cudaSuccess ? e : e2);
+      return VDS_ECUDA;
+    }
+    return VDS_OK;
+  };
+  int par = 0;  // buffers holding the current A, V
   double prev_off = -1.0;
   for (int sweep = 0; sweep < 40; ++sweep) {
-    for (int rnd = 0; rnd < Mpe - 1; ++rnd) {
-      k_jacobi_round<<<nblk_round, 256, 0, c->stream>>>(A0, A1, V0, V1, M, Mpe, rnd);
-      VDS_CUDA_TRY(cudaGetLastError());
-      ++c->launches;
-      double *t = A0;
-      A0 = A1;
-      A1 = t;
-      t = V0;
-      V0 = V1;
-      V1 = t;
-    }
-    k_offnorm<<<offblk, 256, 0, c->stream>>>(A0, M, (double *)c->red.ptr, c->ticket + TK_MISC, c->scal);
+    if (!sg.g[par]) VDS_TRY(capture(par));
+    VDS_CUDA_TRY(cudaGraphLaunch(sg.g[par], c->stream));
+    c->launches += 2 * (Mpe - 1);
+    if ((Mpe - 1) % 2 == 1) par ^= 1;
+    k_offnorm<<<offblk, 256, 0, c->stream>>>(Ab[par], M, (double *)c->red.ptr, c->ticket + TK_MISC, c->scal);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
     VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
@@ -714,6 +674,8 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
     if (off <= 1e-30 * tot || (prev_off >= 0.0 && off >= prev_off && off <= 1e-24 * tot)) break;
     prev_off = off;
   }
+  A0 = Ab[par];
+  V0 = Vb[par];
 
   // 3. sort, rank rule, W = V_r Lambda_r^-1/2
   k_eig_sort<<<1, 1024, 0, c->stream>>>(A0, V0, M, energy, r_max, r_fixed, lam_s, order, W, c->scal);
@@ -825,6 +787,69 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   return VDS_OK;
 }
 
+int pod_load(vds_ctx *c, const float *phi, long Ns, int r, int s, const double *kappa, pod_basis **out) {
+  if (!c || !phi || !out || Ns < 1 || r < 1 || r > 64 || (s != 2 && s != 3) || Ns % s != 0) return VDS_EARG;
+  *out = nullptr;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  struct Restore {
+    int prev, dev;
+    ~Restore() {
+      if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+  } restore{prev, c->device};
+  TmpBufs tb;
+  const int ld = (r + 3) / 4 * 4;
+  pod_basis *b = new pod_basis();
+  b->device = c->device;
+  b->Ns = Ns;
+  b->M = 0;
+  b->r = r;
+  b->ld = ld;
+  b->s = s;
+  int st = VDS_OK;
+  do {
+    b->xh = (double *)malloc(sizeof(double) * r * r);
+    if (!b->xh || cudaMalloc(&b->phi, (size_t)Ns * ld * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&tb.p[0], (size_t)Ns * ld * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&tb.p[1], (size_t)r * r * sizeof(double)) != cudaSuccess) {
+      st = VDS_ENOMEM;
+      break;
+    }
+    if (cudaMemsetAsync(b->phi, 0, (size_t)Ns * ld * sizeof(float), c->stream) != cudaSuccess ||
+        cudaMemcpy2DAsync(b->phi, (size_t)ld * sizeof(float), phi, (size_t)r * sizeof(float),
+                          (size_t)r * sizeof(float), (size_t)Ns, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    KappaArg ka;
+    for (int k = 0; k < 9; ++k) ka.k[k] = 0.0;
+    if (kappa)
+      for (int k = 0; k < s * s; ++k) ka.k[k] = kappa[k];
+    k_kappa_phi<<<(unsigned)((Ns * ld + 255) / 256), 256, 0, c->stream>>>(b->phi, Ns, ld, s, ka,
+                                                                         (float *)tb.p[0]);
+    if (cudaGetLastError() != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    ++c->launches;
+    double *G = (double *)tb.p[1];
+    if ((st = pod_tsgram(c, b->phi, (const float *)tb.p[0], Ns, ld, r, G)) != VDS_OK) break;
+    if (cudaMemcpyAsync(b->xh, G, sizeof(double) * r * r, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    st = vds_sync_status(c);
+  } while (0);
+  if (st != VDS_OK) {
+    pod_free(b);
+    return st;
+  }
+  *out = b;
+  return VDS_OK;
+}
+
 int pod_info(const pod_basis *b, int *r, int *ld, const float **phi, long *Ns) {
   if (!b) return VDS_EARG;
   if (r) *r = b->r;
@@ -836,7 +861,7 @@ int pod_info(const pod_basis *b, int *r, int *ld, const float **phi, long *Ns) {
 
 int pod_eigenvalues(const pod_basis *b, double *lam, int M) {
   if (!b || !lam || M < b->M) return VDS_EARG;
-  memcpy(lam, b->lam, sizeof(double) * b->M);
+  if (b->M > 0) memcpy(lam, b->lam, sizeof(double) * b->M);
   return VDS_OK;
 }
 

@@ -13,6 +13,11 @@ struct pod_basis {
   double *xh = nullptr;        // host, r x r
 };
 
+// C (device, M x M FP64) = X^T X for column-major FP32 X (Ns x M) on the
+// tensor cores (3xTF32, FP64 across 512-row segments; gram_tc.cu); `part` is
+// device workspace of pod_gram_tc_workspace bytes.
+size_t pod_gram_tc_workspace(const vds_ctx *c, long Ns, int M);
+int pod_gram_tc(vds_ctx *c, const float *X, long Ns, int M, double *part, double *C);
 // G (device, r x r FP64) = A^T B for row-major Ns x ld FP32 matrices.
 int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *G);
 // P = Phi^T q (r x nb) into pd (FP64, may be NULL) and/or pf (FP32, may be NULL).

@@ -82,6 +82,7 @@ _SIGS = {
     "vds_energy_grad_noalloc": ([_vp, _i, _i, _pp, _dp, _vp, _vp, _vp], _i),
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
     "pod_build": ([_vp, _vp, _l, _i, _i, _d, _i, _i, _dp, ctypes.POINTER(_vp), _ip], _i),
+    "pod_load": ([_vp, _vp, _l, _i, _i, _dp, ctypes.POINTER(_vp)], _i),
     "pod_info": ([_vp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_l)], _i),
     "pod_eigenvalues": ([_vp, _dp, _i], _i),
     "pod_xh": ([_vp, _dp], _i),
@@ -225,6 +226,15 @@ class Context:
         _check(lib.pod_build(self.h, _ptr(X), int(Ns), int(M), int(s), float(energy), int(r_max),
                              int(r_fixed), kbuf, ctypes.byref(out), ctypes.byref(r)))
         return PodBasis(out, M), r.value
+
+    def pod_load(self, phi, s, kappa=None):
+        """Basis from a device (N s) x r FP32 tensor with orthonormal columns."""
+        Ns, r = phi.shape
+        kap = np.zeros(9) if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64).ravel()
+        kbuf = (ctypes.c_double * 9)(*[float(v) for v in kap[:s * s]] + [0.0] * (9 - s * s))
+        out = _vp()
+        _check(lib.pod_load(self.h, _ptr(phi), int(Ns), int(r), int(s), kbuf, ctypes.byref(out)))
+        return PodBasis(out, 0)
 
     def pod_project(self, basis: "PodBasis", q, p_out):
         N, D = q.shape

@@ -4,10 +4,19 @@ basis, X^H, project and lift against the FP64 oracle.
 The snapshot matrices are either synthetic with a prescribed spectrum or taken
 from the oracle's own FP64 trajectory (rounded to FP32), never from the GPU.
 
-Tolerances: the Gram is exact-product FP64 on both sides, so eigenvalues agree
-to 1e-10 lambda_1; the basis is stored in FP32: per column
-||Phi_gpu - Phi_oracle||_2 <= 2e-5 (unit columns, modes with a relative gap
-> 1e-9 of lambda_1); Phi^T Phi = I within 1e-6; X^H and P within 1e-5 relative.
+Tolerances.  The GPU Gram runs on the tensor cores in TF32 with one
+refinement step (3xTF32: every product carries x_hi y_hi + x_hi y_lo +
+x_lo y_hi, relative error <= 3 * 2^-22) and FP32 sums over 512-row segments
+(at most 192 FP32 additions, relative error <= 192 * 2^-24 of the segment's
+sum of |products|), FP64 across segments.  A CPU emulation of exactly that
+arithmetic on these matrices gives Gram errors of 1-3e-7 of max|C| and
+eigenvalue errors <= 8e-8 lambda_1; the tests allow 1e-6 lambda_1.  A basis
+column t moves by at most ||dC|| / gap_t (Davis-Kahan), emulated at about
+1e-9 / (gap_t / lambda_1); the tests allow 2e-5 + 1e-8 / (gap_t / lambda_1)
+(the first term is the FP32 storage of Phi).  Phi^T Phi = I within 1e-6
+(Cholesky-QR in FP64).  X^H is checked against the oracle's X^H of the GPU's
+own basis (1e-5 relative), so it tests the X^H map, not the basis again; P
+and the lifted state against the oracle with the GPU basis, 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -58,17 +67,17 @@ def _compare_basis(orc, vds, ctx, X, s, energy, r_max, r_fixed, kappa):
                              kappa=kappa)
     assert r == o["r"]  # bit-exact rank
     lam = basis.eigenvalues()
-    np.testing.assert_allclose(lam, o["lam"], rtol=0, atol=1e-10 * o["lam"][0])
+    np.testing.assert_allclose(lam, o["lam"], rtol=0, atol=1e-6 * o["lam"][0])
     Phi = basis.phi().cpu().numpy().astype(np.float64)
     Po = o["Phi"]
     assert np.abs(Phi.T @ Phi - np.eye(r)).max() <= 1e-6
     gaps = np.abs(np.diff(np.append(o["lam"], 0.0)[:r + 1])) / o["lam"][0]
     for t in range(r):
         sep = min(gaps[t], gaps[t - 1] if t > 0 else np.inf)
-        if sep > 1e-9:
-            assert np.linalg.norm(Phi[:, t] - Po[:, t]) <= 2e-5, t
+        if sep > 1e-6:
+            assert np.linalg.norm(Phi[:, t] - Po[:, t]) <= 2e-5 + 1e-8 / sep, (t, sep)
     XH = basis.xh()
-    XH_o = orc.x_h(Po, kappa, s)
+    XH_o = orc.x_h(Phi, kappa, s)
     assert np.abs(XH - XH_o).max() <= 1e-5 * max(1.0, np.abs(XH_o).max())
     return basis, o, Phi
 

@@ -3,10 +3,13 @@ matrices X^B1, X^B2, mode 1 (Galerkin, Eq. model_DymRepParPod) and mode 2
 (Eq. model_DymReduced with periodic refresh) against the FP64 oracle.
 
 Both sides start from the same reduced state P0 (the oracle's projection of an
-oracle trajectory state) and use their own bases built from the same FP32
-snapshot matrix.  Tolerances: X^B within 1e-4 relative (Frobenius; FP32 pair
-sums with O(1) cancellation in Phi - W/rho), P within 1e-4 relative after the
-steps.
+oracle trajectory state) and use the same basis: the oracle's POD basis of an
+oracle trajectory, rounded to FP32, loaded on the GPU with pod_load (the GPU's
+own pod_build is checked against the oracle in test_gpu_pod.py; its TF32 Gram
+moves basis columns with small eigenvalue gaps by up to about 1e-9 / gap,
+which these trajectory snapshots have).  Tolerances: X^B within 1e-4 relative
+(Frobenius; FP32 pair sums with O(1) cancellation in Phi - W/rho), P within
+1e-4 relative after the steps.
 """
 import numpy as np
 import pytest
@@ -47,12 +50,20 @@ def setup(orc, vds, ctx):
     X = orc.snapshots_from_states([x.astype(np.float32).astype(np.float64) for x in states], s, nb)
     X32 = X.astype(np.float32)
     o = orc.pod_build(X32.astype(np.float64), r_fixed=r)
-    basis, rg = ctx.pod_build(torch.from_numpy(np.ascontiguousarray(X32.T)).cuda(), N * s, X.shape[1], s,
-                              r_fixed=r, kappa=kap)
-    assert rg == r
-    P0 = orc.project(o["Phi"], states[0], s, nb)
+    Phi32 = o["Phi"].astype(np.float32)
+    basis = ctx.pod_load(torch.from_numpy(np.ascontiguousarray(Phi32)).cuda(), s, kappa=kap)
+    Phi = Phi32.astype(np.float64)
+    P0 = orc.project(Phi, states[0], s, nb)
     pg = vds.params(nb, s, h=0.9, dt=0.005, kappa=kap)
-    return dict(N=N, nb=nb, s=s, r=r, kap=kap, po=po, pg=pg, Phi=o["Phi"], basis=basis, P0=P0)
+    return dict(N=N, nb=nb, s=s, r=r, kap=kap, po=po, pg=pg, Phi=Phi, basis=basis, P0=P0)
+
+
+def test_pod_load_keeps_the_basis(orc, vds, ctx, setup):
+    S = setup
+    Phi = S["basis"].phi().cpu().numpy().astype(np.float64)
+    assert np.array_equal(Phi, S["Phi"])
+    XH_o = orc.x_h(S["Phi"], S["kap"], S["s"])
+    assert np.abs(S["basis"].xh() - XH_o).max() <= 1e-5 * max(1.0, np.abs(XH_o).max())
 
 
 def _rel(a, b):
