@@ -45,7 +45,9 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the secondary measurements (implicit step, POD, batched)")
+                    help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
+    ap.add_argument("--extras", default="implicit,pod,batched,surrogate",
+                    help="comma-separated subset of the secondary measurements to run")
     return ap.parse_args()
 
 
@@ -190,13 +192,11 @@ def run_reference(a, wl, rank):
     print(json.dumps(line), flush=True)
 
 
-def _extras(ctx, vds, inputs, torch, wl, h, stream):
+def _extras(ctx, vds, inputs, torch, wl, h, stream, which):
     """Secondary rows on the same GPU: implicit steps of the 4-bead workload,
     POD build and reduced-order steps, batched vs per-ensemble implicit steps."""
     out = {}
-    N, nb, s = wl["N"], wl["nb"], wl["s"]
-    D = nb * s
-    kap = inputs.shear_kappa(s, wl["rate"])
+    kap = inputs.shear_kappa(wl["s"], wl["rate"])
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -205,15 +205,30 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
         torch.cuda.synchronize()
         return time.perf_counter() - t0, r
 
-    # implicit steps (minimiser) on the 4-bead workload
+    if "implicit" in which:
+        out["implicit_step"] = _extra_implicit(ctx, vds, inputs, torch, wl, h, kap, timed)
+    if "pod" in which:
+        out["pod"] = _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed)
+    if "batched" in which:
+        out["batched"] = _extra_batched(ctx, vds, inputs, torch, timed)
+    return out
+
+
+def _extra_implicit(ctx, vds, inputs, torch, wl, h, kap, timed):
+    """Implicit steps (minimiser) on the 4-bead workload."""
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
     q = torch.from_numpy(inputs.equilibrium_cloud(N, nb, s, H=wl["H"], seed=wl["seed"])).cuda()
     pi = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"], kappa=kap,
                     scheme=1, tol=1e-6, jfloor=1e-9)
     ctx.vds_step(q, pi, 1)
     sec, its = timed(lambda: ctx.vds_step(q, pi, 3, want_iters=True))
-    out["implicit_step"] = {"workload": "chain4_n65536_d9", "steps_per_s": 3 / sec,
-                            "gradient_evaluations_per_step": its, "tol": 1e-6}
+    return {"workload": "chain4_n65536_d9", "steps_per_s": 3 / sec,
+            "gradient_evaluations_per_step": its, "tol": 1e-6}
 
+
+def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
+    D = nb * s
     # POD: 200 snapshots every 5 explicit steps, basis at 99.99 % energy (r <= 64),
     # then the reduced steps (mode 2 refresh every 60 steps = 0.3 time units)
     pe = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"], kappa=kap)
@@ -239,7 +254,7 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
     rf_ms, rf_n, _ = ctx.vds_timing_read()
     ctx.vds_timing(False)
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
-    out["pod"] = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
+    out = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
                   "build_phases_ms": {"gram": ph_ms[4], "eigensolve": ph_ms[5], "basis": ph_ms[6]},
                   "eigenvalues_top": basis.eigenvalues()[:8].tolist(),
                   "mode2_steps_per_s": 240 / sec2, "mode2_refresh_every": 60,
@@ -247,7 +262,10 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
                   "mode1_galerkin_steps_per_s": 3 / sec3, "snapshot_run_s": snap_s}
     del X
     basis.free()
+    return out
 
+
+def _extra_batched(ctx, vds, inputs, torch, timed):
     # batched: 512 ensembles, 3-bead chains (D = 6), N_e = round(2^U(10,14)),
     # shear rates 10^U(-1,1), dt = 0.005, implicit steps
     bnb, bs = 2, 3
@@ -283,7 +301,7 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream):
         t1, _ = ctx.vds_stress(q_all[off[e]:off[e + 1]], pe_)
         t2, _ = ctx.vds_stress(views[e], pe_)
         dev = max(dev, float(np.linalg.norm(t1 - t2) / np.linalg.norm(t2)))
-    out["batched"] = {"ensembles": len(sizes), "d": bnb * bs, "total_particles": int(sizes.sum()),
+    out = {"ensembles": len(sizes), "d": bnb * bs, "total_particles": int(sizes.sum()),
                       "pairs_per_pass": float((sizes.astype(np.float64) ** 2).sum()),
                       "batched_steps_per_s": 2 / sec_b, "per_ensemble_steps_per_s": 2 / sec_p,
                       "speedup": sec_p / sec_b,
@@ -405,6 +423,21 @@ def _extras_surrogate(ctx, vds, inputs, torch, wl, h):
     return res
 
 
+def max_over_ranks(dist, value, device):
+    """Largest value over all ranks (a job's time is that of its slowest rank)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, max_ms):
+    """Whole-job throughput: the steps all ranks took over the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
+
+
 def main():
     a = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -468,11 +501,8 @@ def main():
     total_ms = float(sum(step_ms))
     pass_ms, pass_n, launches = ctx.vds_timing_read()
     ctx.vds_timing(False)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * a.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = job_rate(world, a.steps, total_ms)
 
     # ---- end to end through the C ABI with host buffers -----------------
     q_h = torch.from_numpy(q0).pin_memory()
@@ -493,11 +523,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": world * a.steps / (e2e_ms / 1e3), "unit": UNIT,
+    e2e_ms = max_over_ranks(dist, e2e_ms, "cuda")
+    e2e = {"value": job_rate(world, a.steps, e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes)}
 
     if rank != 0:
@@ -527,8 +554,10 @@ def main():
 
     extras = None
     if not a.no_extras:
-        extras = _extras(ctx, vds, inputs, torch, wl, h, stream)
-        extras["surrogate"] = _extras_surrogate(ctx, vds, inputs, torch, wl, h)
+        which = set(a.extras.split(","))
+        extras = _extras(ctx, vds, inputs, torch, wl, h, stream, which)
+        if "surrogate" in which:
+            extras["surrogate"] = _extras_surrogate(ctx, vds, inputs, torch, wl, h)
 
     cpu = None
     if not a.no_cpu_baseline:
