@@ -17,9 +17,10 @@ extern "C" {
  * X: device, column-major (N s) x M snapshot matrix, one column per
  * (snapshot l, bond k) = q_k(t_l) flattened over rows (I, alpha).
  * C = X^T X (M x M) on the tensor cores: TF32 with one refinement step (each
- * FP32 value split into two TF32 parts, three products per pair), FP32 sums
- * over 512-row segments and FP64 across segments (relative error about 1e-7
- * of max|C|); C = V Lambda V^T by cyclic Jacobi in FP64; rank r = r_fixed if > 0, else
+ * FP32 value split into two TF32 parts, three products per pair), FP32
+ * tensor-memory sums over 32-row chunks, Kahan-compensated FP32 across
+ * chunks and FP64 across K splits; C = V Lambda V^T by cyclic Jacobi in FP64;
+ * rank r = r_fixed if > 0, else
  * the smallest r with sum_{i<=r} lambda_i >= energy * sum_i lambda_i,
  * capped at r_max (<= 64); Phi = X V_r Lambda_r^(-1/2), re-orthonormalised
  * by one Cholesky-QR pass; sign: the largest-magnitude entry of each column

@@ -1,18 +1,19 @@
 // gram_tc.cu -- the POD snapshot Gram C = X^T X (Sec. 2.3, method of
 // snapshots) on the 5th-generation tensor cores, TF32 with one refinement
-// step (3xTF32), FP64 across segments.
+// step (3xTF32), compensated FP32 across chunks, FP64 across K splits.
 //
 // Every FP32 snapshot value x is split into x_hi = tf32(x) and
 // x_lo = tf32(x - x_hi) (round to nearest), so x = x_hi + x_lo up to 2^-22 |x|,
 // and each product is formed as x_hi y_hi + x_hi y_lo + x_lo y_hi (the
 // dropped x_lo y_lo is below 2^-22 |x y|): three tcgen05.mma of kind::tf32
-// per K step, accumulating in FP32 in tensor memory.  The FP32 accumulator
-// covers one segment of 512 snapshot rows; after each segment the 128 x 128
-// tile is read back (tcgen05.ld) and added to FP64 registers (each of the 8
-// warps holds 64 columns of its 32 rows), so the FP32 rounding never
-// accumulates over more than 512 terms.  Per-CTA FP64 partial tiles are summed
-// over the K splits in a fixed order: the result does not depend on the
-// schedule.
+// per K step, accumulating in FP32 in tensor memory: x_hi y_hi in one
+// accumulator, the two correction products (2^-11 smaller) in another, so the
+// rounding of the large running sum is confined to the 4 MMAs of one 32-row
+// chunk.  After each chunk both accumulators are read back (tcgen05.ld) and
+// added into per-thread FP32 totals with Kahan compensation (each of the 8
+// warps holds 64 columns of its 32 rows) while the next chunk accumulates into
+// a second accumulator pair.  Per-CTA FP64 partial tiles are summed over the
+// K splits in a fixed order: the result does not depend on the schedule.
 //
 // Layout: X is column-major (Ns x M), so a tile row (one snapshot column) is
 // contiguous along K; chunks of 32 rows are staged by cp.async into the
@@ -29,12 +30,11 @@ namespace {
 constexpr int TG_M = 128;                 // C tile (rows = cols)
 constexpr int TG_KC = 32;                 // snapshot rows per chunk (128 B per tile row)
 constexpr int TG_ST = 3;                  // ring stages
-constexpr int TG_SEG = 16;                // chunks per FP32 segment (512 rows)
 constexpr int TG_NT = 256;                // threads (8 warps)
 constexpr int TG_OP = TG_M * TG_KC * 4;   // bytes of one operand tile (16 KB)
 constexpr int TG_STAGE = 4 * TG_OP;       // A hi, A lo, B hi, B lo
 constexpr size_t TG_SMEM = (size_t)TG_ST * TG_STAGE;
-constexpr uint32_t TG_TMEM_COLS = 128;
+constexpr uint32_t TG_TMEM_COLS = 512;     // two (big, small) accumulator pairs; one CTA per SM
 
 // Copy tile rows (snapshot columns col0..col0+127) x chunk rows
 // [kr0, kr0 + 32) of X into the canonical layout at dst; zero outside
@@ -112,12 +112,31 @@ __global__ void __launch_bounds__(TG_NT, 1)
   const uint32_t tmem = s_tmem;
   const uint32_t idesc = tc_idesc(TC_FMT_TF32, TG_M, TG_M);
   const uint32_t sbase = smem_u32(gsm);
-  // warp w reads TMEM lanes 32 (w % 4) .. (its rows) and columns 64 (w / 4) ..
+  // tensor memory: per chunk parity b, x_hi y_hi into columns 256 b and the
+  // two correction products into columns 256 b + 128; warp w reads lanes
+  // 32 (w % 4) .. (its rows) and columns 64 (w / 4) .. of both
   const uint32_t lane_base = (uint32_t)((warp & 3) * 32);
   const int col_half = (warp >> 2) * 64;
-  double acc[64];
+  float tot[64], cmp[64];
 #pragma unroll
-  for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+  for (int j = 0; j < 64; ++j) tot[j] = cmp[j] = 0.f;
+  // chunk c's FP32 tile into the compensated per-thread totals
+  auto flush = [&](int c) {
+    const uint32_t base = tmem + (lane_base << 16) + (uint32_t)((c & 1) * 256 + col_half);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t vb[16], vs[16];
+      tc_ld16(base + 16 * q, vb);
+      tc_ld16(base + 128 + 16 * q, vs);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float y = (__uint_as_float(vb[j]) + __uint_as_float(vs[j])) - cmp[16 * q + j];
+        const float t = tot[16 * q + j] + y;
+        cmp[16 * q + j] = (t - tot[16 * q + j]) - y;
+        tot[16 * q + j] = t;
+      }
+    }
+  };
 
   auto issue_loads = [&](int ch) {
     if (ch < nch) {
@@ -145,44 +164,41 @@ __global__ void __launch_bounds__(TG_NT, 1)
       tc_fence_after();
       const uint32_t a_hi = sbase + stage * TG_STAGE, a_lo = a_hi + TG_OP;
       const uint32_t b_hi = diag ? a_hi : a_hi + 2 * TG_OP, b_lo = diag ? a_lo : a_hi + 3 * TG_OP;
+      const uint32_t d_big = tmem + (uint32_t)((ch & 1) * 256), d_small = d_big + 128;
 #pragma unroll
       for (int k = 0; k < TG_KC / 8; ++k) {
         const uint32_t o = (uint32_t)k * 256u;  // 8 TF32 of K = two core matrices
-        const int first = (ch % TG_SEG == 0 && k == 0) ? 0 : 1;
-        tc_mma_tf32(tmem, tc_sdesc(a_lo + o), tc_sdesc(b_hi + o), idesc, first);
-        tc_mma_tf32(tmem, tc_sdesc(a_hi + o), tc_sdesc(b_lo + o), idesc, 1);
-        tc_mma_tf32(tmem, tc_sdesc(a_hi + o), tc_sdesc(b_hi + o), idesc, 1);
+        tc_mma_tf32(d_small, tc_sdesc(a_lo + o), tc_sdesc(b_hi + o), idesc, k > 0 ? 1 : 0);
+        tc_mma_tf32(d_small, tc_sdesc(a_hi + o), tc_sdesc(b_lo + o), idesc, 1);
+        tc_mma_tf32(d_big, tc_sdesc(a_hi + o), tc_sdesc(b_hi + o), idesc, k > 0 ? 1 : 0);
       }
       tc_commit(&bars[stage]);
     }
     last_committed = ch;
-    // end of a segment: wait for its MMAs, add the FP32 tile into FP64
-    if (ch % TG_SEG == TG_SEG - 1 || ch == nch - 1) {
-      const bool got = mbar_wait_bounded(&bars[stage], (uint32_t)((ch / TG_ST) & 1), VDS_WAIT_LIMIT_NS);
-      if (__syncthreads_or(!got)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        uint32_t v[16];
-        tc_ld16(tmem + (lane_base << 16) + (uint32_t)(col_half + 16 * c), v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) acc[16 * c + j] += (double)__uint_as_float(v[j]);
-      }
-      tc_fence_before();
-    }
-    // the stage refilled next was read by the MMAs of chunk ch - 1
-    if (ch >= 1 && ch + TG_ST - 1 < nch) {
+    // chunk ch - 1: its MMAs are done before its stage is refilled and its
+    // accumulators are read (chunk ch runs meanwhile on the other pair)
+    if (ch >= 1) {
       const int pc = ch - 1;
       const bool got = mbar_wait_bounded(&bars[pc % TG_ST], (uint32_t)((pc / TG_ST) & 1), VDS_WAIT_LIMIT_NS);
       if (__syncthreads_or(!got)) {
         ok = false;
         break;
       }
+      tc_fence_after();
+      flush(pc);
+      tc_fence_before();
     }
     issue_loads(ch + TG_ST - 1);
+  }
+  if (ok && nch > 0) {
+    const int pc = nch - 1;
+    const bool got = mbar_wait_bounded(&bars[pc % TG_ST], (uint32_t)((pc / TG_ST) & 1), VDS_WAIT_LIMIT_NS);
+    if (__syncthreads_or(!got)) {
+      ok = false;
+    } else {
+      tc_fence_after();
+      flush(pc);
+    }
   }
   cp_async_wait<0>();
   if (!ok) {
@@ -199,7 +215,7 @@ __global__ void __launch_bounds__(TG_NT, 1)
   const int row = (int)lane_base + lane;
   double *dst = part + (((size_t)blockIdx.y * nbt * nbt + blockIdx.x) * TG_M + row) * TG_M + col_half;
 #pragma unroll
-  for (int j = 0; j < 64; ++j) dst[j] = acc[j];
+  for (int j = 0; j < 64; ++j) dst[j] = (double)tot[j] - (double)cmp[j];
 }
 
 // C (M x M, FP64) = sum over K splits (in order) of the tile partials,

@@ -4,6 +4,7 @@
 #include <math.h>
 
 #include "pair.cuh"
+#include "pair_impl.cuh"
 
 namespace {
 __global__ void k_axpy(int n, const float *__restrict__ a, const float *__restrict__ b,
@@ -107,6 +108,8 @@ KParams make_kparams(const vds_params *p, int N, int D) {
   k.lnorm = -log((double)N) - 0.5 * D * log(2.0 * 3.14159265358979323846 * p->h * p->h);
   return k;
 }
+
+int pass_npad(int N) { return (N + vds_pair::TJ - 1) / vds_pair::TJ * vds_pair::TJ; }
 
 int pass_prep(vds_ctx *c, const KParams &kp, const float *base, const float *delta,
               const float *dir, float alpha, float *delta_out) {

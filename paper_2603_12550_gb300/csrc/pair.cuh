@@ -39,6 +39,10 @@ KParams make_kparams(const vds_params *p, int N, int D);
 // Records of y = base + delta (delta may be NULL) scaled by c, with w = 0,
 // padded to Npad with padding records.  If delta_out != NULL it receives
 // delta - alpha*dir (and the record is built from base + that).
+// Rows of the record array written by pass_prep for N particles: N rounded
+// up to the pair passes' j-tile, the rows beyond N far away (kernel value 0)
+// with w = 0.
+int pass_npad(int N);
 int pass_prep(vds_ctx *c, const KParams &kp, const float *base, const float *delta,
               const float *dir, float alpha, float *delta_out);
 

@@ -90,9 +90,10 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Round to TF32 (10 explicit mantissa bits), nearest, ties away from zero.
+// Round a finite FP32 value to TF32 (10 explicit mantissa bits), to nearest
+// with ties away from zero: add half a TF32 unit in the last place to the
+// magnitude bits (a carry moves into the exponent, as rounding up to the next
+// binade should) and clear the 13 bits below it.  Two integer operations.
 __device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }

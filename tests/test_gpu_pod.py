@@ -6,17 +6,21 @@ from the oracle's own FP64 trajectory (rounded to FP32), never from the GPU.
 
 Tolerances.  The GPU Gram runs on the tensor cores in TF32 with one
 refinement step (3xTF32: every product carries x_hi y_hi + x_hi y_lo +
-x_lo y_hi, relative error <= 3 * 2^-22) and FP32 sums over 512-row segments
-(at most 192 FP32 additions, relative error <= 192 * 2^-24 of the segment's
-sum of |products|), FP64 across segments.  A CPU emulation of exactly that
-arithmetic on these matrices gives Gram errors of 1-3e-7 of max|C| and
-eigenvalue errors <= 8e-8 lambda_1; the tests allow 1e-6 lambda_1.  A basis
-column t moves by at most ||dC|| / gap_t (Davis-Kahan), emulated at about
-1e-9 / (gap_t / lambda_1); the tests allow 2e-5 + 1e-8 / (gap_t / lambda_1)
-(the first term is the FP32 storage of Phi).  Phi^T Phi = I within 1e-6
-(Cholesky-QR in FP64).  X^H is checked against the oracle's X^H of the GPU's
-own basis (1e-5 relative), so it tests the X^H map, not the basis again; P
-and the lifted state against the oracle with the GPU basis, 1e-5 relative.
+x_lo y_hi, relative error <= 3 * 2^-22).  The tensor cores' FP32 accumulator
+rounds each MMA result into the running sum (toward zero, as measured: a
+512-row accumulation came out low by 4e-6); the kernel therefore keeps
+x_hi y_hi and the correction products in separate accumulators, reads them
+back after every 32-row chunk (4 MMAs into the large sum) and adds them into
+Kahan-compensated FP32 totals, FP64 across K splits.  A CPU emulation of that
+arithmetic (truncating FP32 accumulation) gives Gram errors of 1.5e-7 of
+max|C| on a 196608-row matrix and <= 1e-7 lambda_1 on the eigenvalues of the
+smaller matrices here; the tests allow 1e-6 lambda_1.  A basis column t moves
+by at most ||dC|| / gap_t (Davis-Kahan), emulated at about 1e-9 /
+(gap_t / lambda_1); the tests allow 2e-5 + 1e-8 / (gap_t / lambda_1) (the first
+term is the FP32 storage of Phi).  Phi^T Phi = I within 1e-6 (Cholesky-QR in
+FP64).  X^H is checked against the oracle's X^H of the GPU's own basis (1e-5
+relative), so it tests the X^H map, not the basis again; P and the lifted
+state against the oracle with the GPU basis, 1e-5 relative.
 """
 import numpy as np
 import pytest
@@ -128,3 +132,20 @@ def test_pod_bad_arguments(vds, ctx):
         ctx.pod_build(X, 31, 4, 3)  # Ns not a multiple of s
     with pytest.raises(vds.VdsError):
         ctx.pod_build(X, 30, 4, 3, r_max=65)
+
+
+def test_pod_full_size_spectrum(orc, vds, ctx):
+    # the 4-bead workload's snapshot matrix size (N s = 196608 rows, 200
+    # snapshots x 3 bonds = 600 columns) with a prescribed spectrum: the GPU
+    # eigenvalues against the FP64 oracle's (Gram and eigensolve in FP64 on
+    # the host); emulated error 1.5e-7 lambda_1, allowed 1e-6 lambda_1.
+    X = inputs.snapshot_matrix(196608, 600, 600, seed=7, decay=0.97)
+    Ns, M = X.shape
+    o = orc.pod_build(X.astype(np.float64), energy=0.9999, r_max=64)
+    basis, r = ctx.pod_build(_xdev(X), Ns, M, 3, energy=0.9999, r_max=64)
+    assert r == o["r"]
+    lam = basis.eigenvalues()
+    np.testing.assert_allclose(lam, o["lam"], rtol=0, atol=1e-6 * o["lam"][0])
+    Phi = basis.phi().cpu().numpy().astype(np.float64)
+    assert np.abs(Phi.T @ Phi - np.eye(r)).max() <= 1e-6
+    basis.free()
