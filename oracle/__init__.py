@@ -107,6 +107,7 @@ def _L():
                 "or_count_pairs_f32": [fp, L, I, ctypes.c_float, lp, lp],
                 "or_refresh_sums": [dp, L, I, D, dp, dp, I, I, dp, dp, dp],
                 "or_entropy_grad_rows": [dp, L, I, D, dp, lp, L, dp],
+                "or_density_rows": [dp, L, I, D, lp, L, dp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -151,6 +152,17 @@ def entropy_grad(q, h, rho=None):
     S, Sp = _d(np.empty((N, D)))
     _check(_L().or_entropy_grad(qp, N, D, h, rp, Sp))
     return S
+
+
+def density_rows(q, h, rows):
+    """rho_I for the particles in ``rows`` only (the same sums as density)."""
+    q, qp = _d(q)
+    N, D = q.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    rho, rp = _d(np.empty(len(rows)))
+    _check(_L().or_density_rows(qp, N, D, h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                len(rows), rp))
+    return rho
 
 
 def entropy_grad_rows(q, h, rho, rows):

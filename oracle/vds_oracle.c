@@ -468,6 +468,21 @@ int or_refresh_sums(const double *q, long N, int D, double h, const double *rho,
  * rows[0..nrows) index particles, S is nrows x D.  rho must hold the density
  * of every particle (the second term of Eq. model_DymRepPar needs all of
  * them). */
+/* rho_I (Eq. model_DeteParAppr without the normalisation) for the particles
+ * in rows only: the same sum as or_density, O(N) per row. */
+int or_density_rows(const double *q, long N, int D, double h, const long *rows, long nrows,
+                    double *rho) {
+  if (N < 0 || D < 1 || !(h > 0)) return OR_EARG;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long r = 0; r < nrows; ++r) {
+    const long I = rows[r];
+    double acc = 0.0;
+    for (long J = 0; J < N; ++J) acc += khat(q + I * D, q + J * D, D, h);
+    rho[r] = acc;
+  }
+  return OR_OK;
+}
+
 int or_entropy_grad_rows(const double *q, long N, int D, double h, const double *rho,
                          const long *rows, long nrows, double *S) {
   if (N < 0 || D < 1 || D > 64 || !(h > 0)) return OR_EARG;

@@ -107,3 +107,9 @@ def test_fene_domain(orc):
     p = orc.params(1, 3, spring=1, b=4.0, h=0.5, H=[2.0], kBT=0.0)
     _, g, _ = orc.energy_grad(q, p)
     np.testing.assert_allclose(g[0], 2.0 * q[0] / (1 - 1.25 / 4.0), rtol=1e-14)
+
+
+def test_density_rows_are_the_density(orc):
+    q = inputs.equilibrium_cloud(300, 3, 3, seed=4).astype(np.float64)
+    rows = np.array([0, 7, 299, 150])
+    np.testing.assert_array_equal(orc.density_rows(q, 0.8, rows), orc.density(q, 0.8)[rows])
