@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
-    ap.add_argument("--extras", default="implicit,pod,batched,surrogate",
+    ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate",
                     help="comma-separated subset of the secondary measurements to run")
     return ap.parse_args()
 
@@ -211,7 +211,36 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream, which):
         out["pod"] = _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed)
     if "batched" in which:
         out["batched"] = _extra_batched(ctx, vds, inputs, torch, timed)
+    if "dumbbell2d" in which:
+        out["dumbbell2d"] = _extra_dumbbell2d(ctx, vds, inputs, torch, timed)
     return out
+
+
+def _extra_dumbbell2d(ctx, vds, inputs, torch, timed):
+    """The 2D Hookean dumbbell, N=512, h=0.3, 50 implicit steps: through
+    vds_step (host-driven minimiser) and through a one-ensemble batch (device
+    state machine, one CUDA graph per round)."""
+    wl = inputs.WORKLOADS["dumbbell2d_n512"]
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
+    kap = inputs.shear_kappa(s, wl["rate"])
+    q0 = torch.from_numpy(inputs.equilibrium_cloud(N, nb, s, seed=wl["seed"])).cuda()
+    p = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=wl["h"], dt=wl["dt"], kappa=kap,
+                   scheme=1, tol=1e-6, jfloor=1e-9)
+    q = q0.clone()
+    ctx.vds_step(q, p, 2)
+    q = q0.clone()
+    sec1, its = timed(lambda: ctx.vds_step(q, p, wl["steps"], want_iters=True))
+    b = vds.Batch(ctx, [N], nb * s, p, [wl["h"]], kap[None])
+    qb = q0.clone()
+    b.step(qb, 2)
+    qb = q0.clone()
+    sec2, _ = timed(lambda: b.step(qb, wl["steps"]))
+    tau, _ = ctx.vds_stress(q, p)
+    tau_b, _ = ctx.vds_stress(qb, p)
+    b.free()
+    return {"workload": "dumbbell2d_n512", "steps": wl["steps"], "implicit_steps_per_s": wl["steps"] / sec1,
+            "batch_of_one_steps_per_s": wl["steps"] / sec2, "mean_gradient_evaluations": float(np.mean(its)),
+            "stress_rel_diff": float(np.linalg.norm(tau - tau_b) / np.linalg.norm(tau))}
 
 
 def _extra_implicit(ctx, vds, inputs, torch, wl, h, kap, timed):
@@ -256,6 +285,7 @@ def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
     out = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
                   "build_phases_ms": {"gram": ph_ms[4], "eigensolve": ph_ms[5], "basis": ph_ms[6]},
+                  "jacobi_sweeps": basis.sweeps(),
                   "eigenvalues_top": basis.eigenvalues()[:8].tolist(),
                   "mode2_steps_per_s": 240 / sec2, "mode2_refresh_every": 60,
                   "mode2_refresh_ms": rf_ms[3] / max(1, rf_n[3]), "mode2_refreshes": rf_n[3],

@@ -42,6 +42,10 @@ VDS_API int pod_load(vds_ctx *ctx, const float *phi, long Ns, int r, int s, cons
 VDS_API int pod_info(const pod_basis *b, int *r, int *ld, const float **phi_dev,
              long *Ns);
 VDS_API int pod_eigenvalues(const pod_basis *b, double *lam_host, int M);
+/* Number of cyclic Jacobi sweeps pod_build ran (0 for pod_load, VDS_EARG for
+ * NULL); the eigensolve stops when every off-diagonal entry is below
+ * 1e-11 ||C||_F or the off-diagonal norm stops falling. */
+VDS_API int pod_sweeps(const pod_basis *b);
 VDS_API int pod_xh(const pod_basis *b, double *xh_host);
 /* p_{k:} = Phi^T q_{k:} (Eq. model_pq).  q: device N x D; p: device r x nb
  * row-major (p[t*nb + k]). */

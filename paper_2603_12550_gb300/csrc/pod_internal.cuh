@@ -8,6 +8,7 @@ struct pod_basis {
   int device = 0;
   long Ns = 0;
   int M = 0, r = 0, ld = 0, s = 0;
+  int sweeps = 0;              // Jacobi sweeps of the eigensolve (0 for pod_load)
   float *phi = nullptr;        // device, Ns x ld row-major (columns >= r zero)
   double *lam = nullptr;       // host, M eigenvalues descending
   double *xh = nullptr;        // host, r x r

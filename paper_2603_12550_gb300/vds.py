@@ -83,6 +83,7 @@ _SIGS = {
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
     "pod_build": ([_vp, _vp, _l, _i, _i, _d, _i, _i, _dp, ctypes.POINTER(_vp), _ip], _i),
     "pod_load": ([_vp, _vp, _l, _i, _i, _dp, ctypes.POINTER(_vp)], _i),
+    "pod_sweeps": ([_vp], _i),
     "pod_info": ([_vp, _ip, _ip, ctypes.POINTER(_vp), ctypes.POINTER(_l)], _i),
     "pod_eigenvalues": ([_vp, _dp, _i], _i),
     "pod_xh": ([_vp, _dp], _i),
@@ -419,6 +420,9 @@ class PodBasis:
         r, ld, phi, Ns = ctypes.c_int(), ctypes.c_int(), _vp(), ctypes.c_long()
         _check(lib.pod_info(self.h, ctypes.byref(r), ctypes.byref(ld), ctypes.byref(phi), ctypes.byref(Ns)))
         return dict(r=r.value, ld=ld.value, phi=phi.value, Ns=Ns.value)
+
+    def sweeps(self):
+        return lib.pod_sweeps(self.h)
 
     def eigenvalues(self):
         buf = (ctypes.c_double * self.M)()
