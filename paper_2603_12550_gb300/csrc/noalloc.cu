@@ -75,17 +75,17 @@ int setup_device(int dev, DevState **out) {
 
 // One pair pass into the fixed partial buffer: the stream-K grid is shrunk
 // until the partial sums fit.
-template <int D, int RI, bool GRAD>
+template <int D, int RI, int NT, bool GRAD>
 int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double *part, int *err,
             Sched &sc) {
   using namespace vds_pair;
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
-  constexpr int TI = NT_PAIR * RI;
+  constexpr int TI = NT * RI;
   const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
   int occ = 0;
-  VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<D, RI, GRAD>, NT_PAIR, smem));
+  VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<D, RI, NT, GRAD>, NT, smem));
   if (occ < 1) occ = 1;
   sc.TI = TI;
   sc.Npad = (N + TJ - 1) / TJ * TJ;
@@ -108,7 +108,7 @@ int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double 
     if (G < 1) G = 1;
   }
   if ((size_t)sc.n_itiles * sc.maxseg * TI * ACC * sizeof(double) > kPartBytes) return VDS_ESIZE;
-  k_pair<D, RI, GRAD><<<sc.G, NT_PAIR, smem, st>>>(rec, sc, part, err);
+  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, st>>>(rec, sc, part, err);
   VDS_CUDA_TRY(cudaGetLastError());
   return VDS_OK;
 }
@@ -131,13 +131,13 @@ int na_energy_grad(const DevState &s, const float *q, const KParams &kp, double 
   k_prep<D><<<(Npad + 255) / 256, 256, 0, st>>>(N, Npad, kp.c, q, nullptr, nullptr, 0.f, nullptr, rec);
   VDS_CUDA_TRY(cudaGetLastError());
   Sched sd, sg;
-  VDS_TRY((na_pair<D, PairCfg<D>::RI_DENS, false>(s, N, st, rec, part, err, sd)));
+  VDS_TRY((na_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(s, N, st, rec, part, err, sd)));
   const int nb = (N + NT_FIN - 1) / NT_FIN;
   k_dens_finish<D><<<nb, NT_FIN, 0, st>>>(sd, part, rec, rho, kp, E ? 1 : 0, q, nullptr, nullptr, nullptr,
                                          red, ticket + TK_DENS, scal, err);
   VDS_CUDA_TRY(cudaGetLastError());
   if (g) {
-    VDS_TRY((na_pair<D, PairCfg<D>::RI_GRAD, true>(s, N, st, rec, part, err, sg)));
+    VDS_TRY((na_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(s, N, st, rec, part, err, sg)));
     k_grad_finish<D, GM_OUT><<<nb, NT_FIN, 0, st>>>(sg, part, rec, kp, g, q, nullptr, nullptr, nullptr,
                                                    nullptr, red, ticket + TK_GRAD, scal, err);
     VDS_CUDA_TRY(cudaGetLastError());

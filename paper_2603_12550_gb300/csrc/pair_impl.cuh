@@ -21,42 +21,36 @@
 namespace vds_pair {
 
 // Tile shape (overridable at build time for tuning sweeps).
-#ifndef VDS_PAIR_NT
-#define VDS_PAIR_NT 256
-#endif
 #ifndef VDS_PAIR_TJ
 #define VDS_PAIR_TJ 256
 #endif
 #ifndef VDS_PAIR_NSTAGE
 #define VDS_PAIR_NSTAGE 3
 #endif
-#ifndef VDS_PAIR_RI_DENS
-#define VDS_PAIR_RI_DENS 4
-#endif
-#ifndef VDS_PAIR_RI_GRAD_LARGE_D
-#define VDS_PAIR_RI_GRAD_LARGE_D 4
-#endif
-constexpr int NT_PAIR = VDS_PAIR_NT;     // threads per CTA
 constexpr int TJ = VDS_PAIR_TJ;          // records per j-tile (= j-chunk)
 constexpr int NSTAGE = VDS_PAIR_NSTAGE;  // shared-memory ring depth
 
+// Threads per CTA and particles per thread of each pass.  D = 9 takes the
+// fastest shapes of a sweep on GB300 at N = 65536 (density 512 x 4, gradient
+// 384 x 3: 2.46 + 3.86 ms against 2.51 + 3.99 ms for 256 x 4 in both); other
+// D keep 256 threads, 4 particles per thread, 2 for the gradient above D = 9
+// (255 registers).
 template <int D>
 struct PairCfg {
-  static constexpr int RI_DENS = VDS_PAIR_RI_DENS;
-  // (chosen by a sweep on GB300 at N=65536, D=9; large D keeps 2 to stay
-  // within 255 registers)
-  static constexpr int RI_GRAD = (D <= 6) ? 4 : (D <= 9 ? VDS_PAIR_RI_GRAD_LARGE_D : 2);
+  static constexpr int NT_DENS = (D == 9) ? 512 : 256;
+  static constexpr int RI_DENS = 4;
+  static constexpr int NT_GRAD = (D == 9) ? 384 : 256;
+  static constexpr int RI_GRAD = (D <= 6) ? 4 : (D == 9 ? 3 : (D <= 9 ? 4 : 2));
 };
 
 // ------------------------------------------------------------- pair kernel
 
-template <int D, int RI, bool GRAD>
-__global__ void __launch_bounds__(NT_PAIR)
+template <int D, int RI, int NT, bool GRAD>
+__global__ void __launch_bounds__(NT)
     k_pair(const float *__restrict__ rec, Sched sc, double *__restrict__ part,
            int *__restrict__ err) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
-  constexpr int NT = NT_PAIR;
   constexpr uint32_t TILE_FLOATS = TJ * DP;
   constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
   extern __shared__ __align__(128) float tiles[];  // NSTAGE * TILE_FLOATS
@@ -606,19 +600,21 @@ __global__ void k_flow(KParams kp, const float *__restrict__ q, float *__restric
 
 // ------------------------------------------------------------ host plumbing
 
-template <int D, int RI, bool GRAD>
+template <int D, int RI, int NT, bool GRAD>
 int launch_pair(vds_ctx *c, int N, Sched &sc) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
-  constexpr int TI = NT_PAIR * RI;
+  constexpr int TI = NT * RI;
   const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
-  static int occ = -1;
-  if (occ < 0) {
+  // per device: the attribute is a property of the function on that device
+  static int occ_dev[VDS_MAX_DEVICES] = {};
+  int &occ = occ_dev[c->device < VDS_MAX_DEVICES ? c->device : 0];
+  if (occ <= 0 || c->device >= VDS_MAX_DEVICES) {
     // large D needs more than the default 48 KB of dynamic shared memory
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     int o = 0;
-    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, GRAD>, NT_PAIR, smem));
+    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, NT, GRAD>, NT, smem));
     occ = o > 0 ? o : 1;
   }
   sc.TI = TI;
@@ -638,7 +634,7 @@ int launch_pair(vds_ctx *c, int N, Sched &sc) {
   VDS_TRY(vds_ensure(c, c->part, (size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double)));
   const int pk = GRAD ? PK_GRADIENT : PK_DENSITY;
   VDS_TRY(vds_time_begin(c, pk));
-  k_pair<D, RI, GRAD><<<sc.G, NT_PAIR, smem, c->stream>>>((const float *)c->rec.ptr, sc,
+  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, sc,
                                                            (double *)c->part.ptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   VDS_TRY(vds_time_end(c, pk));
@@ -662,7 +658,7 @@ template <int D>
 int density_impl(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
                  const float *ybase, const float *ydelta, const float *qa, const float *qb) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, false>(c, kp.N, sc)));
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   k_dens_finish<D><<<nb, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, (float *)c->rec.ptr,
@@ -678,7 +674,7 @@ template <int D>
 int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,
               const float *ydelta, const float *qa, const float *qb, float *q_io) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, true>(c, kp.N, sc)));
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(c, kp.N, sc)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   const double *pp = (const double *)c->part.ptr;

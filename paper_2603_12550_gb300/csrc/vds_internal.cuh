@@ -124,6 +124,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 #define VDS_WAIT_LIMIT_NS 2000000000ull  // 2 s
 
+// Per-device caches of launch attributes cover devices 0 .. VDS_MAX_DEVICES-1.
+constexpr int VDS_MAX_DEVICES = 64;
+
 // ------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum_d(double v) {
