@@ -32,9 +32,15 @@ constexpr int GM = 128;   // rows per CTA tile
 constexpr int KC = 64;    // K per chunk
 constexpr int TMEM_COLS = 128;
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + expf(-z)); }
+// Logistic sigma(z) = 1 / (1 + e^-z) with the hardware 2^x (e^-z = 2^(-z log2 e))
+// and a fast reciprocal: about 1e-7 relative, far below the BF16 rounding of
+// the activations it feeds.
+__device__ __forceinline__ float sigmoid_f(float z) {
+  return __fdividef(1.f, 1.f + ex2_approx(-1.4426950408889634f * z));
+}
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 __device__ __forceinline__ float dsilu_f(float z) {
-  const float s = 1.f / (1.f + expf(-z));
+  const float s = sigmoid_f(z);
   return s * (1.f + z * (1.f - s));
 }
 
@@ -55,7 +61,7 @@ struct Epi {
 };
 
 constexpr int GBN = 128;   // columns of C per CTA
-constexpr int GST = 4;     // pipeline stages (K chunks in flight)
+constexpr int GNT = 256;   // threads: warps w and w + 4 share TMEM lanes 32 (w % 4), split the columns
 constexpr int GSTAGE = GM * KC * 2 + GBN * KC * 2;  // bytes per stage (A 16 KB + B <= 16 KB)
 
 // Asynchronous copy of a rows_tile x 64 chunk (rows beyond nvalid zero-filled)
@@ -74,12 +80,14 @@ __device__ __forceinline__ void load_chunk_async(uint32_t dst, const bf16 *__res
   }
 }
 
-// C tile [128 rows x BN cols] = A[m0:, K-split] . B[n0:n0+BN, K-split]^T
-__global__ void __launch_bounds__(128)
+// C tile [128 rows x BN cols] = A[m0:, K-split] . B[n0:n0+BN, K-split]^T,
+// GS chunks of K in flight (2 when K is short: three CTAs fit on an SM).
+template <int GS>
+__global__ void __launch_bounds__(GNT)
     k_gemm_tn(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int N, int Ksplit,
               Epi ep, int *err) {
   extern __shared__ __align__(1024) uint8_t gsm[];
-  __shared__ __align__(8) uint64_t bars[GST];
+  __shared__ __align__(8) uint64_t bars[GS];
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * GM;
@@ -90,7 +98,7 @@ __global__ void __launch_bounds__(128)
     tc_alloc(&s_tmem, TMEM_COLS);
   }
   if (tid == 0) {
-    for (int k = 0; k < GST; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < GS; ++k) mbar_init(&bars[k], 1);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -103,75 +111,121 @@ __global__ void __launch_bounds__(128)
   const uint32_t sbase = smem_u32(gsm);
   auto issue_loads = [&](int ch) {
     if (ch < nch) {
-      const uint32_t st = sbase + (ch % GST) * GSTAGE;
+      const uint32_t st = sbase + (ch % GS) * GSTAGE;
       load_chunk_async(st, A, lda, m0, avalid, GM, kbase + ch * KC);
       load_chunk_async(st + GM * KC * 2, B, ldb, n0, BN, BN, kbase + ch * KC);
     }
     cp_async_commit();
   };
-  for (int ch = 0; ch < GST - 1; ++ch) issue_loads(ch);
+  for (int ch = 0; ch < GS - 1; ++ch) issue_loads(ch);
   bool ok = true;
   for (int ch = 0; ch < nch; ++ch) {
-    cp_async_wait<GST - 2>();
+    cp_async_wait<GS - 2>();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a0 = sbase + (ch % GST) * GSTAGE, b0 = a0 + GM * KC * 2;
+      const uint32_t a0 = sbase + (ch % GS) * GSTAGE, b0 = a0 + GM * KC * 2;
 #pragma unroll
       for (int k = 0; k < KC / 16; ++k)
         tc_mma_bf16(tmem, tc_sdesc(a0 + k * 256), tc_sdesc(b0 + k * 256), idesc, (ch > 0 || k > 0) ? 1 : 0);
-      tc_commit(&bars[ch % GST]);
+      tc_commit(&bars[ch % GS]);
     }
     // the stage refilled next was read by the MMAs of chunk ch-1
-    if (ch >= 1 && ch + GST - 1 < nch) {
+    if (ch >= 1 && ch + GS - 1 < nch) {
       const int pc = ch - 1;
-      const bool got = mbar_wait_bounded(&bars[pc % GST], (uint32_t)((pc / GST) & 1), VDS_WAIT_LIMIT_NS);
+      const bool got = mbar_wait_bounded(&bars[pc % GS], (uint32_t)((pc / GS) & 1), VDS_WAIT_LIMIT_NS);
       if (__syncthreads_or(!got)) {
         ok = false;
         break;
       }
     }
-    issue_loads(ch + GST - 1);
+    issue_loads(ch + GS - 1);
   }
   cp_async_wait<0>();
   if (ok && nch > 0) {
     const int last = nch - 1;
-    const bool got = mbar_wait_bounded(&bars[last % GST], (uint32_t)((last / GST) & 1), VDS_WAIT_LIMIT_NS);
+    const bool got = mbar_wait_bounded(&bars[last % GS], (uint32_t)((last / GS) & 1), VDS_WAIT_LIMIT_NS);
     if (__syncthreads_or(!got)) ok = false;
   }
   tc_fence_after();
   if (!ok) {
     if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
   } else {
-    const int row = m0 + warp * 32 + lane;
+    // warp w: rows 32 (w % 4) + lane, columns [cb, ce) of the tile
+    const int row = m0 + (warp & 3) * 32 + lane;
     const bool vrow = row < ep.rows;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
+    const int half = ((BN + 31) / 32) * 16;
+    const int cb = (warp >> 2) * half, ce = min(BN, cb + half);
+    for (int c0 = cb; c0 < ce; c0 += 16) {
       uint32_t v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
       if (!vrow) continue;
+      const int colb = n0 + c0;
+      const bool full = colb + 16 <= ep.ncols;
+      float a[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int col = n0 + c0 + j;
-        if (col >= ep.ncols) continue;
-        float a = __uint_as_float(v[j]);
-        if (ep.mode == EPI_F32) {
-          if (ep.bias) a += ep.bias[col];
-          ep.outf[(long long)blockIdx.y * ep.split_stride + (size_t)row * ep.ldc + col] = a;
-        } else if (ep.mode == EPI_SILU) {
-          const float z = a + (ep.bias ? ep.bias[col] : 0.f);
-          if (ep.outf) ep.outf[(size_t)row * ep.ldc + col] = z;
-          const bf16 hv = __float2bfloat16_rn(silu_f(z));
-          ep.h[(size_t)row * ep.ldc + col] = hv;
-          if (ep.ht) ep.ht[(size_t)col * ep.ldt + row] = hv;
+      for (int j = 0; j < 16; ++j) a[j] = __uint_as_float(v[j]);
+      if (ep.mode == EPI_F32) {
+        float *o = ep.outf + (long long)blockIdx.y * ep.split_stride + (size_t)row * ep.ldc + colb;
+        if (full && (ep.ldc & 3) == 0 && (ep.split_stride & 3) == 0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (ep.bias) a[j] += ep.bias[colb + j];
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(o + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
         } else {
-          const float dz = a * dsilu_f(ep.zin[(size_t)row * ep.ldc + col]);
-          if (ep.outf) ep.outf[(size_t)row * ep.ldc + col] = dz;
-          const bf16 hv = __float2bfloat16_rn(dz);
-          ep.h[(size_t)row * ep.ldc + col] = hv;
-          if (ep.ht) ep.ht[(size_t)col * ep.ldt + row] = hv;
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (colb + j < ep.ncols) o[j] = a[j] + (ep.bias ? ep.bias[colb + j] : 0.f);
         }
+        continue;
+      }
+      float y[16];
+      if (ep.mode == EPI_SILU) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float z = a[j] + ((ep.bias && (full || colb + j < ep.ncols)) ? ep.bias[colb + j] : 0.f);
+          a[j] = z;
+          y[j] = silu_f(z);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float zin = (full || colb + j < ep.ncols) ? ep.zin[(size_t)row * ep.ldc + colb + j] : 0.f;
+          y[j] = a[j] * dsilu_f(zin);
+          a[j] = y[j];
+        }
+      }
+      // FP32 copy (z, or dz) and BF16 activations, row-major; transposed copy
+      if (full && (ep.ldc & 7) == 0) {
+        if (ep.outf) {
+          float *o = ep.outf + (size_t)row * ep.ldc + colb;
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(o + j) = make_float4(a[j], a[j + 1], a[j + 2], a[j + 3]);
+        }
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const __nv_bfloat162 t = __floats2bfloat162_rn(y[2 * j], y[2 * j + 1]);
+          pk[j] = *reinterpret_cast<const uint32_t *>(&t);
+        }
+        uint4 *hp = reinterpret_cast<uint4 *>(ep.h + (size_t)row * ep.ldc + colb);
+        hp[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        hp[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (colb + j >= ep.ncols) continue;
+          if (ep.outf) ep.outf[(size_t)row * ep.ldc + colb + j] = a[j];
+          ep.h[(size_t)row * ep.ldc + colb + j] = __float2bfloat16_rn(y[j]);
+        }
+      }
+      if (ep.ht) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (colb + j < ep.ncols) ep.ht[(size_t)(colb + j) * ep.ldt + row] = __float2bfloat16_rn(y[j]);
       }
     }
   }
@@ -181,7 +235,6 @@ __global__ void __launch_bounds__(128)
     tc_dealloc(tmem, TMEM_COLS);
 }
 
-constexpr size_t GEMM_SMEM = (size_t)GST * GSTAGE;
 
 // ------------------------------------------------------------ small kernels
 
@@ -355,14 +408,20 @@ struct Dev {
 
 int gemm(vds_ctx *c, const bf16 *A, int lda, const bf16 *B, int ldb, int rows, int N, int K, int splits,
          const Epi &ep) {
-  static bool attr = false;
-  if (!attr) {
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEMM_SMEM));
-    attr = true;
-  }
   if (N % 16 != 0 || N < 16 || N > 256 || K % (KC * splits) != 0) return VDS_EARG;
+  // per device: the shared-memory attribute is a property of the function on that device
+  static bool attr[VDS_MAX_DEVICES] = {};
+  if (c->device >= VDS_MAX_DEVICES || !attr[c->device]) {
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * GSTAGE));
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * GSTAGE));
+    if (c->device < VDS_MAX_DEVICES) attr[c->device] = true;
+  }
   dim3 grid((rows + GM - 1) / GM, splits, (N + GBN - 1) / GBN);
-  k_gemm_tn<<<grid, 128, GEMM_SMEM, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
+  const int nch = K / splits / KC;
+  if (nch <= 4)
+    k_gemm_tn<2><<<grid, GNT, 2 * GSTAGE, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
+  else
+    k_gemm_tn<4><<<grid, GNT, 4 * GSTAGE, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;

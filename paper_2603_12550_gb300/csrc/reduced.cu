@@ -153,17 +153,90 @@ __global__ void k_score_vel(KParams kp, const float *__restrict__ q, const float
   }
 }
 
-// sums over the checked particles (every stride-th) of |s - mean s - S|^2 and |S|^2
+// The exact entropy gradient S of the checked particles only (every
+// stride-th, nrows of them) from records that carry w = 1/rho of all N: the
+// gradient pair pass restricted to those rows.  grid.x covers the rows (128
+// per CTA), grid.y splits the j range into segments whose FP64 partials are
+// summed in a fixed order by k_grad_rows_sum; inside a segment FP32 sums per
+// 128-record tile with Kahan compensation across tiles.
+constexpr int GR_NT = 128;
+constexpr int GR_TJ = 128;
+
+template <int D>
+__global__ void __launch_bounds__(GR_NT)
+    k_grad_rows(const float *__restrict__ rec, int Npad, int stride, int nrows, int jseg,
+                double *__restrict__ part) {
+  constexpr int DP = Rec<D>::DP;
+  __shared__ __align__(16) float srec[GR_TJ * DP];
+  const int r = blockIdx.x * GR_NT + threadIdx.x;
+  const long i = (long)(r < nrows ? r : nrows - 1) * stride;
+  float xi[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) xi[d] = rec[i * DP + d];
+  const float wi = rec[i * DP + D];
+  float sum[D], cmp[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) sum[d] = cmp[d] = 0.f;
+  const int j0 = blockIdx.y * jseg, j1 = min(Npad, j0 + jseg);
+  for (int jt = j0; jt < j1; jt += GR_TJ) {
+    __syncthreads();
+    const float4 *src = reinterpret_cast<const float4 *>(rec + (size_t)jt * DP);
+    float4 *dst = reinterpret_cast<float4 *>(srec);
+    for (int e = threadIdx.x; e < GR_TJ * DP / 4; e += GR_NT) dst[e] = src[e];
+    __syncthreads();
+    float acc[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) acc[d] = 0.f;
+#pragma unroll 2
+    for (int j = 0; j < GR_TJ; ++j) {
+      const float *rj = srec + j * DP;
+      float dd[D], r2 = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        dd[d] = xi[d] - rj[d];
+        r2 = fmaf(dd[d], dd[d], r2);
+      }
+      const float u = ex2_approx(-r2) * (wi + rj[D]);
+#pragma unroll
+      for (int d = 0; d < D; ++d) acc[d] = fmaf(u, dd[d], acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const float y = acc[d] - cmp[d];
+      const float t = sum[d] + y;
+      cmp[d] = (t - sum[d]) - y;
+      sum[d] = t;
+    }
+  }
+  if (r >= nrows) return;
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    part[((size_t)blockIdx.y * nrows + r) * D + d] = (double)sum[d] - (double)cmp[d];
+}
+
+// S_rows = -sfac * (sum over the j segments, in order); sfac = 1/(h^2 c)
+__global__ void k_grad_rows_sum(const double *__restrict__ part, int nseg, int nrows, int D, double sfac,
+                                float *__restrict__ S) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nrows * D) return;
+  double v = 0.0;
+  for (int k = 0; k < nseg; ++k) v += part[(size_t)k * nrows * D + e];
+  S[e] = (float)(-sfac * v);
+}
+
+// sums over the checked particles of |s - mean s - S|^2 and |S|^2, with S
+// given for the checked rows only (row r is particle r * stride)
 __global__ void k_check_err(const float *__restrict__ sc, const double *__restrict__ smean,
-                            const float *__restrict__ S, int N, int D, int stride, double *__restrict__ out) {
+                            const float *__restrict__ S, int nrows, int D, int stride, double *__restrict__ out) {
   __shared__ double sh[2][256];
   double e = 0.0, n = 0.0;
-  for (int r = threadIdx.x; (long)r * stride < N; r += blockDim.x) {
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
     const long i = (long)r * stride;
     for (int a = 0; a < D; ++a) {
-      const double d = (double)sc[i * D + a] - smean[a] - (double)S[i * D + a];
+      const double Sv = (double)S[(size_t)r * D + a];
+      const double d = (double)sc[i * D + a] - smean[a] - Sv;
       e += d * d;
-      n += (double)S[i * D + a] * S[i * D + a];
+      n += Sv * Sv;
     }
   }
   sh[0][threadIdx.x] = e;
@@ -179,6 +252,50 @@ __global__ void k_check_err(const float *__restrict__ sc, const double *__restri
   if (threadIdx.x == 0) {
     out[0] = sh[0][0];
     out[1] = sh[1][0];
+  }
+}
+
+// j segments of the checked-row gradient: about four CTAs per SM over the row
+// blocks, segment length a multiple of the tile
+void grad_rows_split(const vds_ctx *c, int N, int nrows, int &nseg, int &jseg) {
+  const int Npad = pass_npad(N);
+  const int rb = (nrows + GR_NT - 1) / GR_NT;
+  nseg = (4 * c->num_sms + rb - 1) / rb;
+  jseg = (Npad + nseg - 1) / nseg;
+  jseg = (jseg + GR_TJ - 1) / GR_TJ * GR_TJ;
+  nseg = (Npad + jseg - 1) / jseg;
+}
+
+size_t grad_rows_part_bytes(const vds_ctx *c, int N, int nrows, int D) {
+  int nseg, jseg;
+  grad_rows_split(c, N, nrows, nseg, jseg);
+  return (size_t)nseg * nrows * D * sizeof(double);
+}
+
+template <int D>
+int grad_rows_impl(vds_ctx *c, const KParams &kS, int stride, int nrows, double *part, float *Srows) {
+  const int Npad = pass_npad(kS.N);
+  const int rb = (nrows + GR_NT - 1) / GR_NT;
+  int nseg, jseg;
+  grad_rows_split(c, kS.N, nrows, nseg, jseg);
+  k_grad_rows<D><<<dim3(rb, nseg), GR_NT, 0, c->stream>>>((const float *)c->rec.ptr, Npad, stride, nrows, jseg,
+                                                          part);
+  k_grad_rows_sum<<<(nrows * D + 255) / 256, 256, 0, c->stream>>>(part, nseg, nrows, D, kS.sfac, Srows);
+  VDS_CUDA_TRY(cudaGetLastError());
+  c->launches += 2;
+  return VDS_OK;
+}
+
+int grad_rows(vds_ctx *c, const KParams &kS, int stride, int nrows, double *part, float *Srows) {
+  switch (kS.D) {
+    case 2: return grad_rows_impl<2>(c, kS, stride, nrows, part, Srows);
+    case 3: return grad_rows_impl<3>(c, kS, stride, nrows, part, Srows);
+    case 4: return grad_rows_impl<4>(c, kS, stride, nrows, part, Srows);
+    case 6: return grad_rows_impl<6>(c, kS, stride, nrows, part, Srows);
+    case 8: return grad_rows_impl<8>(c, kS, stride, nrows, part, Srows);
+    case 9: return grad_rows_impl<9>(c, kS, stride, nrows, part, Srows);
+    case 12: return grad_rows_impl<12>(c, kS, stride, nrows, part, Srows);
+    default: return VDS_EARG;
   }
 }
 
@@ -346,6 +463,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   const int stride = check_n >= N ? 1 : N / check_n;
+  const int nrows = (N + stride - 1) / stride;
   double worst = 0.0;
   int nfall = 0;
   for (int step = 0; step < nsteps; ++step) {
@@ -357,10 +475,17 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     c->launches += 2;
     bool exact = false;
     if (check_every > 0 && step % check_every == 0) {
+      // full density (every 1/rho_J enters S_I), gradient of the checked rows
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
       VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr));
-      VDS_TRY(pass_grad(c, kS, GM_OUT, Sx, qt, nullptr, nullptr, nullptr, nullptr));
-      k_check_err<<<1, 256, 0, c->stream>>>(sbuf, smean, Sx, N, D, stride, errs);
+      // compact exact S of the checked rows (after the FP64 segment partials)
+      // in the shared scratch, taken afresh at every check
+      const size_t rows_bytes = ((size_t)nrows * D * sizeof(float) + 255) / 256 * 256;
+      VDS_TRY(vds_ensure(c, c->gbuf, rows_bytes + grad_rows_part_bytes(c, N, nrows, D)));
+      float *Srows = (float *)c->gbuf.ptr;
+      double *rows_part = (double *)((char *)c->gbuf.ptr + rows_bytes);
+      VDS_TRY(grad_rows(c, kS, stride, nrows, rows_part, Srows));
+      k_check_err<<<1, 256, 0, c->stream>>>(sbuf, smean, Srows, nrows, D, stride, errs);
       VDS_CUDA_TRY(cudaGetLastError());
       ++c->launches;
       double h_err[2];
@@ -369,6 +494,8 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
       const double rel = h_err[1] > 0.0 ? sqrt(h_err[0] / h_err[1]) : 0.0;
       if (rel > worst) worst = rel;
       if (!(rel <= check_tol)) {
+        // fall back: the exact gradient of every particle for this step
+        VDS_TRY(pass_grad(c, kS, GM_OUT, Sx, qt, nullptr, nullptr, nullptr, nullptr));
         exact = true;
         ++nfall;
       }
