@@ -258,11 +258,25 @@ static int step_implicit(vds_ctx *c, float *q, const KParams &kp, const vds_para
   float *qs = vec(c, 0, nd), *d0 = vec(c, 1, nd), *d1 = vec(c, 2, nd), *dir = vec(c, 3, nd);
   for (int n = 0; n < nsteps; ++n) {
     VDS_TRY(pass_flow(c, kp, q, qs));
-    VDS_CUDA_TRY(cudaMemsetAsync(d0, 0, nd * sizeof(float), c->stream));
-    VDS_TRY(pass_prep(c, kp, qs, d0, nullptr, 0.f, nullptr));
-    VDS_TRY(pass_density(c, kp, nullptr, true, qs, d0, d0, nullptr));
-    VDS_TRY(read_scalars(c));
-    double J = c->h_scal[SC_E];
+    // start from y = q* + (the previous step's solution - its q*): the
+    // correction varies slowly between steps, so the minimiser usually needs
+    // one gradient evaluation fewer; q* itself for the first step of a call or
+    // when that start leaves the FENE domain
+    double J = 0.0;
+    bool warm = n > 0;
+    for (;;) {
+      if (!warm) VDS_CUDA_TRY(cudaMemsetAsync(d0, 0, nd * sizeof(float), c->stream));
+      VDS_TRY(pass_prep(c, kp, qs, d0, nullptr, 0.f, nullptr));
+      VDS_TRY(pass_density(c, kp, nullptr, true, qs, d0, d0, nullptr));
+      const int st = read_scalars(c);
+      if (st == VDS_EDOMAIN && warm) {
+        warm = false;
+        continue;
+      }
+      VDS_TRY(st);
+      J = c->h_scal[SC_E];
+      break;
+    }
     int it = 0;
     bool converged = false;
     while (it < p->max_iter) {
