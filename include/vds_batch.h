@@ -56,6 +56,17 @@ VDS_API int vds_batch_energy_grad(vds_ctx *ctx, vds_batch *b, const float *q_all
  * and step; status of the first failing ensemble is returned. */
 VDS_API int vds_batch_step(vds_ctx *ctx, vds_batch *b, float *q_all, int nsteps, int *iters_out);
 
+/* Micro-macro coupling (Sec. 1: one ensemble per grid point of a
+ * macroscopic solver).  vds_batch_stress: the polymer stress of every
+ * ensemble, tau_e = (1/N_e) sum_I sum_k q_k (x) grad Psi_k (as vds_stress),
+ * from q_all (device, total x D) into tau (host, E x s x s doubles, row-major
+ * per ensemble); FP64 sums in a fixed order; synchronises.
+ * vds_batch_set_kappa: new velocity gradients for every ensemble (host,
+ * E x s x s doubles, qdot = kappa q), e.g. the macroscopic velocity field at
+ * the ensembles' grid points, used from the next step on. */
+VDS_API int vds_batch_stress(vds_ctx *ctx, vds_batch *b, const float *q_all, double *tau);
+VDS_API int vds_batch_set_kappa(vds_ctx *ctx, vds_batch *b, const double *kappa);
+
 /* Tile autotuner (no counterpart in the paper).  The batched pair kernel has
  * VDS_BATCH_CONFIGS candidate shapes: config k runs 128 << (k >> 1) threads
  * per CTA with 2 << (k & 1) particles per thread, so a work item's i-tile is

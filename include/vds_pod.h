@@ -22,7 +22,9 @@ extern "C" {
  * chunks and FP64 across K splits; C = V Lambda V^T by cyclic Jacobi in FP64;
  * rank r = r_fixed if > 0, else
  * the smallest r with sum_{i<=r} lambda_i >= energy * sum_i lambda_i,
- * capped at r_max (<= 64); Phi = X V_r Lambda_r^(-1/2), re-orthonormalised
+ * capped at r_max (<= 64), and reduced to the number of leading eigenvalues
+ * that are positive and above 1e-13 lambda_1 (a rank beyond them cannot be
+ * normalised; *r reports the rank used); Phi = X V_r Lambda_r^(-1/2), re-orthonormalised
  * by one Cholesky-QR pass; sign: the largest-magnitude entry of each column
  * is positive (ties: lowest row).  kappa (host, s x s) gives
  * X^H = Phi^T (I (x) kappa) Phi (Sec. 2.4).  *out receives a new basis owned

@@ -556,6 +556,53 @@ __global__ void k_binit(int E, BState *st) {
   st[e] = s;
 }
 
+// tau_e = (1/N_e) sum_I sum_k q_k (x) grad Psi_k(q_k) for ensemble e = block;
+// FP64, fixed per-thread assignment and tree order (deterministic).
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_bstress(const float *__restrict__ q, const long long *__restrict__ off, const int *__restrict__ sizes,
+              const BCommon cm, double *__restrict__ tau, int *err) {
+  __shared__ double sh[9][256];
+  const int e = blockIdx.x, s = cm.s;
+  const long long base = off[e];
+  const int Ne = sizes[e];
+  double acc[9];
+#pragma unroll
+  for (int x = 0; x < 9; ++x) acc[x] = 0.0;
+  for (int i = threadIdx.x; i < Ne; i += blockDim.x) {
+    float y[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) y[d] = q[(size_t)(base + i) * D + d];
+    for (int k = 0; k < cm.nb; ++k) {
+      double f = cm.H[k];
+      if (cm.spring == 1) {
+        double n2 = 0.0;
+        for (int a = 0; a < s; ++a) n2 += (double)y[s * k + a] * y[s * k + a];
+        if (!(n2 < cm.b)) vds_flag(err, VDS_EDOMAIN);
+        f = cm.H[k] / (1.0 - n2 / cm.b);
+      }
+      for (int a = 0; a < s; ++a)
+        for (int b = 0; b < s; ++b) acc[a * s + b] += (double)y[s * k + a] * f * (double)y[s * k + b];
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 9; ++x) sh[x][threadIdx.x] = acc[x];
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+#pragma unroll
+      for (int x = 0; x < 9; ++x) sh[x][threadIdx.x] += sh[x][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < s * s) tau[(size_t)e * s * s + threadIdx.x] = sh[threadIdx.x][0] / (double)Ne;
+}
+
+__global__ void k_bset_kappa(EParam *ep, const double *__restrict__ kappa, int E, int ss) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int k = 0; k < 9; ++k) ep[e].kappa[k] = k < ss ? kappa[(size_t)e * ss + k] : 0.0;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
@@ -997,6 +1044,35 @@ int vds_batch_queue(const vds_batch *b, int *items, int n_items) {
   if (!b || !items || n_items < b->nitems) return VDS_EARG;
   memcpy(items, b->items.data(), sizeof(int) * 2 * b->nitems);
   return VDS_OK;
+}
+
+int vds_batch_stress(vds_ctx *c, vds_batch *b, const float *q, double *tau) {
+  if (!c || !b || !q || !tau || b->device != c->device) return VDS_EARG;
+  Dev dg(c->device);
+  const int ss = b->cm.s * b->cm.s;
+  VDS_TRY(vds_ensure(c, c->red, (size_t)b->E * ss * sizeof(double)));
+  double *dt = (double *)c->red.ptr;
+#define CALL(DD) (k_bstress<DD><<<b->E, 256, 0, c->stream>>>(q, b->d_off, b->d_sizes, b->cm, dt, c->err), VDS_OK)
+  const int st = [&]() -> int { VDS_BATCH_D(b->D, CALL) }();
+#undef CALL
+  VDS_TRY(st);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_CUDA_TRY(cudaMemcpyAsync(tau, dt, (size_t)b->E * ss * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return vds_sync_status(c);
+}
+
+int vds_batch_set_kappa(vds_ctx *c, vds_batch *b, const double *kappa) {
+  if (!c || !b || !kappa || b->device != c->device) return VDS_EARG;
+  Dev dg(c->device);
+  const int ss = b->cm.s * b->cm.s;
+  VDS_TRY(vds_ensure(c, c->red, (size_t)b->E * ss * sizeof(double)));
+  double *dk = (double *)c->red.ptr;
+  VDS_CUDA_TRY(cudaMemcpyAsync(dk, kappa, (size_t)b->E * ss * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  k_bset_kappa<<<(b->E + 255) / 256, 256, 0, c->stream>>>(b->d_ep, dk, b->E, ss);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return vds_sync_status(c);
 }
 
 int vds_batch_set_config(vds_ctx *c, vds_batch *b, int config) {

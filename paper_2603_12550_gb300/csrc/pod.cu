@@ -691,9 +691,11 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   VDS_CUDA_TRY(cudaMemcpyAsync(c->h_scal, c->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
   VDS_TRY(vds_sync_status(c));
-  const int r_rule = (int)c->h_scal[SC_AUX + 2];
+  // the rank of the rule (or r_fixed), reduced to the leading eigenvalues
+  // that are positive and above 1e-13 lambda_1 (the others cannot be
+  // normalised); *r_out reports it
   const int r = (int)c->h_scal[SC_AUX + 3];
-  if (r < 1 || r != r_rule) return VDS_EARG;  // rank exceeds the resolved spectrum
+  if (r < 1) return VDS_EARG;
   const int ld = (r + 3) / 4 * 4;
 
   pod_basis *b = new pod_basis();

@@ -97,6 +97,8 @@ _SIGS = {
     "vds_batch_energy_grad": ([_vp, _vp, _vp, _dp, _vp, _vp], _i),
     "vds_batch_step": ([_vp, _vp, _vp, _i, _ip], _i),
     "vds_batch_autotune": ([_vp, _vp, _vp, _i, _ip, _dp], _i),
+    "vds_batch_stress": ([_vp, _vp, _vp, _dp], _i),
+    "vds_batch_set_kappa": ([_vp, _vp, _dp], _i),
     "vds_batch_set_config": ([_vp, _vp, _i], _i),
     "vds_batch_get_config": ([_vp, _ip], _i),
     "vds_score_param_count": ([_i, _i], _l),
@@ -296,6 +298,16 @@ class Batch:
         _check(lib.vds_batch_energy_grad(self.ctx.h, self.h, _ptr(q_all), E if want_energy else None,
                                          _ptr(g), _ptr(rho)))
         return np.array(E[:]) if want_energy else None
+
+    def stress(self, q_all, s):
+        """Per-ensemble stress, E x s x s."""
+        tau = np.empty((self.E, s, s))
+        _check(lib.vds_batch_stress(self.ctx.h, self.h, _ptr(q_all), tau.ctypes.data_as(_dp)))
+        return tau
+
+    def set_kappa(self, kappa):
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        _check(lib.vds_batch_set_kappa(self.ctx.h, self.h, kappa.ctypes.data_as(_dp)))
 
     def autotune(self, q_all, reps=3):
         """Times every pair-kernel shape on q_all, keeps the fastest; returns

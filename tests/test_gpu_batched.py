@@ -171,3 +171,32 @@ def test_autotune_keeps_the_fastest_shape(vds, ctx):
     # implicit step after the switch (graph captured again): same bits
     b.step(q_all, 1)
     assert torch.equal(q_all, q_ref)
+
+
+def test_batched_stress_matches_oracle(orc, vds, ctx):
+    # micro-macro coupling: the stress of every ensemble in one launch
+    qs, h, kap = _ensembles(5)
+    b = _batch(vds, ctx, SIZES, h, kap, H=[1.0, 2.0])
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    tau = b.stress(q_all, S)
+    for e, q in enumerate(qs):
+        tau_o, _ = orc.stress(q.astype(np.float64), orc.params(NB, S, H=[1.0, 2.0], h=h[e]))
+        assert np.linalg.norm(tau[e] - tau_o) <= 1e-6 * np.linalg.norm(tau_o), e
+
+
+def test_set_kappa_drives_the_next_steps(orc, vds, ctx):
+    # new velocity gradients from a macroscopic field take effect at the next step
+    qs, h, kap = _ensembles(6)
+    b = _batch(vds, ctx, SIZES, h, kap, dt=0.005, scheme=0)
+    kap2 = kap[:, ::-1, ::-1].copy() * 2.0  # another flow per ensemble
+    b.set_kappa(kap2)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    b.step(q_all, 3)
+    q_all = q_all.cpu().numpy()
+    off = 0
+    for e, q in enumerate(qs):
+        n = q.shape[0]
+        po = orc.params(NB, S, h=h[e], dt=0.005, kappa=kap2[e])
+        q_o = orc.explicit_steps(q.astype(np.float64), po, 3)
+        assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o)), e
+        off += n

@@ -143,3 +143,27 @@ def test_chain4_full_size_steps_match_oracle(orc, vds, ctx, spring, steps):
     tau, qq = ctx.vds_stress(q, pg)
     assert _rel(tau, tau_o) <= 1e-3
     assert _rel(qq, qq_o) <= 1e-3
+
+
+def test_time_step_convergence(vds, ctx):
+    # Appendix A: explicit and implicit Euler are first order in dt (4-bead
+    # chain in shear, P = 1000): against a fine explicit run, halving dt halves
+    # the error of both, and the two schemes approach the same limit
+    P, nb, s, h, T = 1000, 3, 3, 0.9, 0.25
+    kap = inputs.shear_kappa(s, 1.0)
+    q0 = _dev(inputs.equilibrium_cloud(P, nb, s, seed=31))
+
+    def run(dt, scheme):
+        q = q0.clone()
+        p = vds.params(nb, s, h=h, dt=dt, kappa=kap, scheme=scheme, tol=1e-8, jfloor=1e-9)
+        ctx.vds_step(q, p, int(round(T / dt)))
+        return q.cpu().numpy().astype(np.float64)
+
+    ref = run(T / 2000, 0)
+    dts = (1e-2, 5e-3, 2.5e-3)
+    for scheme in (0, 1):
+        err = [np.linalg.norm(run(dt, scheme) - ref) / np.linalg.norm(ref) for dt in dts]
+        for a, b in zip(err, err[1:]):
+            assert 0.35 < b / a < 0.65, (scheme, err)
+    gap = [np.linalg.norm(run(dt, 0) - run(dt, 1)) / np.linalg.norm(ref) for dt in dts]
+    assert gap[-1] < gap[0] and gap[-1] < 1e-2, gap
