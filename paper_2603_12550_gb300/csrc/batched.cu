@@ -269,7 +269,7 @@ __device__ __forceinline__ void write_rec(float *rec, long i, float c, const flo
 template <int D>
 __global__ void k_bprep(long total, const int *__restrict__ ens, const EParam *__restrict__ ep,
                         const BState *__restrict__ st, const BCommon cm, int mode, float *q, float *qs,
-                        float *dA, float *dB, float *dir, float *__restrict__ rec) {
+                        float *dA, float *dB, float *dir, float *dprev, float *__restrict__ rec) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int e = ens[i];
@@ -293,10 +293,24 @@ __global__ void k_bprep(long total, const int *__restrict__ ens, const EParam *_
       for (int b = 0; b < D; ++b)
         if (b / cm.s == k) v += ep[e].kappa[al * cm.s + (b - k * cm.s)] * (double)x[b];
       qs[(size_t)i * D + a] = (float)((double)x[a] + cm.dt * v);
-      dA[(size_t)i * D + a] = 0.f;
       dB[(size_t)i * D + a] = 0.f;
       dir[(size_t)i * D + a] = 0.f;
     }
+    // start from q* + the previous step's correction of this call (zero at
+    // its first step); a particle whose start would leave the FENE domain
+    // starts from q*
+    bool inside = true;
+    if (cm.spring == 1)
+      for (int k = 0; k < cm.nb; ++k) {
+        double n2 = 0.0;
+        for (int a = 0; a < cm.s; ++a) {
+          const double y = (double)qs[(size_t)i * D + cm.s * k + a] + dprev[(size_t)i * D + cm.s * k + a];
+          n2 += y * y;
+        }
+        if (!(n2 < cm.b)) inside = false;
+      }
+#pragma unroll
+    for (int a = 0; a < D; ++a) dA[(size_t)i * D + a] = inside ? dprev[(size_t)i * D + a] : 0.f;
     return;
   }
   const BState s = st[e];
@@ -317,6 +331,7 @@ __global__ void k_bprep(long total, const int *__restrict__ ens, const EParam *_
       float dl = dcur[(size_t)i * D + d];
       if (s.fin_dir) dl = dl - 1.f * dir[(size_t)i * D + d];
       q[(size_t)i * D + d] = qs[(size_t)i * D + d] + dl;
+      dprev[(size_t)i * D + d] = dl;
     }
   }
 }
@@ -620,7 +635,7 @@ struct vds_batch {
   unsigned *d_counter = nullptr;
   EParam *d_ep = nullptr;
   BState *d_st = nullptr;
-  float *rec = nullptr, *qs = nullptr, *dA = nullptr, *dB = nullptr, *dir = nullptr;
+  float *rec = nullptr, *qs = nullptr, *dA = nullptr, *dB = nullptr, *dir = nullptr, *dprev = nullptr;
   double *acc = nullptr, *contrib = nullptr, *eout = nullptr;
   size_t smem = 0;
   cudaGraphExec_t round_exec = nullptr;
@@ -657,7 +672,7 @@ int b_launch_pair(vds_ctx *c, vds_batch *b, int mode) {
 template <int D>
 int b_prep(vds_ctx *c, vds_batch *b, int mode, float *q) {
   k_bprep<D><<<(unsigned)((b->total + 255) / 256), 256, 0, c->stream>>>(
-      b->total, b->d_ens, b->d_ep, b->d_st, b->cm, mode, q, b->qs, b->dA, b->dB, b->dir, b->rec);
+      b->total, b->d_ens, b->d_ep, b->d_st, b->cm, mode, q, b->qs, b->dA, b->dB, b->dir, b->dprev, b->rec);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;
@@ -840,6 +855,8 @@ int b_step(vds_ctx *c, vds_batch *b, float *q, int nsteps, int *iters_out, int s
   const int max_rounds = 32 * (b->cm.max_iter + 1) + 4;
   std::vector<BState> hs(b->E);
   int status = VDS_OK;
+  // the first step of a call starts every minimiser from q*
+  VDS_CUDA_TRY(cudaMemsetAsync(b->dprev, 0, sizeof(float) * (size_t)b->total * D, c->stream));
   for (int n = 0; n < nsteps; ++n) {
     k_binit<<<(b->E + 255) / 256, 256, 0, c->stream>>>(b->E, b->d_st);
     VDS_CUDA_TRY(cudaGetLastError());
@@ -934,7 +951,7 @@ void vds_batch_free(vds_batch *b) {
   Dev dg(b->device);
   b_drop_graph(b);
   void *ptrs[] = {b->d_off, b->d_sizes, b->d_ens, b->d_active, b->d_queue, b->d_counter, b->d_ep, b->d_st,
-                  b->rec, b->qs, b->dA, b->dB, b->dir, b->acc, b->contrib, b->eout};
+                  b->rec, b->qs, b->dA, b->dB, b->dir, b->dprev, b->acc, b->contrib, b->eout};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (b->h_active) cudaFreeHost(b->h_active);
@@ -1010,6 +1027,7 @@ int vds_batch_create(vds_ctx *c, int E, const int *sizes, int D, const vds_param
   A((void **)&b->dA, sizeof(float) * nd);
   A((void **)&b->dB, sizeof(float) * nd);
   A((void **)&b->dir, sizeof(float) * nd);
+  A((void **)&b->dprev, sizeof(float) * nd);
   A((void **)&b->acc, sizeof(double) * nd);
   A((void **)&b->contrib, sizeof(double) * 3 * tot);
   A((void **)&b->eout, sizeof(double) * E);

@@ -200,3 +200,24 @@ def test_set_kappa_drives_the_next_steps(orc, vds, ctx):
         q_o = orc.explicit_steps(q.astype(np.float64), po, 3)
         assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o)), e
         off += n
+
+
+def test_batched_implicit_fene_matches_oracle(orc, vds, ctx):
+    # FENE springs (b = 50), three implicit steps in one call: the later steps
+    # start from the previous correction unless that leaves the FENE domain
+    sizes = [300, 129, 77]
+    qs = [inputs.equilibrium_cloud(n, NB, S, seed=300 + e, fene_b=50.0) for e, n in enumerate(sizes)]
+    h = np.array([0.6, 0.7, 0.8])
+    kap = np.stack([inputs.shear_kappa(S, r) for r in (0.5, 1.0, 3.0)])
+    b = vds.Batch(ctx, sizes, D, vds.params(NB, S, spring=1, b=50.0, dt=0.005, scheme=1, tol=1e-6, jfloor=1e-9),
+                  h, kap)
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    b.step(q_all, 3)
+    q_all = q_all.cpu().numpy()
+    off = 0
+    for e, q in enumerate(qs):
+        n = q.shape[0]
+        po = orc.params(NB, S, spring=1, b=50.0, h=h[e], dt=0.005, kappa=kap[e], tol=1e-10)
+        q_o, _, _ = orc.implicit_steps(q.astype(np.float64), po, 3)
+        assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o)), e
+        off += n
