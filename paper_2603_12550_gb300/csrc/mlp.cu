@@ -373,6 +373,325 @@ __global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 
   }
 }
 
+// ------------------------------------------------- fused inference forward
+//
+// k_mlp_fwd evaluates all four layers of the width-256 network for 128-row
+// tiles in one persistent launch (one CTA per SM, 320 threads): the hidden
+// activations of a tile never leave shared memory.  Roles:
+//   warp 8, one lane   streams the packed weights (F_NCHUNK chunks per tile,
+//                      each the exact shared-memory image of a 128-row x 64-K
+//                      operand block) through an F_STAGES-deep ring with 1-D
+//                      bulk copies (TMA engine);
+//   warp 9, one lane   issues the tcgen05.mma (M=128, N=128 per weight half,
+//                      K=16; N=16 for the output layer) into the tile's
+//                      256-column accumulator;
+//   warps 0-7          read the accumulator (warp w: rows 32 (w % 4) + lane,
+//                      columns 32 (w / 4) + ... of each 64-column K-chunk),
+//                      add the bias, apply SiLU and write BF16 activations
+//                      back as the next layer's A operand; for the output
+//                      layer they add b4 and store the first D columns.
+// Two tiles are in flight (slots 0 and 1, 256 TMEM columns and a 64 KB
+// activation buffer each): the MMAs of one slot run while the epilogue warps
+// work on the other.  The CTA takes tiles b, b + G, b + 2G, ...; round r puts
+// its tiles 2r and 2r + 1 into slots 0 and 1.
+//
+// Synchronisation per slot (completion counts per round r, layer l):
+//   edone[s]  256 arrivals: the operand of layer l is written and the
+//             accumulator released (completion 4r + l; the A0 of round r + 1
+//             is written by the output epilogue of round r);
+//   afull[s]  tcgen05.commit after the MMAs of layer l (completion 4r + l);
+//   full/empty[stage]  weight ring (bulk-copy bytes / MMA commit).
+// Every wait is bounded: a wait that runs out sets the abort flag and the
+// error flag, every role then leaves its loop, the copies and MMAs in flight
+// are waited for (again bounded) and the tensor memory is freed.
+//
+// SiLU here is z sigma(z) = h (1 + tanh h) with h = z / 2 and the hardware
+// tanh approximation (relative error about 2^-11, far below the BF16
+// rounding of the activation it produces).
+
+constexpr int F_THREADS = 320;
+constexpr int F_STAGES = 5;
+constexpr int F_CHUNK = 16384;                 // bytes of one weight chunk
+constexpr int F_NCHUNK = 19;                   // W1: 2, W2: 8, W3: 8, W4: 1 (8 KB)
+constexpr int F_HBYTES = 4 * 16384;            // activations of one tile: 4 K-chunks of 128 x 64 BF16
+constexpr int F_BIAS_FLOATS = 3 * 256 + 16;
+constexpr size_t F_SMEM = 2 * F_HBYTES + F_STAGES * F_CHUNK + F_BIAS_FLOATS * 4;
+constexpr size_t F_WPACK_BYTES = 18 * (size_t)F_CHUNK + 8192;
+
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool fwait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t n = 0;; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 63u) == 63u) {
+      if (*abort) return false;
+      if (global_timer_ns() - t0 > VDS_WAIT_LIMIT_NS) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__host__ __device__ constexpr int f_first_chunk(int l) { return l == 0 ? 0 : (l == 1 ? 2 : (l == 2 ? 10 : 18)); }
+__host__ __device__ constexpr int f_nchunks(int l) { return l == 0 ? 2 : (l == 3 ? 1 : 8); }
+static_assert(f_first_chunk(3) + f_nchunks(3) == F_NCHUNK, "weight stream length");
+static_assert(F_SMEM <= 227 * 1024 - 1024, "shared memory of k_mlp_fwd");
+
+// Packed weight stream: chunk j holds, in the canonical K-major layout
+// ((r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2 bytes), rows 128 nh .. of W1
+// (j = nh), of W2 (j = 2 + 2 kc + nh, K columns 64 kc ..) or W3 (j = 10 +
+// ...); chunk 18 is W4 (16 rows) as four 2 KB blocks of 64 K columns.
+__global__ void k_pack_w(const bf16 *__restrict__ w1, const bf16 *__restrict__ w2, const bf16 *__restrict__ w3,
+                         const bf16 *__restrict__ w4, int Dp, int W, bf16 *__restrict__ pack) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)(F_WPACK_BYTES / 2)) return;
+  const int j = (int)(e / (F_CHUNK / 2));
+  int b = (int)(e - (long)j * (F_CHUNK / 2)) * 2;  // byte inside the chunk
+  int sub = 0;
+  if (j == 18) {
+    sub = b >> 11;
+    b &= 2047;
+  }
+  const int g = b >> 10, c = (b >> 7) & 7, r8 = (b >> 4) & 7, k8 = (b >> 1) & 7;
+  const int r = g * 8 + r8, k = c * 8 + k8;
+  bf16 v;
+  if (j < 2) {
+    v = w1[(size_t)(j * 128 + r) * Dp + k];
+  } else if (j < 18) {
+    const int jj = (j - 2) & 7, kc = jj >> 1, nh = jj & 1;
+    const bf16 *w = j < 10 ? w2 : w3;
+    v = w[(size_t)(nh * 128 + r) * W + kc * 64 + k];
+  } else {
+    v = w4[(size_t)r * W + sub * 64 + k];
+  }
+  pack[e] = v;
+}
+
+__global__ void __launch_bounds__(F_THREADS, 1)
+    k_mlp_fwd(const float *__restrict__ x, int N, int D, const bf16 *__restrict__ wpack,
+              const float *__restrict__ b1, const float *__restrict__ b2, const float *__restrict__ b3,
+              const float *__restrict__ b4, float *__restrict__ out, int *err) {
+  extern __shared__ __align__(1024) uint8_t fsm[];
+  __shared__ __align__(8) uint64_t full[F_STAGES], empty[F_STAGES], afull[2], edone[2], fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (N + GM - 1) / GM;
+  const int G = gridDim.x;
+  const int nk = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this CTA
+  const int rounds = (nk + 1) / 2;
+  uint8_t *hbuf = fsm;                                  // 2 x 64 KB activations
+  uint8_t *ring = fsm + 2 * F_HBYTES;                   // weight stages
+  float *sbias = reinterpret_cast<float *>(ring + F_STAGES * F_CHUNK);
+  volatile int *abort = &s_abort;
+
+  if (warp == 0) tc_alloc(&s_tmem, 512);
+  if (tid == 0) {
+    for (int k = 0; k < F_STAGES; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&afull[k], 1);
+      mbar_init(&edone[k], 256);
+    }
+    mbar_init(&fin, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  for (int i = tid; i < F_BIAS_FLOATS; i += F_THREADS)
+    sbias[i] = i < 256 ? b1[i] : (i < 512 ? b2[i - 256] : (i < 768 ? b3[i - 512] : (i - 768 < D ? b4[i - 768] : 0.f)));
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  auto tile_of = [&](int r, int s) { return (int)blockIdx.x + (2 * r + s) * G; };
+
+  if (warp == 8) {
+    // ------------------------------------------------ weight producer
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int r = 0; r < rounds && ok; ++r)
+        for (int l = 0; l < 4 && ok; ++l)
+          for (int s = 0; s < 2 && ok; ++s) {
+            if (2 * r + s >= nk) continue;
+            for (int j = f_first_chunk(l); j < f_first_chunk(l) + f_nchunks(l); ++j, ++g) {
+              const uint32_t st = g % F_STAGES;
+              if (g >= F_STAGES && !fwait(&empty[st], ((g / F_STAGES) - 1) & 1, abort)) {
+                ok = false;
+                break;
+              }
+              const uint32_t bytes = j == 18 ? 8192u : (uint32_t)F_CHUNK;
+              mbar_arrive_expect_tx(&full[st], bytes);
+              bulk_g2s(ring + st * F_CHUNK, reinterpret_cast<const uint8_t *>(wpack) + (size_t)j * F_CHUNK, bytes,
+                       &full[st]);
+            }
+          }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      // the copies still in flight land before the CTA may exit
+      for (uint32_t k = g > F_STAGES ? g - F_STAGES : 0; k < g; ++k)
+        mbar_wait_bounded(&full[k % F_STAGES], (k / F_STAGES) & 1, VDS_WAIT_LIMIT_NS);
+    }
+  } else if (warp == 9) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id128 = tc_idesc(TC_FMT_BF16, GM, 128), id16 = tc_idesc(TC_FMT_BF16, GM, 16);
+      const uint32_t hb0 = smem_u32(hbuf), rb = smem_u32(ring);
+      uint32_t g = 0;
+      bool ok = true;
+      for (int r = 0; r < rounds && ok; ++r)
+        for (int l = 0; l < 4 && ok; ++l)
+          for (int s = 0; s < 2 && ok; ++s) {
+            if (2 * r + s >= nk) continue;
+            if (!fwait(&edone[s], (uint32_t)(l & 1), abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(s * 256), hb = hb0 + (uint32_t)(s * F_HBYTES);
+            for (int jj = 0; jj < f_nchunks(l); ++jj, ++g) {
+              const uint32_t st = g % F_STAGES;
+              if (!fwait(&full[st], (g / F_STAGES) & 1, abort)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t wb = rb + st * F_CHUNK;
+              if (l == 3) {
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc)
+#pragma unroll
+                  for (int k = 0; k < 4; ++k)
+                    tc_mma_bf16(d, tc_sdesc(hb + kc * 16384 + k * 256), tc_sdesc(wb + kc * 2048 + k * 256), id16,
+                                (kc > 0 || k > 0) ? 1 : 0);
+              } else {
+                const int kc = l == 0 ? 0 : jj >> 1, nh = l == 0 ? jj : jj & 1;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  tc_mma_bf16(d + (uint32_t)(nh * 128), tc_sdesc(hb + kc * 16384 + k * 256), tc_sdesc(wb + k * 256),
+                              id128, (kc > 0 || k > 0) ? 1 : 0);
+              }
+              tc_commit(&empty[st]);
+            }
+            if (ok) tc_commit(&afull[s]);
+          }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+    }
+  } else {
+    // ------------------------------------------------ epilogue warps 0-7
+    const int q = warp & 3, half = warp >> 2;
+    const int rl = q * 32 + lane;                       // accumulator row of this thread
+    const int ar = tid & 127, ag = tid >> 7;            // A0 row and 8-column group of this thread
+    float xp[2][8];
+    auto fetch_x = [&](int tile, float (&xv)[8]) {
+      const int row = tile * GM + ar;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = ag * 8 + i;
+        xv[i] = (row < N && k < D) ? x[(size_t)row * D + k] : 0.f;
+      }
+    };
+    // A0 = bf16(x) padded to 64 columns, into K-chunk 0 of the slot's buffer
+    auto put_a0 = [&](int s, const float (&xv)[8]) {
+      uint8_t *h = hbuf + s * F_HBYTES + (ar >> 3) * 1024 + (ar & 7) * 16;
+      uint32_t pk[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 t = __floats2bfloat162_rn(xv[2 * i], xv[2 * i + 1]);
+        pk[i] = *reinterpret_cast<const uint32_t *>(&t);
+      }
+      *reinterpret_cast<uint4 *>(h + ag * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+      for (int c = 1; c < 4; ++c) *reinterpret_cast<uint4 *>(h + (ag + 2 * c) * 128) = make_uint4(0, 0, 0, 0);
+    };
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      if (s < nk) {
+        fetch_x(tile_of(0, s), xp[s]);
+        put_a0(s, xp[s]);
+        fence_proxy_async_smem();
+        mbar_arrive(&edone[s]);
+      }
+    bool ok = true;
+    for (int r = 0; r < rounds && ok; ++r)
+      for (int l = 0; l < 4 && ok; ++l)
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if (!ok || 2 * r + s >= nk) continue;
+          ok = __all_sync(0xffffffffu, fwait(&afull[s], (uint32_t)(l & 1), abort));
+          if (!ok) continue;
+          tc_fence_after();
+          const uint32_t ta = tmem + (uint32_t)(s * 256) + ((uint32_t)(q * 32) << 16);
+          const bool next = 2 * (r + 1) + s < nk;
+          if (l < 3) {
+            if (l == 2 && next) fetch_x(tile_of(r + 1, s), xp[s]);
+            const float *bias = sbias + l * 256;
+            uint8_t *h = hbuf + s * F_HBYTES + (rl >> 3) * 1024 + (rl & 7) * 16;
+#pragma unroll 1
+            for (int kc = 0; kc < 4; ++kc) {
+              uint32_t v[32];
+              const int c0 = kc * 64 + half * 32;
+              tc_ld32(ta + (uint32_t)c0, v);
+              uint32_t pk[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                const float z0 = __uint_as_float(v[2 * i]) + bias[c0 + 2 * i];
+                const float z1 = __uint_as_float(v[2 * i + 1]) + bias[c0 + 2 * i + 1];
+                const float h0 = 0.5f * z0, h1 = 0.5f * z1;
+                const __nv_bfloat162 t =
+                    __floats2bfloat162_rn(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
+                pk[i] = *reinterpret_cast<const uint32_t *>(&t);
+              }
+              uint8_t *hk = h + kc * 16384 + half * 4 * 128;
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<uint4 *>(hk + i * 128) =
+                    make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            }
+          } else {
+            // the layer-4 MMAs have read the activations: the next tile's A0 may go in
+            if (next) put_a0(s, xp[s]);
+            if (half == 0) {
+              uint32_t v[16];
+              tc_ld16(ta, v);
+              const int row = tile_of(r, s) * GM + rl;
+              if (row < N) {
+                const float *bias = sbias + 768;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                  if (j < D) out[(size_t)row * D + j] = __uint_as_float(v[j]) + bias[j];
+              }
+            }
+          }
+          fence_proxy_async_smem();
+          tc_fence_before();
+          mbar_arrive(&edone[s]);
+        }
+    if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
+  }
+  // every role has left its loop; the MMAs issued are complete before the
+  // tensor memory is released
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9 && lane == 0) {
+    tc_commit(&fin);
+    mbar_wait_bounded(&fin, 0, VDS_WAIT_LIMIT_NS);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, 512);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
@@ -384,6 +703,8 @@ struct vds_score {
   float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
   bf16 *w1b = nullptr, *w2b = nullptr, *w3b = nullptr, *w4b = nullptr;
   bf16 *w2t = nullptr, *w3t = nullptr, *w4t = nullptr;  // transposes (w4t: W x 64, K padded)
+  bf16 *wpack = nullptr;  // weight stream of the fused inference kernel (F_WPACK_BYTES)
+  bool packed = false;    // wpack matches the current BF16 weights
   int t = 0;
   int mcap = 0;
   // activations for up to mcap rows
@@ -520,6 +841,7 @@ int refresh_bf16(vds_ctx *c, vds_score *s) {
   VDS_TRY(conv(s->p + s->off[2], W, W, s->w2b, s->w2t, W));
   VDS_TRY(conv(s->p + s->off[4], W, W, s->w3b, s->w3t, W));
   VDS_TRY(conv(s->p + s->off[6], s->Op, W, s->w4b, s->w4t, 64));
+  s->packed = false;  // repacked by the next inference call
   return VDS_OK;
 }
 
@@ -680,6 +1002,7 @@ int vds_score_create(vds_ctx *c, int D, int width, const float *params, vds_scor
   A((void **)&s->w2t, sizeof(bf16) * W * W);
   A((void **)&s->w3t, sizeof(bf16) * W * W);
   A((void **)&s->w4t, sizeof(bf16) * W * 64);
+  A((void **)&s->wpack, F_WPACK_BYTES);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->m, 0, sizeof(float) * o, c->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->v, 0, sizeof(float) * o, c->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->g, 0, sizeof(float) * o, c->stream);
@@ -701,7 +1024,7 @@ void vds_score_free(vds_score *s) {
   if (!s) return;
   Dev dg(s->device);
   free_acts(s);
-  void *ptrs[] = {s->p, s->m, s->v, s->g, s->w1b, s->w2b, s->w3b, s->w4b, s->w2t, s->w3t, s->w4t};
+  void *ptrs[] = {s->p, s->m, s->v, s->g, s->w1b, s->w2b, s->w3b, s->w4b, s->w2t, s->w3t, s->w4t, s->wpack};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete s;
@@ -735,6 +1058,29 @@ int vds_score_get_params(vds_ctx *c, const vds_score *s, float *params) {
 int vds_score_eval(vds_ctx *c, vds_score *s, const float *x, int N, float *out) {
   if (!c || !s || !x || !out || N < 1) return VDS_EARG;
   Dev dg(c->device);
+  if (s->W == 256 && s->Dp == 64 && s->Op == 16) {
+    // all four layers in one persistent launch (k_mlp_fwd)
+    static bool attr[VDS_MAX_DEVICES] = {};
+    if (c->device >= VDS_MAX_DEVICES || !attr[c->device]) {
+      VDS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F_SMEM));
+      if (c->device < VDS_MAX_DEVICES) attr[c->device] = true;
+    }
+    if (!s->packed) {
+      const long ne = (long)(F_WPACK_BYTES / 2);
+      k_pack_w<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(s->w1b, s->w2b, s->w3b, s->w4b, s->Dp, s->W,
+                                                                    s->wpack);
+      VDS_CUDA_TRY(cudaGetLastError());
+      ++c->launches;
+      s->packed = true;
+    }
+    const int ntiles = (N + GM - 1) / GM;
+    const int grid = ntiles < c->num_sms ? ntiles : c->num_sms;
+    k_mlp_fwd<<<grid, F_THREADS, F_SMEM, c->stream>>>(x, N, s->D, s->wpack, s->p + s->off[1], s->p + s->off[3],
+                                                      s->p + s->off[5], s->p + s->off[7], out, c->err);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    return VDS_OK;
+  }
   const int chunk = 65536;
   VDS_TRY(ensure_acts(s, N < chunk ? N : chunk));
   for (int n0 = 0; n0 < N; n0 += chunk) {

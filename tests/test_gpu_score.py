@@ -53,6 +53,68 @@ def test_forward_matches_oracle(vds, ctx, N):
     assert _rel(out.cpu().numpy(), s_o) <= 2e-2
 
 
+def _bf16(a):
+    """Round to the nearest BF16 (ties to even) through FP32, as the kernels
+    round their FP32 values; returned as float64."""
+    f = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    f = ((f + 0x7FFF + ((f >> 16) & 1)) >> 16) << 16
+    return f.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _forward_bf16_points(layers, x):
+    """The oracle's forward with BF16 rounding applied where the inference
+    kernel rounds (input, weights, hidden activations); FP64 otherwise."""
+    lo = mlp.as64(layers)
+    h = _bf16(x)
+    for i, (W, b) in enumerate(lo):
+        z = h @ _bf16(W).T + b
+        h = _bf16(mlp.silu(z)) if i < len(lo) - 1 else z
+    return h
+
+
+@pytest.mark.parametrize("N", [1, 127, 129, 19457, 100003])
+def test_fused_inference_per_tile(vds, ctx, N):
+    # one persistent launch covers every 128-row tile; with 100003 rows each
+    # CTA takes 5 or 6 tiles (three rounds of the two in-flight slots, the
+    # last one half empty on some CTAs).  Every tile is checked on its own
+    # against the FP64 forward with the kernel's BF16 rounding points, and
+    # the rows past N are left untouched.
+    layers = _layers(11)
+    net = vds.Score(ctx, 9, layers)
+    x = np.random.default_rng(N + 5).standard_normal((N, 9)).astype(np.float32)
+    buf = torch.full((N + 64, 9), 12345.0, device="cuda")
+    net.eval(torch.from_numpy(x).cuda(), buf[:N])
+    got = buf.cpu().numpy()
+    assert np.all(got[N:] == 12345.0)
+    got = got[:N]
+    ref = _forward_bf16_points(layers, x)
+    worst = 0.0
+    for t0 in range(0, N, 128):
+        worst = max(worst, _rel(got[t0:t0 + 128], ref[t0:t0 + 128]))
+    assert worst <= 6e-3, worst
+    s_o, _ = mlp.forward(mlp.as64(layers), x.astype(np.float64))
+    assert _rel(got, s_o) <= 2e-2
+
+
+def test_inference_follows_parameter_updates(vds, ctx):
+    # the packed weight stream of the inference kernel is rebuilt after a
+    # training step and after set_params
+    layers = _layers(12)
+    net = vds.Score(ctx, 9, layers)
+    x = np.random.default_rng(13).standard_normal((3000, 9)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty((3000, 9), device="cuda")
+    net.eval(xd, out)
+    xb, eps = inputs.dsm_batch(x, 512, seed=14)
+    net.train_step(torch.from_numpy(xb).cuda(), torch.from_numpy(eps).cuda(), 0.8, 1e-2)
+    net.eval(xd, out)
+    assert _rel(out.cpu().numpy(), _forward_bf16_points(net.params(), x)) <= 6e-3
+    layers2 = _layers(15)
+    net.set_params(layers2)
+    net.eval(xd, out)
+    assert _rel(out.cpu().numpy(), _forward_bf16_points(layers2, x)) <= 6e-3
+
+
 def test_loss_and_gradients_match_oracle(vds, ctx):
     layers = _layers(1)
     net = vds.Score(ctx, 9, layers)
