@@ -509,6 +509,28 @@ def _extras_surrogate(ctx, vds, inputs, torch, wl, h):
     e = final_err(P)
     res["surrogate_fit_exact_S"] = {"train_seconds": fit_s, "steps_per_s": K / sec, "stress_rel_err": e[0],
                                     "err_mor": e[1], "worst_check_rel_err": cerr, "fallbacks": nf}
+    # one network evaluation on all N particles (k_mlp_fwd, one launch), the
+    # step's only O(N) tensor-core work: CUDA events over back-to-back calls
+    xs, out = pool[:N], torch.empty((N, D), device="cuda")
+    for _ in range(5):
+        net2.eval(xs, out)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        net2.eval(xs, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * N * (D * 256 + 2 * 256 * 256 + 256 * D)
+    peaks, src = _peaks()
+    res["mlp_eval"] = {"rows": N, "ms": ms, "algorithmic_gflop": flops / 1e9,
+                       "tflops": flops / (ms * 1e-3) / 1e12,
+                       "frac_of_bf16_peak": flops / (ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                       "peak_source": src,
+                       "note": "algorithmic flops of D-256-256-256-D; the kernel pads layer 1 to K=64 and "
+                               "the output layer to N=16"}
     net2.free()
     # the paper's headline form: reduced time / full-order time, reduced DoF
     full = res["run"]["full_order_steps_per_s"]

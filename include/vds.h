@@ -123,6 +123,20 @@ VDS_API int vds_step(vds_ctx *ctx, float *q, int N, int D, const vds_params *p,
 VDS_API int vds_stress(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
                double *tau, double *qq);
 
+/* Kernel density estimate of the particle cloud at M query points
+ * (Eq. model_DeteParAppr; Appendix A compares runs through it on the grid
+ * {-2, 0, 2}^D):
+ *   f[J] = (1/N) sum_I (2 pi h^2)^(-D/2) exp(-|y_J - q_I|^2 / (2 h^2)),
+ * the same Gaussian kernel and bandwidth p->h as the pair passes (which take
+ * the query points to be the particles themselves: f(q_I) = rho_I (1/N)
+ * (2 pi h^2)^(-D/2)).  q: device N x D, y: device M x D, f: device M (FP32);
+ * p->nb, p->s give D.  One query-particle pair pass (query points as its
+ * rows, counted as a density pass by vds_timing) with FP64 sums across
+ * particle tiles.  Asynchronous on the context stream.  VDS_EARG for a NULL
+ * pointer, N < 1, M < 1 or invalid parameters. */
+VDS_API int vds_density_at(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
+                           const float *y, int M, float *f);
+
 /* Allocation-free density and gradient evaluation.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate
  * device memory at the point of the call: a flow solver that couples one VDS

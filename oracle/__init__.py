@@ -8,7 +8,8 @@ Parts:
   * ``vds_oracle.c`` (compiled here with gcc, FP64, OpenMP over particles):
     density, entropy gradient, energy, explicit and implicit steps, stress,
     median pair distance, pair counts, reduced-order refresh sums.
-  * this module (numpy, FP64): Silverman bandwidth, POD by the method of
+  * this module (numpy, FP64): the density estimate at query points and
+    Appendix A's grid density error, Silverman bandwidth, POD by the method of
     snapshots, project/lift, the linearised reduced step, err_MOR, the batched
     work-queue order.
 
@@ -163,6 +164,36 @@ def density_rows(q, h, rows):
     _check(_L().or_density_rows(qp, N, D, h, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
                                 len(rows), rp))
     return rho
+
+
+def density_at(q, h, y, chunk=16):
+    """Kernel density estimate of the cloud q at the points y (Eq.
+    model_DeteParAppr): f(y_J) = (1/N) sum_I (2 pi h^2)^(-D/2)
+    exp(-|y_J - q_I|^2 / (2 h^2)), differences taken coordinate by coordinate
+    in FP64."""
+    q = np.asarray(q, dtype=np.float64)
+    y = np.atleast_2d(np.asarray(y, dtype=np.float64))
+    N, D = q.shape
+    f = np.empty(y.shape[0])
+    for a in range(0, y.shape[0], chunk):
+        d = y[a:a + chunk, None, :] - q[None, :, :]
+        f[a:a + chunk] = np.exp(-np.sum(d * d, axis=2) / (2.0 * h * h)).sum(axis=1)
+    return f / N * (2.0 * np.pi * h * h) ** (-D / 2.0)
+
+
+def grid_points(D, values=(-2.0, 0.0, 2.0)):
+    """All points of the mesh values^D (Appendix A takes {-2, 0, 2}), the
+    last coordinate varying fastest."""
+    v = np.asarray(values, dtype=np.float64)
+    return np.stack(np.meshgrid(*([v] * D), indexing="ij"), axis=-1).reshape(-1, D)
+
+
+def density_error(f, f0):
+    """Appendix A's l2 and l-infinity relative differences of two density
+    estimates on the same points (f0 the reference)."""
+    f, f0 = np.asarray(f, np.float64), np.asarray(f0, np.float64)
+    return (float(np.sqrt(np.sum((f - f0) ** 2) / np.sum(f0 ** 2))),
+            float(np.max(np.abs(f - f0)) / np.max(np.abs(f0))))
 
 
 def entropy_grad_rows(q, h, rho, rows):

@@ -89,6 +89,7 @@ int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double 
   if (occ < 1) occ = 1;
   sc.TI = TI;
   sc.Npad = (N + TJ - 1) / TJ * TJ;
+  sc.Nipad = sc.Npad;
   sc.nchunk = sc.Npad / TJ;
   sc.n_itiles = (N + TI - 1) / TI;
   sc.items = (long long)sc.n_itiles * sc.nchunk;
@@ -108,7 +109,7 @@ int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double 
     if (G < 1) G = 1;
   }
   if ((size_t)sc.n_itiles * sc.maxseg * TI * ACC * sizeof(double) > kPartBytes) return VDS_ESIZE;
-  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, st>>>(rec, sc, part, err);
+  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, st>>>(rec, rec, sc, part, err);
   VDS_CUDA_TRY(cudaGetLastError());
   return VDS_OK;
 }

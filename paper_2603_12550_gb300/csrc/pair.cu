@@ -37,56 +37,67 @@ int vds_density_2(vds_ctx *, const KParams &, float *, bool, const float *, cons
 int vds_grad_2(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_2(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_2(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_2(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_3(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_3(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_3(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_3(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_3(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_3(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_4(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_4(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_4(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_4(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_4(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_4(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_6(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_6(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_6(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_6(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_6(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_6(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_8(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_8(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_8(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_8(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_8(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_8(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_9(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_9(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_9(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_9(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_9(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_9(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_10(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_10(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_10(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_10(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_10(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_10(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_12(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_12(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_12(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_12(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_12(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_12(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_14(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_14(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_14(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_14(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_14(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_14(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_15(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_15(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_15(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_15(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_15(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_15(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_16(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
 int vds_density_16(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
 int vds_grad_16(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_16(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_16(vds_ctx *, const KParams &, const float *, float *);
+int vds_query_16(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 
 KParams make_kparams(const vds_params *p, int N, int D) {
   KParams k;
@@ -140,6 +151,12 @@ int pass_stress(vds_ctx *c, const KParams &kp, const float *q, double *tau, doub
 
 int pass_flow(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
 #define CALL(DD) vds_flow_##DD(c, kp, q, qs)
+  VDS_DISPATCH_D(kp.D, CALL)
+#undef CALL
+}
+
+int pass_density_at(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M, float *f_out) {
+#define CALL(DD) vds_query_##DD(c, kp, q, y, M, f_out)
   VDS_DISPATCH_D(kp.D, CALL)
 #undef CALL
 }

@@ -16,7 +16,9 @@ struct Sched {
   int n_itiles;
   int maxseg;       // max segments per i-tile
   int TI;           // particles per i-tile
-  int Npad;         // N rounded up to a multiple of TJ
+  int Npad;         // N rounded up to a multiple of TJ (j records)
+  int Nipad;        // rows of the i-record array (= Npad unless the i points
+                    // are other points than the particles, as for queries)
 };
 
 __host__ __device__ __forceinline__ int sched_first_cta(long long x, const Sched &s) {
@@ -70,6 +72,11 @@ int pass_grad(vds_ctx *c, const KParams &kp, int mode, float *out,
 
 // Stress and second moments (FP64) into host arrays.
 int pass_stress(vds_ctx *c, const KParams &kp, const float *q, double *tau, double *qq);
+
+// Kernel density estimate at M query points y (M x D):
+//   f_out[J] = (1/N)(2 pi h^2)^(-D/2) sum_I exp(-|y_J - q_I|^2 / (2 h^2)),
+// the particles' records built from q, the queries' in their own buffer.
+int pass_density_at(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M, float *f_out);
 
 // y = base + delta -> out (element-wise, N x D).
 int pass_axpy(vds_ctx *c, int n, const float *base, const float *delta, float *out);

@@ -47,8 +47,8 @@ struct PairCfg {
 
 template <int D, int RI, int NT, bool GRAD>
 __global__ void __launch_bounds__(NT)
-    k_pair(const float *__restrict__ rec, Sched sc, double *__restrict__ part,
-           int *__restrict__ err) {
+    k_pair(const float *__restrict__ rec, const float *__restrict__ reci, Sched sc,
+           double *__restrict__ part, int *__restrict__ err) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
   constexpr uint32_t TILE_FLOATS = TJ * DP;
@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
       for (int k = 0; k < RI; ++k) {
         int i = t * sc.TI + tid + k * NT;
-        i = i < sc.Npad ? i : sc.Npad - 1;
-        const float *r = rec + (size_t)i * DP;
+        i = i < sc.Nipad ? i : sc.Nipad - 1;
+        const float *r = reci + (size_t)i * DP;
 #pragma unroll
         for (int d = 0; d < D; ++d) xi[k][d] = r[d];
         wi[k] = GRAD ? r[D] : 0.f;
@@ -600,8 +600,10 @@ __global__ void k_flow(KParams kp, const float *__restrict__ q, float *__restric
 
 // ------------------------------------------------------------ host plumbing
 
+// i points: the Ni records at reci (the particles themselves unless a query
+// pass); j points: the N particle records in c->rec.
 template <int D, int RI, int NT, bool GRAD>
-int launch_pair(vds_ctx *c, int N, Sched &sc) {
+int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
   constexpr int TI = NT * RI;
@@ -619,8 +621,9 @@ int launch_pair(vds_ctx *c, int N, Sched &sc) {
   }
   sc.TI = TI;
   sc.Npad = (N + TJ - 1) / TJ * TJ;
+  sc.Nipad = (Ni + TJ - 1) / TJ * TJ;
   sc.nchunk = sc.Npad / TJ;
-  sc.n_itiles = (N + TI - 1) / TI;
+  sc.n_itiles = (Ni + TI - 1) / TI;
   sc.items = (long long)sc.n_itiles * sc.nchunk;
   const long long cap = (long long)c->num_sms * occ;
   sc.G = (int)(sc.items < cap ? sc.items : cap);
@@ -634,7 +637,7 @@ int launch_pair(vds_ctx *c, int N, Sched &sc) {
   VDS_TRY(vds_ensure(c, c->part, (size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double)));
   const int pk = GRAD ? PK_GRADIENT : PK_DENSITY;
   VDS_TRY(vds_time_begin(c, pk));
-  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, sc,
+  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, reci, sc,
                                                            (double *)c->part.ptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   VDS_TRY(vds_time_end(c, pk));
@@ -658,7 +661,8 @@ template <int D>
 int density_impl(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
                  const float *ybase, const float *ydelta, const float *qa, const float *qb) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc)));
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc, kp.N,
+                                                                             (const float *)c->rec.ptr)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   k_dens_finish<D><<<nb, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, (float *)c->rec.ptr,
@@ -674,7 +678,8 @@ template <int D>
 int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,
               const float *ydelta, const float *qa, const float *qb, float *q_io) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(c, kp.N, sc)));
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(c, kp.N, sc, kp.N,
+                                                                           (const float *)c->rec.ptr)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   const double *pp = (const double *)c->part.ptr;
@@ -694,6 +699,42 @@ int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *
     k_grad_finish<D, GM_IMPLICIT_DIR><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rp, kp, out, ybase, ydelta,
                                                                    qa, qb, q_io, red, tk, c->scal,
                                                                    c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+// f at the query points: the segment partials of each query summed in a
+// fixed order (FP64), times (1/N)(2 pi h^2)^(-D/2).
+template <int D>
+__global__ void __launch_bounds__(NT_FIN)
+    k_query_finish(Sched sc, const double *__restrict__ part, int M, double scale, float *__restrict__ f_out,
+                   int *err) {
+  const int i = blockIdx.x * NT_FIN + threadIdx.x;
+  if (i >= M) return;
+  const int t = i / sc.TI, il = i - t * sc.TI;
+  const int f = sched_first_cta((long long)t * sc.nchunk, sc);
+  const int l = sched_first_cta((long long)(t + 1) * sc.nchunk - 1, sc);
+  double s = 0.0;
+  for (int g = 0; g <= l - f; ++g) s += part[((size_t)t * sc.maxseg + g) * sc.TI + il];
+  if (!(s >= 0.0 && s <= 1e300)) vds_flag(err, VDS_ENAN);
+  f_out[i] = (float)(s * scale);
+}
+
+template <int D>
+int query_impl(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M, float *f_out) {
+  VDS_TRY(prep_impl<D>(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  const int Mpad = (M + TJ - 1) / TJ * TJ;
+  VDS_TRY(vds_ensure(c, c->recq, (size_t)Mpad * Rec<D>::DP * sizeof(float)));
+  k_prep<D><<<(Mpad + 255) / 256, 256, 0, c->stream>>>(M, Mpad, kp.c, y, nullptr, nullptr, 0.f, nullptr,
+                                                       (float *)c->recq.ptr);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  Sched sc;
+  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc, M,
+                                                                             (const float *)c->recq.ptr)));
+  k_query_finish<D><<<(M + NT_FIN - 1) / NT_FIN, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, M,
+                                                                         exp(kp.lnorm), f_out, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;
@@ -749,4 +790,8 @@ int flow_impl(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
   }                                                                                           \
   int vds_flow_##DD(vds_ctx *c, const KParams &kp, const float *q, float *qs) {               \
     return vds_pair::flow_impl<DD>(c, kp, q, qs);                                             \
+  }                                                                                           \
+  int vds_query_##DD(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M,     \
+                     float *f) {                                                              \
+    return vds_pair::query_impl<DD>(c, kp, q, y, M, f);                                       \
   }

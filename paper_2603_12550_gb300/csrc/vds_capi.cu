@@ -168,7 +168,7 @@ void vds_destroy(vds_ctx *c) {
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf *bufs[] = {&c->rec, &c->part, &c->red, &c->vecs, &c->gbuf, &c->ubuf};
+  DevBuf *bufs[] = {&c->rec, &c->recq, &c->part, &c->red, &c->vecs, &c->gbuf, &c->ubuf};
   for (DevBuf *b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c->err) cudaFree(c->err);
@@ -237,6 +237,15 @@ int vds_energy_grad(vds_ctx *c, const float *q, int N, int D, const vds_params *
     *E = c->h_scal[SC_E];
   }
   return VDS_OK;
+}
+
+int vds_density_at(vds_ctx *c, const float *q, int N, int D, const vds_params *p, const float *y, int M,
+                   float *f) {
+  if (!c || !q || !y || !f || M < 1) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  return pass_density_at(c, kp, q, y, M, f);
 }
 
 static int step_explicit(vds_ctx *c, float *q, const KParams &kp, int nsteps) {

@@ -190,6 +190,7 @@ struct vds_ctx {
   cudaStream_t stream = nullptr;
   // workspace, grown on demand
   DevBuf rec;      // records (N_pad x DP floats)
+  DevBuf recq;     // records of query points (vds_density_at)
   DevBuf part;     // pair-pass partial sums (FP64)
   DevBuf red;      // block partials of reductions (FP64)
   DevBuf vecs;     // minimiser vectors / scratch (FP32)

@@ -78,6 +78,7 @@ _SIGS = {
     "vds_energy_grad": ([_vp, _vp, _i, _i, _pp, _vp, _dp, _vp, _vp], _i),
     "vds_step": ([_vp, _vp, _i, _i, _pp, _i, _ip], _i),
     "vds_stress": ([_vp, _vp, _i, _i, _pp, _dp, _dp], _i),
+    "vds_density_at": ([_vp, _vp, _i, _i, _pp, _vp, _i, _vp], _i),
     "vds_timing": ([_vp, _i], _i),
     "vds_energy_grad_noalloc": ([_vp, _i, _i, _pp, _dp, _vp, _vp, _vp], _i),
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
@@ -220,6 +221,12 @@ class Context:
         _check(lib.vds_stress(self.h, _ptr(q), N, D, ctypes.byref(p), tau, qq))
         s = p.s
         return (np.array(tau[:s * s]).reshape(s, s), np.array(qq[:]).reshape(D, D))
+
+    def vds_density_at(self, q, p: VdsParams, y, f):
+        """f[J] = kernel density estimate of the cloud q at query point y[J]."""
+        N, D = q.shape
+        M = int(y.shape[0])
+        _check(lib.vds_density_at(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(y), M, _ptr(f)))
 
     def pod_build(self, X, Ns, M, s, energy=0.9999, r_max=64, r_fixed=0, kappa=None):
         kap = np.zeros(9) if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64).ravel()

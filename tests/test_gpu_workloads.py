@@ -167,3 +167,28 @@ def test_time_step_convergence(vds, ctx):
             assert 0.35 < b / a < 0.65, (scheme, err)
     gap = [np.linalg.norm(run(dt, 0) - run(dt, 1)) / np.linalg.norm(ref) for dt in dts]
     assert gap[-1] < gap[0] and gap[-1] < 1e-2, gap
+
+
+def test_grid_density_error_is_first_order(orc, vds, ctx):
+    # Appendix A compares runs through their density estimates on the grid
+    # {-2, 0, 2}^D: for the 4-bead chain in shear (P = 1000) the l2 and
+    # l-infinity differences against a fine run halve with dt
+    P, nb, s, h, T = 1000, 3, 3, 0.9, 0.25
+    kap = inputs.shear_kappa(s, 1.0)
+    q0 = _dev(inputs.equilibrium_cloud(P, nb, s, seed=31))
+    G = _dev(orc.grid_points(nb * s))
+    f = torch.empty(G.shape[0], device="cuda")
+
+    def dens(dt):
+        q = q0.clone()
+        p = vds.params(nb, s, h=h, dt=dt, kappa=kap, scheme=0)
+        ctx.vds_step(q, p, int(round(T / dt)))
+        ctx.vds_density_at(q, p, G, f)
+        return f.cpu().numpy().astype(np.float64)
+
+    f0 = dens(T / 2000)
+    errs = [orc.density_error(dens(dt), f0) for dt in (1e-2, 5e-3, 2.5e-3)]
+    for k in (0, 1):
+        e = [x[k] for x in errs]
+        for a, b in zip(e, e[1:]):
+            assert 0.3 < b / a < 0.7, errs

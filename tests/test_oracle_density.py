@@ -113,3 +113,47 @@ def test_density_rows_are_the_density(orc):
     q = inputs.equilibrium_cloud(300, 3, 3, seed=4).astype(np.float64)
     rows = np.array([0, 7, 299, 150])
     np.testing.assert_array_equal(orc.density_rows(q, 0.8, rows), orc.density(q, 0.8)[rows])
+
+
+@pytest.mark.parametrize("N,nb,s,h,M", [(30, 1, 2, 0.4, 13), (21, 3, 3, 0.8, 7)])
+def test_density_at_matches_library_gaussian_mixture(orc, N, nb, s, h, M):
+    # f(y) = (1/N) sum_I N(y; q_I, h^2 I): the library pdf at arbitrary points
+    q = _cloud(N, nb, s, seed=N + 1)
+    D = nb * s
+    y = np.random.default_rng(M).standard_normal((M, D)) * 1.5
+    f = np.zeros(M)
+    for I in range(N):
+        f += multivariate_normal(mean=q[I], cov=h * h * np.eye(D)).pdf(y)
+    np.testing.assert_allclose(orc.density_at(q, h, y), f / N, rtol=1e-12)
+
+
+def test_density_at_the_particles_is_the_pair_density(orc):
+    # at the particles themselves the estimate is rho_I (1/N)(2 pi h^2)^{-D/2},
+    # rho from the C oracle's pair sum
+    q = _cloud(64, 3, 3, seed=5)
+    h = 0.7
+    f = orc.density_at(q, h, q)
+    np.testing.assert_allclose(f, orc.density(q, h) / 64 * (2 * np.pi * h * h) ** (-4.5), rtol=1e-13)
+
+
+def test_density_at_integrates_to_one():
+    # a probability density: its integral over the plane is 1 (2D cloud,
+    # midpoint rule on a grid covering the support)
+    import oracle
+    q = _cloud(25, 1, 2, seed=8)
+    h = 0.5
+    g = np.linspace(-8, 8, 321)
+    dx = g[1] - g[0]
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    f = oracle.density_at(q, h, np.stack([X.ravel(), Y.ravel()], axis=1), chunk=4096)
+    assert abs(f.sum() * dx * dx - 1.0) < 1e-9
+
+
+def test_grid_points_and_density_error():
+    import oracle
+    G = oracle.grid_points(2)
+    assert G.shape == (9, 2)
+    assert np.array_equal(G[1], [-2.0, 0.0]) and np.array_equal(G[-1], [2.0, 2.0])
+    assert oracle.grid_points(9).shape == (3 ** 9, 9)
+    e2, einf = oracle.density_error([1.0, 2.0, 2.0], [1.0, 2.0, 4.0])
+    assert np.isclose(e2, 2.0 / np.sqrt(21.0)) and np.isclose(einf, 0.5)
