@@ -10,18 +10,27 @@
 //
 // All three are one dense contraction W = Z B of the N x N kernel matrix
 // with the N x (2 s r + 1) matrix B = [Phi, Phi / rho, 1 / rho] (one row per
-// particle K): the shape of attention's P V.  Z never exists in memory: per
-// CTA of 128 particles I and per chunk of 32 particles K the CUDA cores form
-// Z_IK = exp2(-|q^_I - q^_K|^2) (2D FP32 ops and one ex2 per pair), split it
-// into two TF32 parts and store them in shared memory in the tensor cores'
-// K-major layout; one thread then issues tcgen05.mma of kind::tf32 against
-// the matching 32-row slice of B (pre-split into TF32 parts in global memory,
-// staged by cp.async).  TF32 with one refinement step: every product is
-// Z_hi B_hi + Z_hi B_lo + Z_lo B_hi (relative error about 2^-21).  The
-// accumulator (FP32, tensor memory) covers 512 particles K; after each such
-// segment it is added into FP32 registers (two-level summation, as in the
-// CUDA-core pair passes), so no FP32 sum runs over more than 512 terms.
-// Basis columns beyond 256 accumulator columns are split across grid.y.
+// particle K): the shape of attention's P V.  Z never exists in memory.  One
+// CTA per 128 particles I (and per column chunk of B), warp-specialised:
+//   warps 0-7   form Z_IK = exp2(-|q^_I - q^_K|^2) for a chunk of 32
+//               particles K (2D FP32 ops and one ex2 per pair, 4 x 4 pairs
+//               per thread), split it into two TF32 parts and store them in
+//               the tensor cores' K-major layout;
+//   warp 8      stages each chunk's 32 records and its B slice (hi and lo
+//               TF32 parts, pre-arranged in global memory as the exact
+//               shared-memory image) with 1-D bulk copies (TMA engine);
+//   warp 9      issues tcgen05.mma of kind::tf32 (M = 128, N = column chunk,
+//               K = 8; Z_hi B_hi + Z_hi B_lo + Z_lo B_hi: TF32 with one
+//               refinement step, relative error about 2^-21).
+// A ring of RC_NZ slots (records, B slice, Z tile) connects them through
+// mbarriers; nothing waits on a CTA-wide barrier inside the loop.  The
+// accumulator (FP32, tensor memory) covers one segment of 512 particles K
+// and is double-buffered: warps 0-7 add a finished segment into FP32
+// registers while the tensor cores fill the other buffer (two-level
+// summation, as in the CUDA-core pair passes: no FP32 sum runs over more
+// than 512 terms).  Every wait is bounded; a wait that runs out raises the
+// abort flag, every role leaves its loop, copies and MMAs in flight are
+// waited for and the tensor memory is freed.
 #include <math.h>
 
 #include "pair.cuh"
@@ -32,26 +41,27 @@ namespace {
 
 constexpr int RC_M = 128;    // particles I per CTA (MMA M, tensor-memory lanes)
 constexpr int RC_KC = 32;    // particles K per chunk (MMA K = 4 x 8)
-constexpr int RC_NT = 256;   // threads: 4 x 4 blocks of Z per chunk; two per TMEM lane in the flush
+constexpr int RC_PT = 256;   // Z-forming threads (warps 0-7): 4 x 4 blocks of Z per chunk
+constexpr int RC_NT = RC_PT + 64;  // + warp 8 (bulk copies) + warp 9 (MMA issue)
 constexpr int RC_SEG = 16;   // chunks per FP32 accumulator segment (512 K)
+constexpr int RC_FLUSH = 7;  // chunk of the next segment at which a segment is flushed
 constexpr int RC_ZOP = RC_M * RC_KC * 4;  // bytes of one Z operand tile (16 KB)
 
-// Shared memory: two Z slots (hi and lo tiles each), a 2-stage ring of B
-// slices (hi, lo) and a 3-stage ring of record tiles; the epilogue reuses it
-// for the per-particle totals.
+// Shared memory: RC_NZ slots of [Z hi | Z lo | B hi | B lo | records]; the
+// epilogue reuses it for the per-particle totals.
 template <int D, int NCP>
 struct RcLayout {
   static constexpr int DP = Rec<D>::DP;
-  static constexpr int BOP = NCP * RC_KC * 4;          // one B operand tile
-  static constexpr int REC = ((RC_KC * DP * 4 + 127) / 128) * 128;
-  static constexpr int ZOFF = 0;                       // slot z: + z * 2 ZOP (hi), + ZOP (lo)
-  static constexpr int BOFF = 4 * RC_ZOP;              // stage b: + b * 2 BOP (hi), + BOP (lo)
-  static constexpr int ROFF = BOFF + 4 * BOP;          // stage k: + k * REC
-  static constexpr int TOT_LD = NCP + 1;               // epilogue row stride (floats)
-  static constexpr size_t RING = (size_t)ROFF + 3 * REC;
+  static constexpr int BOP = NCP * RC_KC * 4;            // one B operand tile
+  static constexpr int REC_BYTES = RC_KC * DP * 4;       // records of one chunk
+  static constexpr int REC = ((REC_BYTES + 127) / 128) * 128;
+  static constexpr int SLOT = ((2 * RC_ZOP + 2 * BOP + REC + 1023) / 1024) * 1024;
+  static constexpr int NZ = (200 * 1024 / SLOT) < 4 ? (200 * 1024 / SLOT) : 4;
+  static constexpr int TOT_LD = NCP + 1;                 // epilogue row stride (floats)
+  static constexpr size_t RING = (size_t)NZ * SLOT;
   static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
-  // resident CTAs per SM (two need <= 128 registers: 4 rows of D <= 12 coordinates)
-  static constexpr int OCC = (SMEM <= 110 * 1024 && D <= 12) ? 2 : 1;
+  static_assert(NZ >= 2, "refresh ring depth");
+  static_assert(SMEM <= 227 * 1024 - 1024, "refresh shared memory");
 };
 
 // Column layout of B for column chunk cb (rc basis columns t0 .. t0+rc-1,
@@ -59,11 +69,13 @@ struct RcLayout {
 //   c = a rc + u          -> Phi_(K a)(t0+u)
 //   c = s rc + a rc + u   -> Phi_(K a)(t0+u) / rho_K
 //   c = 2 s rc            -> 1 / rho_K
-// zero elsewhere and for K >= N.  Stored transposed (row c, K contiguous) as
-// TF32 hi and lo parts: bt[(cb * NCP + c) * Npad + K].
+// zero elsewhere and for K >= N.  Stored as TF32 hi and lo parts, per
+// (column chunk, 32-particle chunk of K) the shared-memory image of the
+// tensor cores' K-major operand: element (c, k) at byte (c/8)*1024 +
+// (k/4)*128 + (c%8)*16 + (k%4)*4 of the hi tile, the lo tile BOP bytes after
+// it; image (cb, ch) at float offset ((cb * nch + ch) * 2 NCP RC_KC).
 __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int rr, const float *__restrict__ rec,
-                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bt_hi,
-                        float *__restrict__ bt_lo) {
+                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bimg) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y, cb = blockIdx.z;
   if (K >= Npad) return;
@@ -81,110 +93,175 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
       v = w;
     }
   }
+  const int nch = Npad / RC_KC, ch = K / RC_KC, k = K - ch * RC_KC;
+  const size_t tile = (size_t)NCP * RC_KC;
+  const size_t o = ((size_t)cb * nch + ch) * 2 * tile +
+                   (size_t)(((c >> 3) * 1024 + (k >> 2) * 128 + (c & 7) * 16 + (k & 3) * 4) >> 2);
   const float h = to_tf32(v);
-  const size_t o = ((size_t)cb * NCP + c) * Npad + K;
-  bt_hi[o] = h;
-  bt_lo[o] = to_tf32(v - h);
+  bimg[o] = h;
+  bimg[o + tile] = to_tf32(v - h);
 }
 
-// 16-byte cp.async staging of the record tile of chunk K0..K0+31, and of the
-// B^T slice (NCP rows x 32 K, hi and lo) in the tensor cores' K-major layout:
-// element (row c, k) at (c/8)*1024 + (k/4)*128 + (c%8)*16 + (k%4)*4.
-template <int DP>
-__device__ __forceinline__ void rc_load_rec(uint32_t dst, const float *__restrict__ rec, int K0) {
-  for (int idx = threadIdx.x; idx < RC_KC * DP / 4; idx += RC_NT)
-    cp_async16(dst + idx * 16, rec + (size_t)K0 * DP + idx * 4, true);
-}
-template <int NCP>
-__device__ __forceinline__ void rc_load_b(uint32_t dst, const float *__restrict__ bh, const float *__restrict__ bl,
-                                          int Npad, int K0) {
-  constexpr int BOP = NCP * RC_KC * 4;
-  for (int idx = threadIdx.x; idx < NCP * 8; idx += RC_NT) {
-    const int r8 = idx & 7, kc = (idx >> 3) & 7, g = idx >> 6;
-    const int row = g * 8 + r8;
-    const uint32_t off = g * 1024 + kc * 128 + r8 * 16;
-    const size_t src = (size_t)row * Npad + K0 + 4 * kc;
-    cp_async16(dst + off, bh + src, true);
-    cp_async16(dst + BOP + off, bl + src, true);
+// Wait that also gives up as soon as another role has aborted.
+__device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t n = 0;; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 63u) == 63u) {
+      if (*abort) return false;
+      if (global_timer_ns() - t0 > VDS_WAIT_LIMIT_NS) {
+        *abort = 1;
+        return false;
+      }
+    }
   }
 }
 
-// Per chunk ch: wait for the MMAs of chunk ch-1 (their B stage is refilled
-// next), stage B(ch+1) and the records of ch+2, form Z(ch) in Z slot ch % 2
-// while the tensor cores may still run nothing of this CTA (the other
-// resident CTA fills the gap), then one thread issues the 12 MMAs of ch.
+// Synchronisation per ring slot z (chunk ch uses slot ch % NZ; counts are
+// completions, u = ch / NZ):
+//   full[z]   bulk-copy bytes of records + B of chunk ch (completion u);
+//   zready[z] 256 arrivals: Z of chunk ch stored (completion u);
+//   sfree[z]  tcgen05.commit after the MMAs of chunk ch (completion u).
+// Per accumulator buffer b (segment g uses b = g & 1, v = g >> 1):
+//   segdone[b] commit after the last MMA of segment g (completion v);
+//   accfree[b] 256 arrivals: segment g added into registers (completion v).
 template <int D, int NCP>
-__global__ void __launch_bounds__(RC_NT, RcLayout<D, NCP>::OCC)
-    k_refresh_tc(const float *__restrict__ rec, int N, int Npad, const float *__restrict__ bt_hi,
-                 const float *__restrict__ bt_lo, const float *__restrict__ phi, int ld, int r, int s, int rr,
-                 float *__restrict__ U1, float *__restrict__ U2, int *err) {
+__global__ void __launch_bounds__(RC_NT, 1)
+    k_refresh_tc(const float *__restrict__ rec, int N, int Npad, const float *__restrict__ bimg,
+                 const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
+                 float *__restrict__ U2, int *err) {
   using L = RcLayout<D, NCP>;
   constexpr int DP = L::DP;
-  constexpr int HALF = NCP / 2;  // accumulator columns per thread
+  constexpr int NZ = L::NZ;
+  constexpr int HALF = NCP / 2;  // accumulator columns per thread in a flush
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t full[NZ], zready[NZ], sfree[NZ], segdone[2], accfree[2], fin;
   __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int il = (warp & 3) * 32 + lane;  // row of the tile = tensor-memory lane
-  const int kh = warp >> 2;               // which 16 K of a chunk, and which column half
   const int i0 = blockIdx.x * RC_M;
   const int cb = blockIdx.y;
-  const float *bh = bt_hi + (size_t)cb * NCP * Npad, *bl = bt_lo + (size_t)cb * NCP * Npad;
   const int nch = Npad / RC_KC;
-  if (warp == 0) tc_alloc(&s_tmem, NCP);
+  const int nseg = (nch + RC_SEG - 1) / RC_SEG;
+  volatile int *abort = &s_abort;
+  if (warp == 0) tc_alloc(&s_tmem, 2 * NCP);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    for (int z = 0; z < NZ; ++z) {
+      mbar_init(&full[z], 1);
+      mbar_init(&zready[z], RC_PT);
+      mbar_init(&sfree[z], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&segdone[b], 1);
+      mbar_init(&accfree[b], RC_PT);
+    }
+    mbar_init(&fin, 1);
+    s_abort = 0;
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP);
   const uint32_t sbase = smem_u32(sm);
-  // Z is formed in 4 x 4 blocks: rows rg + 32 m (m < 4) and the 4 K of
-  // k-group jg of the chunk, so each staged record is read once per 4 pairs
-  const int rg = tid & 31, jg = tid >> 5;
-  float xi[4][D];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int i = min(i0 + rg + 32 * m, Npad - 1);
-#pragma unroll
-    for (int d = 0; d < D; ++d) xi[m][d] = rec[(size_t)i * DP + d];
-  }
   float tot[HALF];
-#pragma unroll
-  for (int j = 0; j < HALF; ++j) tot[j] = 0.f;
-
-  // prologue: records of chunks 0 and 1, B of chunk 0
-  rc_load_rec<DP>(sbase + L::ROFF, rec, 0);
-  if (nch > 1) rc_load_rec<DP>(sbase + L::ROFF + L::REC, rec, RC_KC);
-  rc_load_b<NCP>(sbase + L::BOFF, bh, bl, Npad, 0);
-  cp_async_commit();
   bool ok = true;
-  int last = -1;
-  for (int ch = 0; ch < nch; ++ch) {
-    if (ch >= 1) {
-      const int pc = ch - 1;
-      const bool got = mbar_wait_bounded(&bars[pc & 1], (uint32_t)((pc >> 1) & 1), VDS_WAIT_LIMIT_NS);
-      if (__syncthreads_or(!got)) {
+
+  if (warp == 8) {
+    // ---------------------------------------------------- bulk copies
+    if (lane == 0) {
+      const float *bsrc = bimg + (size_t)cb * nch * 2 * NCP * RC_KC;
+      int ch = 0;
+      for (; ch < nch; ++ch) {
+        const int z = ch % NZ;
+        if (ch >= NZ && !rc_wait(&sfree[z], (uint32_t)((ch / NZ - 1) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        uint8_t *slot = sm + (size_t)z * L::SLOT;
+        mbar_arrive_expect_tx(&full[z], (uint32_t)(L::REC_BYTES + 2 * L::BOP));
+        bulk_g2s(slot + 2 * RC_ZOP + 2 * L::BOP, rec + (size_t)ch * RC_KC * DP, L::REC_BYTES, &full[z]);
+        bulk_g2s(slot + 2 * RC_ZOP, bsrc + (size_t)ch * 2 * NCP * RC_KC, 2 * L::BOP, &full[z]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      // the copies still in flight land before the CTA may exit
+      for (int k = ch > NZ ? ch - NZ : 0; k < ch; ++k)
+        mbar_wait_bounded(&full[k % NZ], (uint32_t)((k / NZ) & 1), VDS_WAIT_LIMIT_NS);
+    }
+  } else if (warp == 9) {
+    // ---------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP);
+      for (int ch = 0; ch < nch && ok; ++ch) {
+        const int z = ch % NZ, g = ch / RC_SEG, b = g & 1;
+        if (ch % RC_SEG == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        if (!rc_wait(&zready[z], (uint32_t)((ch / NZ) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t zh = sbase + (uint32_t)(z * L::SLOT), zl = zh + RC_ZOP;
+        const uint32_t b_hi = zh + 2 * RC_ZOP, b_lo = b_hi + L::BOP;
+        const uint32_t acc = tmem + (uint32_t)(b * NCP);
+#pragma unroll
+        for (int k = 0; k < RC_KC / 8; ++k) {
+          const uint32_t o = (uint32_t)k * 256u;
+          const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
+          tc_mma_tf32(acc, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, first);
+          tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_lo + o), idesc, 1);
+          tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc, 1);
+        }
+        tc_commit(&sfree[z]);
+        if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+    }
+  } else {
+    // ---------------------------------------------------- Z formation
+    // rows rg + 32 m (m < 4) and the 4 K of k-group jg of each chunk, so each
+    // staged record is read once per 4 pairs; element (row i, k) of a Z tile
+    // at (i/8)*1024 + (k/4)*128 + (i%8)*16 + (k%4)*4, so a row's 4 K of one
+    // k-group are one float4
+    const int rg = tid & 31, jg = tid >> 5;
+    const int q4 = warp & 3, kh = warp >> 2;  // flush: TMEM lanes 32 q4 .., column half kh
+    float xi[4][D];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = min(i0 + rg + 32 * m, Npad - 1);
+#pragma unroll
+      for (int d = 0; d < D; ++d) xi[m][d] = rec[(size_t)i * DP + d];
+    }
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) tot[j] = 0.f;
+    auto flush = [&](int g) -> bool {
+      const int b = g & 1;
+      if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
+      tc_fence_after();
+#pragma unroll
+      for (int c0 = 0; c0 < HALF; c0 += 16) {
+        uint32_t v[16];
+        tc_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NCP + kh * HALF + c0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tot[c0 + j] += __uint_as_float(v[j]);
+      }
+      tc_fence_before();
+      mbar_arrive(&accfree[b]);
+      return true;
+    };
+    int flushed = 0;  // segments added into registers
+    for (int ch = 0; ch < nch && ok; ++ch) {
+      const int z = ch % NZ;
+      if (!__all_sync(0xffffffffu, rc_wait(&full[z], (uint32_t)((ch / NZ) & 1), abort))) {
         ok = false;
         break;
       }
-    }
-    if (ch + 1 < nch) rc_load_b<NCP>(sbase + L::BOFF + ((ch + 1) & 1) * 2 * L::BOP, bh, bl, Npad, (ch + 1) * RC_KC);
-    if (ch + 2 < nch) rc_load_rec<DP>(sbase + L::ROFF + ((ch + 2) % 3) * L::REC, rec, (ch + 2) * RC_KC);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    // Z block of this thread as TF32 hi / lo; element (row i, k) of a Z tile
-    // at (i/8)*1024 + (k/4)*128 + (i%8)*16 + (k%4)*4, so a row's 4 K of one
-    // k-group are one float4
-    uint8_t *zslot = sm + L::ZOFF + (ch & 1) * 2 * RC_ZOP;
-    {
-      const float *rs = reinterpret_cast<const float *>(sm + L::ROFF + (ch % 3) * L::REC) + jg * 4 * DP;
-      float z[4][4];
+      uint8_t *slot = sm + (size_t)z * L::SLOT;
+      const float *rs = reinterpret_cast<const float *>(slot + 2 * RC_ZOP + 2 * L::BOP) + jg * 4 * DP;
+      float zz[4][4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float xj[D];
@@ -198,7 +275,7 @@ __global__ void __launch_bounds__(RC_NT, RcLayout<D, NCP>::OCC)
             const float dd = xi[m][d] - xj[d];
             r2 = fmaf(dd, dd, r2);
           }
-          z[m][u] = ex2_approx(-r2);
+          zz[m][u] = ex2_approx(-r2);
         }
       }
 #pragma unroll
@@ -206,67 +283,52 @@ __global__ void __launch_bounds__(RC_NT, RcLayout<D, NCP>::OCC)
         const int row = rg + 32 * m;
         const size_t off = (size_t)(row >> 3) * 1024 + (row & 7) * 16 + jg * 128;
         float4 h, l;
-        h.x = to_tf32(z[m][0]);
-        h.y = to_tf32(z[m][1]);
-        h.z = to_tf32(z[m][2]);
-        h.w = to_tf32(z[m][3]);
-        l.x = to_tf32(z[m][0] - h.x);
-        l.y = to_tf32(z[m][1] - h.y);
-        l.z = to_tf32(z[m][2] - h.z);
-        l.w = to_tf32(z[m][3] - h.w);
-        *reinterpret_cast<float4 *>(zslot + off) = h;
-        *reinterpret_cast<float4 *>(zslot + RC_ZOP + off) = l;
+        h.x = to_tf32(zz[m][0]);
+        h.y = to_tf32(zz[m][1]);
+        h.z = to_tf32(zz[m][2]);
+        h.w = to_tf32(zz[m][3]);
+        l.x = to_tf32(zz[m][0] - h.x);
+        l.y = to_tf32(zz[m][1] - h.y);
+        l.z = to_tf32(zz[m][2] - h.z);
+        l.w = to_tf32(zz[m][3] - h.w);
+        *reinterpret_cast<float4 *>(slot + off) = h;
+        *reinterpret_cast<float4 *>(slot + RC_ZOP + off) = l;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive(&zready[z]);
+      // segment g - 1 is added into registers part-way through segment g
+      if (ch % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
+        if (!flush(ch / RC_SEG - 1)) {
+          ok = false;
+          break;
+        }
+        ++flushed;
       }
     }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t zh = sbase + L::ZOFF + (ch & 1) * 2 * RC_ZOP, zl = zh + RC_ZOP;
-      const uint32_t b_hi = sbase + L::BOFF + (ch & 1) * 2 * L::BOP, b_lo = b_hi + L::BOP;
-#pragma unroll
-      for (int k = 0; k < RC_KC / 8; ++k) {
-        const uint32_t o = (uint32_t)k * 256u;
-        const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
-        tc_mma_tf32(tmem, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, first);
-        tc_mma_tf32(tmem, tc_sdesc(zh + o), tc_sdesc(b_lo + o), idesc, 1);
-        tc_mma_tf32(tmem, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc, 1);
-      }
-      tc_commit(&bars[ch & 1]);
-    }
-    last = ch;
-    if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) {
-      const bool got = mbar_wait_bounded(&bars[ch & 1], (uint32_t)((ch >> 1) & 1), VDS_WAIT_LIMIT_NS);
-      if (__syncthreads_or(!got)) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll
-      for (int c0 = 0; c0 < HALF; c0 += 16) {
-        uint32_t v[16];
-        tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(kh * HALF + c0), v);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) tot[c0 + j] += __uint_as_float(v[j]);
-      }
-      tc_fence_before();
-    }
+    for (; ok && flushed < nseg; ++flushed)
+      if (!flush(flushed)) ok = false;
+    if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
   }
-  cp_async_wait<0>();
-  if (!ok) {
-    if (tid == 0 && last >= 0)
-      mbar_wait_bounded(&bars[last & 1], (uint32_t)((last >> 1) & 1), VDS_WAIT_LIMIT_NS / 8);
-    if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
+  // every role has left its loop; the MMAs issued are complete before the
+  // tensor memory and shared memory are released
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 9 && lane == 0) {
+    tc_commit(&fin);
+    mbar_wait_bounded(&fin, 0, VDS_WAIT_LIMIT_NS);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, NCP);
-  if (!ok) return;
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, 2 * NCP);
+  if (*abort) return;
   // epilogue: totals through shared memory, then U1, U2 per (I, a, t)
   float *T = reinterpret_cast<float *>(sm);
+  if (tid < RC_PT) {
+    const int il = (warp & 3) * 32 + lane, kh = warp >> 2;
 #pragma unroll
-  for (int j = 0; j < HALF; ++j) T[il * L::TOT_LD + kh * HALF + j] = tot[j];
+    for (int j = 0; j < HALF; ++j) T[il * L::TOT_LD + kh * HALF + j] = tot[j];
+  }
   __syncthreads();
   const int t0 = cb * rr;
   const int rc = min(rr, r - t0);
@@ -286,13 +348,13 @@ __global__ void __launch_bounds__(RC_NT, RcLayout<D, NCP>::OCC)
 }
 
 template <int D, int NCP>
-int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bh,
-                   const float *bl, float *U1, float *U2) {
+int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
+                   float *U1, float *U2) {
   using L = RcLayout<D, NCP>;
   VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L::SMEM));
   dim3 grid((N + RC_M - 1) / RC_M, ncb);
-  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, N, Npad, bh, bl, b->phi,
+  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, N, Npad, bimg, b->phi,
                                                              b->ld, b->r, b->s, rr, U1, U2, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
@@ -312,17 +374,17 @@ int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
   const int Npad = pass_npad(N);
   const size_t nbt = (size_t)ncb * NCP * Npad;
   VDS_TRY(vds_ensure(c, c->gbuf, 2 * nbt * sizeof(float)));
-  float *bh = (float *)c->gbuf.ptr, *bl = bh + nbt;
+  float *bimg = (float *)c->gbuf.ptr;
   k_rc_bt<<<dim3((Npad + 255) / 256, NCP, ncb), 256, 0, c->stream>>>(b->phi, b->ld, r, s, rr,
                                                                      (const float *)c->rec.ptr, Rec<D>::DP, D,
-                                                                     N, Npad, NCP, bh, bl);
+                                                                     N, Npad, NCP, bimg);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   switch (NCP) {
-    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bh, bl, U1, U2);
-    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bh, bl, U1, U2);
-    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bh, bl, U1, U2);
-    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bh, bl, U1, U2);
+    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
+    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
+    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
+    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
   }
 }
 

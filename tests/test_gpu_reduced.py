@@ -151,3 +151,27 @@ def test_score_check_falls_back_to_exact(vds, ctx, setup):
     assert nf == 3 and err > 0.0
     ctx.pod_step(S["basis"], P2, S["N"], D, S["pg"], nsteps=3, mode=1)
     assert _rel(P1.cpu().numpy(), P2.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.parametrize("N,nb,s,r", [(1000, 3, 3, 5), (1000, 3, 3, 20), (777, 2, 3, 42), (1300, 3, 3, 64),
+                                      (2000, 4, 2, 30), (129, 1, 3, 3)])
+def test_brownian_matrices_every_column_chunk_shape(orc, vds, ctx, N, nb, s, r):
+    # the refresh pass for every width of its B slice (2 s r + 1 columns padded
+    # to 32, 64, 128 or 256; r = 64 with s = 3 takes two column chunks), ragged
+    # N, and a segment count that is not a multiple of the flush schedule:
+    # X^B1 and X^B2 at the lifted state against the oracle
+    D = nb * s
+    rng = np.random.default_rng(N + r)
+    Phi, _ = np.linalg.qr(rng.standard_normal((N * s, r)))
+    Phi32 = np.ascontiguousarray(Phi.astype(np.float32))
+    basis = ctx.pod_load(torch.from_numpy(Phi32).cuda(), s)
+    q0 = inputs.equilibrium_cloud(N, nb, s, seed=N).astype(np.float64)
+    P = orc.project(Phi32.astype(np.float64), q0, s, nb)
+    qt = orc.lift(Phi32.astype(np.float64), P.astype(np.float32).astype(np.float64), s, nb)
+    h = 0.8
+    B1o, B2o, _ = orc.x_b(Phi32.astype(np.float64), qt, h, s)
+    B1, B2 = ctx.pod_brownian(basis, torch.from_numpy(np.ascontiguousarray(P.astype(np.float32))).cuda(), N, D,
+                              vds.params(nb, s, h=h))
+    assert _rel(B1, B1o) <= 1e-4, _rel(B1, B1o)
+    assert _rel(B2, B2o) <= 1e-4, _rel(B2, B2o)
+    basis.free()
