@@ -12,20 +12,20 @@
 // with the N x (2 s r + 1) matrix B = [Phi, Phi / rho, 1 / rho] (one row per
 // particle K): the shape of attention's P V.  Z never exists in memory.  One
 // CTA per 128 particles I (and per column chunk of B), warp-specialised:
-//   warps 0-7   form Z_IK = exp2(-|q^_I - q^_K|^2) for a chunk of 32
-//               particles K (2D FP32 ops and one ex2 per pair, 4 x 4 pairs
+//   warps 0-15  form Z_IK = exp2(-|q^_I - q^_K|^2) for a chunk of 32
+//               particles K (2D FP32 ops and one ex2 per pair, 2 x 4 pairs
 //               per thread), split it into two TF32 parts and store them in
 //               the tensor cores' K-major layout;
-//   warp 8      stages each chunk's 32 records and its B slice (hi and lo
+//   warp 16     stages each chunk's 32 records and its B slice (hi and lo
 //               TF32 parts, pre-arranged in global memory as the exact
 //               shared-memory image) with 1-D bulk copies (TMA engine);
-//   warp 9      issues tcgen05.mma of kind::tf32 (M = 128, N = column chunk,
+//   warp 17     issues tcgen05.mma of kind::tf32 (M = 128, N = column chunk,
 //               K = 8; Z_hi B_hi + Z_hi B_lo + Z_lo B_hi: TF32 with one
 //               refinement step, relative error about 2^-21).
 // A ring of RC_NZ slots (records, B slice, Z tile) connects them through
 // mbarriers; nothing waits on a CTA-wide barrier inside the loop.  The
 // accumulator (FP32, tensor memory) covers one segment of 512 particles K
-// and is double-buffered: warps 0-7 add a finished segment into FP32
+// and is double-buffered: warps 0-15 add a finished segment into FP32
 // registers while the tensor cores fill the other buffer (two-level
 // summation, as in the CUDA-core pair passes: no FP32 sum runs over more
 // than 512 terms).  Every wait is bounded; a wait that runs out raises the
@@ -41,22 +41,28 @@ namespace {
 
 constexpr int RC_M = 128;    // particles I per CTA (MMA M, tensor-memory lanes)
 constexpr int RC_KC = 32;    // particles K per chunk (MMA K = 4 x 8)
-constexpr int RC_PT = 256;   // Z-forming threads (warps 0-7): 4 x 4 blocks of Z per chunk
-constexpr int RC_NT = RC_PT + 64;  // + warp 8 (bulk copies) + warp 9 (MMA issue)
+constexpr int RC_PW = 16;    // Z-forming warps: 2 rows x 4 K blocks of Z per thread and chunk
+constexpr int RC_PT = RC_PW * 32;
+constexpr int RC_NT = RC_PT + 64;  // + one warp of bulk copies + one warp of MMA issue
 constexpr int RC_SEG = 16;   // chunks per FP32 accumulator segment (512 K)
 constexpr int RC_FLUSH = 7;  // chunk of the next segment at which a segment is flushed
 constexpr int RC_ZOP = RC_M * RC_KC * 4;  // bytes of one Z operand tile (16 KB)
 
-// Shared memory: RC_NZ slots of [Z hi | Z lo | B hi | B lo | records]; the
-// epilogue reuses it for the per-particle totals.
+// Shared memory: NZ slots of [Z hi | Z lo | B hi | B lo | records] (no Z
+// tiles when Z goes to tensor memory, TA); the epilogue reuses it for the
+// per-particle totals.
 template <int D, int NCP>
 struct RcLayout {
   static constexpr int DP = Rec<D>::DP;
+  static constexpr bool TA = NCP <= 64;                  // Z tiles in tensor memory
   static constexpr int BOP = NCP * RC_KC * 4;            // one B operand tile
   static constexpr int REC_BYTES = RC_KC * DP * 4;       // records of one chunk
   static constexpr int REC = ((REC_BYTES + 127) / 128) * 128;
-  static constexpr int SLOT = ((2 * RC_ZOP + 2 * BOP + REC + 1023) / 1024) * 1024;
-  static constexpr int NZ = (200 * 1024 / SLOT) < 4 ? (200 * 1024 / SLOT) : 4;
+  static constexpr int ZB = TA ? 0 : 2 * RC_ZOP;         // Z tiles of a slot
+  static constexpr int BOFF = ZB;                        // B hi, then B lo
+  static constexpr int ROFF = ZB + 2 * BOP;              // records
+  static constexpr int SLOT = ((ZB + 2 * BOP + REC + 1023) / 1024) * 1024;
+  static constexpr int NZ = TA ? 4 : ((200 * 1024 / SLOT) < 4 ? (200 * 1024 / SLOT) : 4);
   static constexpr int TOT_LD = NCP + 1;                 // epilogue row stride (floats)
   static constexpr size_t RING = (size_t)NZ * SLOT;
   static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
@@ -121,31 +127,46 @@ __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile
 // Synchronisation per ring slot z (chunk ch uses slot ch % NZ; counts are
 // completions, u = ch / NZ):
 //   full[z]   bulk-copy bytes of records + B of chunk ch (completion u);
-//   zready[z] 256 arrivals: Z of chunk ch stored (completion u);
+//   zready[z] RC_PT arrivals: Z of chunk ch stored (completion u);
 //   sfree[z]  tcgen05.commit after the MMAs of chunk ch (completion u).
 // Per accumulator buffer b (segment g uses b = g & 1, v = g >> 1):
 //   segdone[b] commit after the last MMA of segment g (completion v);
-//   accfree[b] 256 arrivals: segment g added into registers (completion v).
+//   accfree[b] RC_PT arrivals: segment g added into registers (completion v).
 template <int D, int NCP>
 __global__ void __launch_bounds__(RC_NT, 1)
     k_refresh_tc(const float *__restrict__ rec, int N, int Npad, const float *__restrict__ bimg,
                  const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
-                 float *__restrict__ U2, int *err) {
+                 float *__restrict__ U2, int nsplit, float *__restrict__ part, int *err) {
   using L = RcLayout<D, NCP>;
   constexpr int DP = L::DP;
   constexpr int NZ = L::NZ;
-  constexpr int HALF = NCP / 2;  // accumulator columns per thread in a flush
+  constexpr int QC = NCP / 4;  // accumulator columns per thread in a flush
+  // NCP <= 128: one MMA takes Z_hi against [B_hi; B_lo] (N = 2 NCP), so Z_hi
+  // is read from shared memory once per K step; the two halves of the
+  // accumulator are added at the flush.  NCP = 256: three MMAs of N = NCP.
+  constexpr bool FB = NCP <= 128;
+  constexpr int ACW = FB ? 2 * NCP : NCP;  // accumulator columns per buffer
+  // NCP <= 64 (TA): Z goes to tensor memory (tcgen05.st) and is the MMAs' A
+  // operand there, slot z at columns 2 ACW + 64 z (hi) and + 32 (lo); shared
+  // memory then carries only B and the records
+  constexpr bool TA = L::TA;
+  constexpr int TCOLS = TA ? 512 : 2 * ACW;
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t full[NZ], zready[NZ], sfree[NZ], segdone[2], accfree[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i0 = blockIdx.x * RC_M;
+  // CTA = (row tile, split of the K range into whole segments, column chunk)
+  const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+  const int i0 = tile * RC_M;
   const int cb = blockIdx.y;
-  const int nch = Npad / RC_KC;
-  const int nseg = (nch + RC_SEG - 1) / RC_SEG;
+  const int nch_all = Npad / RC_KC, nseg_all = (nch_all + RC_SEG - 1) / RC_SEG;
+  const int sg0 = split * nseg_all / nsplit, sg1 = (split + 1) * nseg_all / nsplit;
+  const int c0 = sg0 * RC_SEG;                                  // first chunk of this CTA
+  const int nch = min(sg1 * RC_SEG, nch_all) - c0;              // chunks of this CTA (local index ch)
+  const int nseg = sg1 - sg0;
   volatile int *abort = &s_abort;
-  if (warp == 0) tc_alloc(&s_tmem, 2 * NCP);
+  if (warp == 0) tc_alloc(&s_tmem, TCOLS);
   if (tid == 0) {
     for (int z = 0; z < NZ; ++z) {
       mbar_init(&full[z], 1);
@@ -165,13 +186,13 @@ __global__ void __launch_bounds__(RC_NT, 1)
   tc_fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t sbase = smem_u32(sm);
-  float tot[HALF];
+  float tot[QC];
   bool ok = true;
 
-  if (warp == 8) {
+  if (warp == RC_PW) {
     // ---------------------------------------------------- bulk copies
     if (lane == 0) {
-      const float *bsrc = bimg + (size_t)cb * nch * 2 * NCP * RC_KC;
+      const float *bsrc = bimg + ((size_t)cb * nch_all + c0) * 2 * NCP * RC_KC;
       int ch = 0;
       for (; ch < nch; ++ch) {
         const int z = ch % NZ;
@@ -181,18 +202,18 @@ __global__ void __launch_bounds__(RC_NT, 1)
         }
         uint8_t *slot = sm + (size_t)z * L::SLOT;
         mbar_arrive_expect_tx(&full[z], (uint32_t)(L::REC_BYTES + 2 * L::BOP));
-        bulk_g2s(slot + 2 * RC_ZOP + 2 * L::BOP, rec + (size_t)ch * RC_KC * DP, L::REC_BYTES, &full[z]);
-        bulk_g2s(slot + 2 * RC_ZOP, bsrc + (size_t)ch * 2 * NCP * RC_KC, 2 * L::BOP, &full[z]);
+        bulk_g2s(slot + L::ROFF, rec + (size_t)(c0 + ch) * RC_KC * DP, L::REC_BYTES, &full[z]);
+        bulk_g2s(slot + L::BOFF, bsrc + (size_t)ch * 2 * NCP * RC_KC, 2 * L::BOP, &full[z]);
       }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
       // the copies still in flight land before the CTA may exit
       for (int k = ch > NZ ? ch - NZ : 0; k < ch; ++k)
         mbar_wait_bounded(&full[k % NZ], (uint32_t)((k / NZ) & 1), VDS_WAIT_LIMIT_NS);
     }
-  } else if (warp == 9) {
+  } else if (warp == RC_PW + 1) {
     // ---------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP);
+      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP), idesc2 = tc_idesc(TC_FMT_TF32, RC_M, ACW);
       for (int ch = 0; ch < nch && ok; ++ch) {
         const int z = ch % NZ, g = ch / RC_SEG, b = g & 1;
         if (ch % RC_SEG == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
@@ -205,15 +226,25 @@ __global__ void __launch_bounds__(RC_NT, 1)
         }
         tc_fence_after();
         const uint32_t zh = sbase + (uint32_t)(z * L::SLOT), zl = zh + RC_ZOP;
-        const uint32_t b_hi = zh + 2 * RC_ZOP, b_lo = b_hi + L::BOP;
-        const uint32_t acc = tmem + (uint32_t)(b * NCP);
+        const uint32_t b_hi = zh + L::BOFF, b_lo = b_hi + L::BOP;
+        const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * z);  // TA: Z hi columns, lo at + 32
+        const uint32_t acc = tmem + (uint32_t)(b * ACW);
 #pragma unroll
         for (int k = 0; k < RC_KC / 8; ++k) {
           const uint32_t o = (uint32_t)k * 256u;
           const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
-          tc_mma_tf32(acc, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, first);
-          tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_lo + o), idesc, 1);
-          tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc, 1);
+          if constexpr (TA) {
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, 1);
+          } else if constexpr (FB) {
+            // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
+            tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_tf32(acc, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, 1);
+          } else {
+            tc_mma_tf32(acc, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, first);
+            tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_lo + o), idesc, 1);
+            tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc, 1);
+          }
         }
         tc_commit(&sfree[z]);
         if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
@@ -222,31 +253,39 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
   } else {
     // ---------------------------------------------------- Z formation
-    // rows rg + 32 m (m < 4) and the 4 K of k-group jg of each chunk, so each
-    // staged record is read once per 4 pairs; element (row i, k) of a Z tile
-    // at (i/8)*1024 + (k/4)*128 + (i%8)*16 + (k%4)*4, so a row's 4 K of one
-    // k-group are one float4
-    const int rg = tid & 31, jg = tid >> 5;
-    const int q4 = warp & 3, kh = warp >> 2;  // flush: TMEM lanes 32 q4 .., column half kh
-    float xi[4][D];
+    // TA: thread = row 32 (warp % 4) + lane (its tensor-memory lane), the 8 K
+    // of quarter warp / 4 of each chunk.  Otherwise rows rg + 32 (2 mh + m)
+    // (m < 2) and the 4 K of k-group jg of each chunk; element (row i, k) of
+    // a shared-memory Z tile at (i/8)*1024 + (k/4)*128 + (i%8)*16 + (k%4)*4,
+    // so a row's 4 K of one k-group are one float4
+    constexpr int RPT = TA ? 1 : 2;  // rows per thread
+    const int rg = lane, jg = warp & 7, mh = warp >> 3;
+    const int q4 = warp & 3, cq = warp >> 2;  // flush (and TA rows): TMEM lanes 32 q4 .., column quarter cq
+    float xi[RPT][D];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int i = min(i0 + rg + 32 * m, Npad - 1);
+    for (int m = 0; m < RPT; ++m) {
+      const int i = min(i0 + (TA ? 32 * q4 + lane : rg + 32 * (2 * mh + m)), Npad - 1);
 #pragma unroll
       for (int d = 0; d < D; ++d) xi[m][d] = rec[(size_t)i * DP + d];
     }
 #pragma unroll
-    for (int j = 0; j < HALF; ++j) tot[j] = 0.f;
+    for (int j = 0; j < QC; ++j) tot[j] = 0.f;
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
       tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * ACW + cq * QC);
 #pragma unroll
-      for (int c0 = 0; c0 < HALF; c0 += 16) {
+      for (int c0 = 0; c0 < QC; c0 += 16) {
         uint32_t v[16];
-        tc_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * NCP + kh * HALF + c0), v);
+        tc_ld16(ta + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j) tot[c0 + j] += __uint_as_float(v[j]);
+        if constexpr (FB) {
+          tc_ld16(ta + (uint32_t)(NCP + c0), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[c0 + j] += __uint_as_float(v[j]);
+        }
       }
       tc_fence_before();
       mbar_arrive(&accfree[b]);
@@ -260,41 +299,65 @@ __global__ void __launch_bounds__(RC_NT, 1)
         break;
       }
       uint8_t *slot = sm + (size_t)z * L::SLOT;
-      const float *rs = reinterpret_cast<const float *>(slot + 2 * RC_ZOP + 2 * L::BOP) + jg * 4 * DP;
-      float zz[4][4];
+      if constexpr (TA) {
+        tc_fence_after();  // the MMAs that read this Z slot have completed
+        const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + cq * 8 * DP;
+        uint32_t hv[8], lv[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float xj[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) xj[d] = rs[u * DP + d];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
+        for (int u = 0; u < 8; ++u) {
           float r2 = 0.f;
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            const float dd = xi[m][d] - xj[d];
+            const float dd = xi[0][d] - rs[u * DP + d];
             r2 = fmaf(dd, dd, r2);
           }
-          zz[m][u] = ex2_approx(-r2);
+          const float zv = ex2_approx(-r2);
+          const float h = to_tf32(zv);
+          hv[u] = __float_as_uint(h);
+          lv[u] = __float_as_uint(to_tf32(zv - h));
         }
+        const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 64 * z + 8 * cq);
+        tc_st8(zt, hv);
+        tc_st8(zt + 32u, lv);
+        tc_wait_st();
+        tc_fence_before();
+      } else {
+        const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + jg * 4 * DP;
+        float zz[2][4];
+  #pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          float xj[D];
+  #pragma unroll
+          for (int d = 0; d < D; ++d) xj[d] = rs[u * DP + d];
+  #pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            float r2 = 0.f;
+  #pragma unroll
+            for (int d = 0; d < D; ++d) {
+              const float dd = xi[m][d] - xj[d];
+              r2 = fmaf(dd, dd, r2);
+            }
+            zz[m][u] = ex2_approx(-r2);
+          }
+        }
+  #pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const int row = rg + 32 * (2 * mh + m);
+          const size_t off = (size_t)(row >> 3) * 1024 + (row & 7) * 16 + jg * 128;
+          float4 h, l;
+          h.x = to_tf32(zz[m][0]);
+          h.y = to_tf32(zz[m][1]);
+          h.z = to_tf32(zz[m][2]);
+          h.w = to_tf32(zz[m][3]);
+          l.x = to_tf32(zz[m][0] - h.x);
+          l.y = to_tf32(zz[m][1] - h.y);
+          l.z = to_tf32(zz[m][2] - h.z);
+          l.w = to_tf32(zz[m][3] - h.w);
+          *reinterpret_cast<float4 *>(slot + off) = h;
+          *reinterpret_cast<float4 *>(slot + RC_ZOP + off) = l;
+        }
+        fence_proxy_async_smem();
       }
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int row = rg + 32 * m;
-        const size_t off = (size_t)(row >> 3) * 1024 + (row & 7) * 16 + jg * 128;
-        float4 h, l;
-        h.x = to_tf32(zz[m][0]);
-        h.y = to_tf32(zz[m][1]);
-        h.z = to_tf32(zz[m][2]);
-        h.w = to_tf32(zz[m][3]);
-        l.x = to_tf32(zz[m][0] - h.x);
-        l.y = to_tf32(zz[m][1] - h.y);
-        l.z = to_tf32(zz[m][2] - h.z);
-        l.w = to_tf32(zz[m][3] - h.w);
-        *reinterpret_cast<float4 *>(slot + off) = h;
-        *reinterpret_cast<float4 *>(slot + RC_ZOP + off) = l;
-      }
-      fence_proxy_async_smem();
       mbar_arrive(&zready[z]);
       // segment g - 1 is added into registers part-way through segment g
       if (ch % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
@@ -320,16 +383,22 @@ __global__ void __launch_bounds__(RC_NT, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tc_dealloc(tmem, 2 * NCP);
+  if (warp == 0) tc_dealloc(tmem, TCOLS);
   if (*abort) return;
-  // epilogue: totals through shared memory, then U1, U2 per (I, a, t)
+  // epilogue: totals through shared memory, then U1, U2 per (I, a, t), or
+  // this split's totals into part (summed over the splits by k_rc_fin)
   float *T = reinterpret_cast<float *>(sm);
   if (tid < RC_PT) {
-    const int il = (warp & 3) * 32 + lane, kh = warp >> 2;
+    const int il = (warp & 3) * 32 + lane, cq = warp >> 2;
 #pragma unroll
-    for (int j = 0; j < HALF; ++j) T[il * L::TOT_LD + kh * HALF + j] = tot[j];
+    for (int j = 0; j < QC; ++j) T[il * L::TOT_LD + cq * QC + j] = tot[j];
   }
   __syncthreads();
+  if (part) {
+    float *dst = part + (((size_t)cb * gridDim.x + blockIdx.x) * RC_M) * NCP;
+    for (int e = tid; e < RC_M * NCP; e += RC_NT) dst[e] = T[(e / NCP) * L::TOT_LD + e % NCP];
+    return;
+  }
   const int t0 = cb * rr;
   const int rc = min(rr, r - t0);
   const int per = s * rc;
@@ -347,18 +416,74 @@ __global__ void __launch_bounds__(RC_NT, 1)
   }
 }
 
+// U1, U2 from the totals of the nsplit K splits of every row tile, summed in
+// split order (FP64): one thread per (I, a, u).
+__global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, int ncta_x, const float *__restrict__ rec,
+                         int DP, int D, int N, const float *__restrict__ phi, int ld, int r, int s, int rr,
+                         float *__restrict__ U1, float *__restrict__ U2) {
+  const int cb = blockIdx.y;
+  const int t0 = cb * rr;
+  const int rc = min(rr, r - t0);
+  const int per = s * rc;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)N * per) return;
+  const int I = (int)(e / per), rem = (int)(e - (long)I * per);
+  const int a = rem / rc, u = rem - a * rc;
+  const int tile = I / RC_M, row = I - tile * RC_M;
+  double w1 = 0.0, w2 = 0.0, cs = 0.0;
+  for (int sp = 0; sp < nsplit; ++sp) {
+    const float *Tr = part + (((size_t)cb * ncta_x + (size_t)tile * nsplit + sp) * RC_M + row) * NCP;
+    w1 += Tr[a * rc + u];
+    w2 += Tr[per + a * rc + u];
+    cs += Tr[2 * per];
+  }
+  const float wI = rec[(size_t)I * DP + D];
+  const size_t o = ((size_t)I * s + a) * ld + t0 + u;
+  const float f = phi[o];
+  U1[o] = f - (float)w1 * wI;
+  U2[o] = (float)cs * f - (float)w2;
+}
+
 template <int D, int NCP>
-int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
-                   float *U1, float *U2) {
+int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg, int nsplit,
+                   float *part, float *U1, float *U2) {
   using L = RcLayout<D, NCP>;
   VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L::SMEM));
-  dim3 grid((N + RC_M - 1) / RC_M, ncb);
+  const int ntiles = (N + RC_M - 1) / RC_M;
+  dim3 grid(ntiles * nsplit, ncb);
   k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, N, Npad, bimg, b->phi,
-                                                             b->ld, b->r, b->s, rr, U1, U2, c->err);
+                                                             b->ld, b->r, b->s, rr, U1, U2, nsplit,
+                                                             nsplit > 1 ? part : nullptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
+  if (nsplit > 1) {
+    const int per = b->s * rr;
+    k_rc_fin<<<dim3((unsigned)(((long)N * per + 255) / 256), ncb), 256, 0, c->stream>>>(
+        part, nsplit, NCP, ntiles * nsplit, (const float *)c->rec.ptr, Rec<D>::DP, D, N, b->phi, b->ld, b->r, b->s,
+        rr, U1, U2);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+  }
   return VDS_OK;
+}
+
+// K splits per row tile: whole segments, chosen so that the CTAs (one per
+// SM) fill their last wave; each CTA costs its segments plus a fixed start
+// and finish of about 1.5 segments.
+int refresh_splits(int ntiles, int ncb, int nseg, int nsm) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ns = 1; ns <= 8 && ns <= nseg; ++ns) {
+    const long items = (long)ntiles * ncb * ns;
+    const long waves = (items + nsm - 1) / nsm;
+    const double cost = (double)waves * ((nseg + ns - 1) / ns + 1.5);
+    if (cost < best_cost * 0.995) {
+      best_cost = cost;
+      best = ns;
+    }
+  }
+  return best;
 }
 
 template <int D>
@@ -373,18 +498,21 @@ int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
   // record rows as written by pass_prep (a multiple of 256 >= RC_KC)
   const int Npad = pass_npad(N);
   const size_t nbt = (size_t)ncb * NCP * Npad;
-  VDS_TRY(vds_ensure(c, c->gbuf, 2 * nbt * sizeof(float)));
-  float *bimg = (float *)c->gbuf.ptr;
+  const int ntiles = (N + RC_M - 1) / RC_M;
+  const int nsplit = refresh_splits(ntiles, ncb, (Npad / RC_KC + RC_SEG - 1) / RC_SEG, c->num_sms);
+  const size_t npart = nsplit > 1 ? (size_t)ncb * ntiles * nsplit * RC_M * NCP : 0;
+  VDS_TRY(vds_ensure(c, c->gbuf, (2 * nbt + npart) * sizeof(float)));
+  float *bimg = (float *)c->gbuf.ptr, *part = bimg + 2 * nbt;
   k_rc_bt<<<dim3((Npad + 255) / 256, NCP, ncb), 256, 0, c->stream>>>(b->phi, b->ld, r, s, rr,
                                                                      (const float *)c->rec.ptr, Rec<D>::DP, D,
                                                                      N, Npad, NCP, bimg);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   switch (NCP) {
-    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
-    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
-    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
-    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, U1, U2);
+    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
+    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
+    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
+    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
   }
 }
 

@@ -44,6 +44,17 @@ __device__ __forceinline__ void tc_mma_tf32(uint32_t tmem_d, uint64_t ad, uint64
       : "memory");
 }
 
+// Same with the A operand in tensor memory (M rows = lanes, K consecutive
+// 32-bit columns from a_tmem) and B from shared memory.
+__device__ __forceinline__ void tc_mma_tf32_ta(uint32_t tmem_d, uint32_t a_tmem, uint64_t bd, uint32_t idesc,
+                                               int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(a_tmem), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -88,6 +99,16 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// 8 consecutive 32-bit columns of the warp's 32 lanes from registers (lane i
+// of the warp writes TMEM lane (base lane) + i); tc_wait_st waits for the
+// warp's stores to tensor memory.
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Plain arrival (release, CTA scope) on an mbarrier.
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
