@@ -113,44 +113,50 @@ __global__ void k_colmean(const double *__restrict__ part, int N, double *__rest
 }
 
 // particle velocity with the entropy gradient replaced by the surrogate
-// (mean-centred): v = kappa q - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi)
-template <int D>
+// (mean-centred): v = kappa q - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi),
+// in FP32 (the inputs and the output are FP32); A is the Rouse matrix, so
+// (A g)_k = 2 g_k - g_(k-1) - g_(k+1) per bond k.
+template <int D, int S>
 __global__ void k_score_vel(KParams kp, const float *__restrict__ q, const float *__restrict__ sc,
                             const double *__restrict__ smean, float *__restrict__ v, int *err) {
+  constexpr int NB = D / S;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kp.N) return;
-  double y[D], g[D];
+  float y[D], g[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) y[a] = (double)q[(size_t)i * D + a];
-  double f[8];
-  for (int k = 0; k < kp.nb; ++k) {
-    double n2 = 0.0;
+  for (int a = 0; a < D; ++a) y[a] = q[(size_t)i * D + a];
+  const float kBT = (float)kp.kBT, izeta = (float)(1.0 / kp.zeta);
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (a / kp.s == k) n2 += y[a] * y[a];
-    if (kp.spring == 0) {
-      f[k] = kp.H[k];
-    } else {
-      const double x = 1.0 - n2 / kp.b;
-      if (!(x > 0.0)) vds_flag(err, VDS_EDOMAIN);
-      f[k] = x > 0.0 ? kp.H[k] / x : 0.0;
+  for (int k = 0; k < NB; ++k) {
+    float f = (float)kp.H[k];
+    if (kp.spring != 0) {
+      float n2 = 0.f;
+#pragma unroll
+      for (int al = 0; al < S; ++al) n2 = fmaf(y[k * S + al], y[k * S + al], n2);
+      const float x = 1.f - n2 / (float)kp.b;
+      if (!(x > 0.f)) vds_flag(err, VDS_EDOMAIN);
+      f = x > 0.f ? f / x : 0.f;
+    }
+#pragma unroll
+    for (int al = 0; al < S; ++al) {
+      const int a = k * S + al;
+      const float sm = smean ? (float)smean[a] : 0.f;
+      g[a] = fmaf(kBT, sc[(size_t)i * D + a] - sm, f * y[a]);
     }
   }
 #pragma unroll
-  for (int a = 0; a < D; ++a)
-    g[a] = kp.kBT * ((double)sc[(size_t)i * D + a] - (smean ? smean[a] : 0.0)) + f[a / kp.s] * y[a];
+  for (int k = 0; k < NB; ++k)
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const int k = a / kp.s, al = a - k * kp.s;
-    double vv = 0.0, m = 0.0;
+    for (int al = 0; al < S; ++al) {
+      const int a = k * S + al;
+      float vv = 0.f;
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const int kb = b / kp.s, be = b - kb * kp.s;
-      if (kb == k) vv += kp.kappa[al * kp.s + be] * y[b];
-      if (be == al) m += rA(k, kb) * g[b];
+      for (int be = 0; be < S; ++be) vv = fmaf((float)kp.kappa[al * S + be], y[k * S + be], vv);
+      float m = 2.f * g[a];
+      if (k > 0) m -= g[a - S];
+      if (k < NB - 1) m -= g[a + S];
+      v[(size_t)i * D + a] = fmaf(-izeta, m, vv);
     }
-    v[(size_t)i * D + a] = (float)(vv - m / kp.zeta);
-  }
 }
 
 // The exact entropy gradient S of the checked particles only (every
@@ -299,24 +305,27 @@ int grad_rows(vds_ctx *c, const KParams &kS, int stride, int nrows, double *part
   }
 }
 
-template <int D>
+template <int D, int S>
 int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean,
                    float *v) {
-  k_score_vel<D><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp, q, sc, smean, v, c->err);
+  k_score_vel<D, S><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp, q, sc, smean, v, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;
 }
 
 int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean, float *v) {
-  switch (kp.D) {
-    case 2: return score_vel_impl<2>(c, kp, q, sc, smean, v);
-    case 3: return score_vel_impl<3>(c, kp, q, sc, smean, v);
-    case 4: return score_vel_impl<4>(c, kp, q, sc, smean, v);
-    case 6: return score_vel_impl<6>(c, kp, q, sc, smean, v);
-    case 8: return score_vel_impl<8>(c, kp, q, sc, smean, v);
-    case 9: return score_vel_impl<9>(c, kp, q, sc, smean, v);
-    case 12: return score_vel_impl<12>(c, kp, q, sc, smean, v);
+  const int key = kp.D * 4 + kp.s;
+  switch (key) {
+    case 2 * 4 + 2: return score_vel_impl<2, 2>(c, kp, q, sc, smean, v);
+    case 3 * 4 + 3: return score_vel_impl<3, 3>(c, kp, q, sc, smean, v);
+    case 4 * 4 + 2: return score_vel_impl<4, 2>(c, kp, q, sc, smean, v);
+    case 6 * 4 + 2: return score_vel_impl<6, 2>(c, kp, q, sc, smean, v);
+    case 6 * 4 + 3: return score_vel_impl<6, 3>(c, kp, q, sc, smean, v);
+    case 8 * 4 + 2: return score_vel_impl<8, 2>(c, kp, q, sc, smean, v);
+    case 9 * 4 + 3: return score_vel_impl<9, 3>(c, kp, q, sc, smean, v);
+    case 12 * 4 + 2: return score_vel_impl<12, 2>(c, kp, q, sc, smean, v);
+    case 12 * 4 + 3: return score_vel_impl<12, 3>(c, kp, q, sc, smean, v);
     default: return VDS_EARG;
   }
 }
@@ -466,7 +475,82 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   const int nrows = (N + stride - 1) / stride;
   double worst = 0.0;
   int nfall = 0;
+  // one surrogate step without a check: lift, network, mean, velocity,
+  // projection, Euler update of P
+  auto plain_step = [&]() -> int {
+    VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
+    VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
+    k_colmean_part<<<dim3(D, CM_BLK), 256, 0, c->stream>>>(sbuf, N, D, cpart);
+    k_colmean<<<D, 32, 0, c->stream>>>(cpart, N, smean);
+    VDS_CUDA_TRY(cudaGetLastError());
+    c->launches += 2;
+    VDS_TRY(score_vel(c, kp, qt, sbuf, smean, vel));
+    VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
+    k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
+    VDS_CUDA_TRY(cudaGetLastError());
+    ++c->launches;
+    return VDS_OK;
+  };
+  // Steps without a check replay one captured CUDA graph of plain_step (its
+  // buffers are all sized by then: the first step runs uncaptured); if the
+  // capture fails they are launched one by one.
+  cudaGraphExec_t gexec = nullptr;
+  long graph_kernels = 0;
+  const void *graph_gbuf = nullptr;  // scratch the captured projection uses
+  bool try_graph = true;
+  struct GraphGuard {
+    cudaGraphExec_t *g;
+    ~GraphGuard() {
+      if (*g) cudaGraphExecDestroy(*g);
+    }
+  } gguard{&gexec};
   for (int step = 0; step < nsteps; ++step) {
+    const bool check_step = check_every > 0 && step % check_every == 0;
+    if (!check_step && step > 0 && try_graph) {
+      if (!gexec) {
+        // captured on a private stream (the caller's may be the legacy
+        // default stream, which cannot be captured); nothing runs while
+        // capturing, and the graph is then launched on the caller's stream
+        const long l0 = c->launches;
+        cudaGraph_t g = nullptr;
+        int st = VDS_OK;
+        cudaStream_t cs = nullptr, user = c->stream;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+          st = VDS_ECUDA;
+        } else if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          st = VDS_ECUDA;
+        } else {
+          c->stream = cs;
+          st = plain_step();
+          c->stream = user;
+          const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+          if (st == VDS_OK && ec != cudaSuccess) st = VDS_ECUDA;
+        }
+        c->stream = user;
+        if (cs) cudaStreamDestroy(cs);
+        if (st == VDS_OK && cudaGraphInstantiate(&gexec, g, 0) != cudaSuccess) {
+          gexec = nullptr;
+          st = VDS_ECUDA;
+        }
+        if (g) cudaGraphDestroy(g);
+        graph_kernels = c->launches - l0;
+        c->launches = l0;
+        graph_gbuf = c->gbuf.ptr;
+        if (st != VDS_OK) {
+          (void)cudaGetLastError();  // a failed capture leaves its status behind; launch directly instead
+          try_graph = false;
+        }
+      }
+      if (gexec) {
+        VDS_CUDA_TRY(cudaGraphLaunch(gexec, c->stream));
+        c->launches += graph_kernels;
+        continue;
+      }
+    }
+    if (!check_step) {
+      VDS_TRY(plain_step());
+      continue;
+    }
     VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
     VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
     k_colmean_part<<<dim3(D, CM_BLK), 256, 0, c->stream>>>(sbuf, N, D, cpart);
@@ -474,7 +558,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     VDS_CUDA_TRY(cudaGetLastError());
     c->launches += 2;
     bool exact = false;
-    if (check_every > 0 && step % check_every == 0) {
+    {
       // full density (every 1/rho_J enters S_I), gradient of the checked rows
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
       VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr));
@@ -505,6 +589,12 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
+    if (gexec && c->gbuf.ptr != graph_gbuf) {
+      // the check grew the scratch the captured projection writes into:
+      // capture again before the next plain step
+      cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+    }
   }
   if (check_err) *check_err = worst;
   if (fallbacks) *fallbacks = nfall;
