@@ -108,6 +108,28 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
   bimg[o + tile] = to_tf32(v - h);
 }
 
+// Packed pairs of FP32 values (f32x2 instructions: one issue slot for two
+// lanes' worth of FP32 work, each half rounded as the scalar instruction).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 // Wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -270,6 +292,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
 #pragma unroll
     for (int j = 0; j < QC; ++j) tot[j] = 0.f;
+    unsigned long long xi2[TA ? D : 1];  // TA: the row's coordinates duplicated in both halves
+#pragma unroll
+    for (int d = 0; d < (TA ? D : 1); ++d) xi2[d] = f2_pack(xi[0][d], xi[0][d]);
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
@@ -301,20 +326,26 @@ __global__ void __launch_bounds__(RC_NT, 1)
       uint8_t *slot = sm + (size_t)z * L::SLOT;
       if constexpr (TA) {
         tc_fence_after();  // the MMAs that read this Z slot have completed
+        // two K per f32x2 instruction: the squared distance of the row to
+        // records u and u + 1 in the two halves of a packed register
         const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + cq * 8 * DP;
         uint32_t hv[8], lv[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          float r2 = 0.f;
+        for (int u = 0; u < 8; u += 2) {
+          unsigned long long r2 = f2_pack(0.f, 0.f);
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            const float dd = xi[0][d] - rs[u * DP + d];
-            r2 = fmaf(dd, dd, r2);
+            const unsigned long long dd = f2_sub(xi2[d], f2_pack(rs[u * DP + d], rs[(u + 1) * DP + d]));
+            r2 = f2_fma(dd, dd, r2);
           }
-          const float zv = ex2_approx(-r2);
-          const float h = to_tf32(zv);
-          hv[u] = __float_as_uint(h);
-          lv[u] = __float_as_uint(to_tf32(zv - h));
+          float r2a, r2b;
+          f2_unpack(r2, r2a, r2b);
+          const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
+          const float ha = to_tf32(za), hb = to_tf32(zb);
+          hv[u] = __float_as_uint(ha);
+          hv[u + 1] = __float_as_uint(hb);
+          lv[u] = __float_as_uint(to_tf32(za - ha));
+          lv[u + 1] = __float_as_uint(to_tf32(zb - hb));
         }
         const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 64 * z + 8 * cq);
         tc_st8(zt, hv);
