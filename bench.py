@@ -220,31 +220,50 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream, which):
 
 # The paper's Sec. 3 tables at P = 1000, delta t = 1e-3, t in [0, 6] (its
 # R column and its printed T_mor/T_ref and err_MOR, for context)
+# The paper's Sec. 3 tables (P particles, bonds nb in 3D, shear rate, bond
+# constants H) with their printed T_mor/T_ref and err_MOR(t = 6) per R.
+_R8 = [1, 2, 3, 4, 5, 10, 20, 40]
+_R6 = [10, 15, 20, 25, 30, 40]
 PAPER_TABLES = {
-    "noflow_2bead": {"nb": 1, "rate": 0.0, "R": [1, 2, 3, 4, 5, 10, 20, 40],
-                     "paper_T_ratio": [0.0036, None, None, None, None, None, None, 0.433],
-                     "paper_err_mor": [0.0476, None, None, None, None, None, None, 0.00865]},
-    "shear_4bead": {"nb": 3, "rate": 1.0, "R": [10, 20, 40],
-                    "paper_T_ratio": [None, 0.0689, None], "paper_err_mor": [None, 0.0567, None]},
+    "noflow_2bead": {"table": 1, "nb": 1, "rate": 0.0, "P": 1000, "H": None, "R": _R8,
+                     "paper_T_ratio": [0.0036, 0.00605, 0.00819, 0.0108, 0.0143, 0.0366, 0.118, 0.433],
+                     "paper_err_mor": [0.0476, 0.0234, 0.0104, 0.00635, 0.00595, 0.00816, 0.00843, 0.00865]},
+    "noflow_3bead": {"table": 2, "nb": 2, "rate": 0.0, "P": 1000, "H": None, "R": _R8,
+                     "paper_T_ratio": [0.00441, 0.00612, 0.00758, 0.00955, 0.0123, 0.0282, 0.0890, 0.321],
+                     "paper_err_mor": [0.708, 0.128, 0.0750, 0.0447, 0.0272, 0.0182, 0.0198, 0.0198]},
+    "shear_2bead": {"table": 3, "nb": 1, "rate": 1.0, "P": 1000, "H": None, "R": _R6,
+                    "paper_T_ratio": [0.0377, 0.0731, 0.122, 0.184, 0.260, 0.449],
+                    "paper_err_mor": [0.105, 0.0947, 0.0876, 0.0841, 0.0823, 0.0808]},
+    "shear_4bead": {"table": 4, "nb": 3, "rate": 1.0, "P": 1000, "H": None, "R": _R6,
+                    "paper_T_ratio": [0.0230, 0.0424, 0.0689, 0.103, 0.144, 0.248],
+                    "paper_err_mor": [0.125, 0.0667, 0.0567, 0.0500, 0.0442, 0.0372]},
+    "shear_4bead_P10000": {"table": 5, "nb": 3, "rate": 1.0, "P": 10000, "H": None, "R": _R6,
+                           "paper_T_ratio": [0.0231, 0.0430, 0.0690, 0.105, 0.148, 0.254],
+                           "paper_err_mor": [0.132, 0.0660, 0.0599, 0.0559, 0.0541, 0.0518]},
+    "shear_4bead_H123": {"table": 6, "nb": 3, "rate": 1.0, "P": 1000, "H": [1.0, 2.0, 3.0], "R": _R6,
+                         "paper_T_ratio": [0.0239, 0.0443, 0.0720, 0.108, 0.151, 0.258],
+                         "paper_err_mor": [0.183, 0.111, 0.0955, 0.0836, 0.0793, 0.0702]},
 }
 
 
 def _extra_paper_tables(ctx, vds, inputs, torch, timed):
-    """Replication of the paper's Sec. 3 experiments on the GPU: full-order
-    run of P = 1000 particles to t = 6 (6000 steps), POD from the snapshots of
-    t in [0, 3] (every second step for one bond, every fifth for three: within
-    the 2048-column limit), reduced runs of the frozen step (Eq. model_DymReduced, refresh
-    every 300 steps) for each rank R; err_MOR at t = 6 and T_mor / T_ref.
-    Seeds and the snapshot spacing differ from the paper's: trend only."""
-    P, s, dt, steps, snap_to = 1000, 3, 1e-3, 6000, 3000
+    """Replication of the paper's Sec. 3 experiments (its six tables) on the
+    GPU: full-order run of P particles to t = 6 (6000 steps), POD from the
+    snapshots of t in [0, 3] (every step for one bond, every second for two,
+    every fifth for three: within the 2048-column limit), reduced runs of the
+    frozen step (Eq. model_DymReduced, refresh every 300 steps) for each rank
+    R; err_MOR at t = 6 and T_mor / T_ref next to the printed values.  Seeds
+    and the snapshot spacing differ from the paper's: trend only."""
+    s, dt, steps, snap_to = 3, 1e-3, 6000, 3000
     res = {}
     for name, cfg in PAPER_TABLES.items():
-        nb = cfg["nb"]
+        nb, P = cfg["nb"], cfg["P"]
         D = nb * s
+        H = cfg["H"] or [1.0] * nb
         kap = inputs.shear_kappa(s, cfg["rate"])
-        q0 = torch.from_numpy(inputs.equilibrium_cloud(P, nb, s, seed=2024)).cuda()
+        q0 = torch.from_numpy(inputs.equilibrium_cloud(P, nb, s, H=H, seed=2024)).cuda()
         h = ctx.vds_bandwidth(q0, 0)
-        p = vds.params(nb, s, h=h, dt=dt, kappa=kap, scheme=0)
+        p = vds.params(nb, s, H=H, h=h, dt=dt, kappa=kap, scheme=0)
         q = q0.clone()
         every = -(-snap_to * nb // 2048)  # snapshot spacing within the 2048-column limit
         L = snap_to // every
@@ -273,10 +292,11 @@ def _extra_paper_tables(ctx, vds, inputs, torch, timed):
             rows.append({"R": R_req, "R_used": R, "T_ratio": t_mor / t_ref, "err_mor": err})
             bR.free()
         basis.free()
-        res[name] = {"P": P, "d": D, "h": h, "snapshots": L, "snapshot_every": every, "T_ref_s": t_ref, "rows": rows,
+        res[name] = {"table": cfg["table"], "P": P, "d": D, "H": H, "h": h, "snapshots": L, "snapshot_every": every,
+                     "T_ref_s": t_ref, "rows": rows,
                      "paper_T_ratio": cfg["paper_T_ratio"], "paper_err_mor": cfg["paper_err_mor"]}
-    res["note"] = ("GPU times: the full-order step at P = 1000 is launch-latency bound, so T_mor/T_ref is not "
-                   "comparable with the paper's CPU ratio; err_MOR is the physics (trend only)")
+    res["note"] = ("GPU times: the full-order step at P = 1000 or 10000 is launch-latency bound, so T_mor/T_ref "
+                   "is not comparable with the paper's CPU ratio; err_MOR is the physics (trend only)")
     return res
 
 
