@@ -138,6 +138,26 @@ def test_score_mode_matches_oracle(orc, vds, ctx, setup):
     assert _rel(P.cpu().numpy(), Po) <= 1e-2
 
 
+def test_score_steps_replayed_as_a_graph_equal_uncaptured_steps(vds, ctx, setup):
+    # the steps between checks replay one captured CUDA graph; a call in which
+    # every step is a check step (with a tolerance no error exceeds, so no
+    # fallback) launches the same update kernels one by one, uncaptured: the
+    # reduced coordinates come out bit-identical, with and without checks in
+    # between
+    S = setup
+    _, net = _score_net(vds, ctx)
+    D = S["nb"] * S["s"]
+    P0 = torch.from_numpy(S["P0"].astype(np.float32)).cuda()
+    runs = {}
+    for name, every in (("graph", 0), ("graph_between_checks", 3), ("uncaptured", 1)):
+        P = P0.clone()
+        ctx.pod_step_score(S["basis"], net, P, S["N"], D, S["pg"], nsteps=7, check_every=every, check_n=100,
+                           check_tol=1e9)
+        runs[name] = P
+    assert torch.equal(runs["graph"], runs["uncaptured"])
+    assert torch.equal(runs["graph_between_checks"], runs["uncaptured"])
+
+
 def test_score_check_falls_back_to_exact(vds, ctx, setup):
     # with a zero tolerance every checked step uses the exact entropy gradient,
     # which is the Galerkin step
