@@ -376,30 +376,38 @@ __global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 
 // ------------------------------------------------- fused inference forward
 //
 // k_mlp_fwd evaluates all four layers of the width-256 network for 128-row
-// tiles in one persistent launch (one CTA per SM, 320 threads): the hidden
+// tiles in one persistent launch (one CTA per SM, 576 threads): the hidden
 // activations of a tile never leave shared memory.  Roles:
-//   warp 8, one lane   streams the packed weights (F_NCHUNK chunks per tile,
-//                      each the exact shared-memory image of a 128-row x 64-K
-//                      operand block) through an F_STAGES-deep ring with 1-D
-//                      bulk copies (TMA engine);
-//   warp 9, one lane   issues the tcgen05.mma (M=128, N=128 per weight half,
-//                      K=16; N=16 for the output layer) into the tile's
-//                      256-column accumulator;
-//   warps 0-7          read the accumulator (warp w: rows 32 (w % 4) + lane,
-//                      columns 32 (w / 4) + ... of each 64-column K-chunk),
-//                      add the bias, apply SiLU and write BF16 activations
-//                      back as the next layer's A operand; for the output
+//   warp 16, one lane  streams the packed weights (F_NCOPY copies per tile,
+//                      each the exact shared-memory image of the two 128-row
+//                      x 64-K operand blocks of one K-chunk) through an
+//                      F_STAGES-deep ring with 1-D bulk copies (TMA engine);
+//   warp 17, one lane  issues the tcgen05.mma (M=128, N=256: the two 128-row
+//                      weight blocks of a K-chunk are adjacent and form one
+//                      B operand; K=16; N=16 for the output layer);
+//   warps 0-15         read the accumulator (warp w: rows 32 (w % 4) + lane,
+//                      16 columns (w / 4) of each 64-column K-chunk), add the
+//                      bias, apply SiLU and write BF16 activations back in
+//                      place as the next layer's A operand; for the output
 //                      layer they add b4 and store the first D columns.
-// Two tiles are in flight (slots 0 and 1, 256 TMEM columns and a 64 KB
-// activation buffer each): the MMAs of one slot run while the epilogue warps
-// work on the other.  The CTA takes tiles b, b + G, b + 2G, ...; round r puts
-// its tiles 2r and 2r + 1 into slots 0 and 1.
+// One tile is in flight, with two 256-column accumulators: layer L writes
+// accumulator L % 2, so the MMAs of layer L + 1 start on K-chunk kc as soon
+// as the epilogue of layer L has written it (barrier hb[kc]) while the
+// epilogue goes on with the next chunks.  Shared memory holds one tile's
+// activations (64 KB) and the weight ring.  The weights (the same 296 KB for
+// every tile, read by every SM from L2) move in 32 KB copies: on GB300 one
+// SM's bulk copies complete one after another at about a quarter
+// microsecond each up to tens of KB, so per-SM throughput grows with the copy
+// size (16 KB copies: about 63 KB/us, 32 KB: about 130 KB/us), not with the
+// number in flight.  The CTA takes tiles b, b + G, b + 2G, ...
 //
-// Synchronisation per slot (completion counts per round r, layer l):
-//   edone[s]  256 arrivals: the operand of layer l is written and the
-//             accumulator released (completion 4r + l; the A0 of round r + 1
-//             is written by the output epilogue of round r);
-//   afull[s]  tcgen05.commit after the MMAs of layer l (completion 4r + l);
+// Synchronisation (L = 4 i + l: layer l of the CTA's i-th tile):
+//   afull      tcgen05.commit after the MMAs of layer L (completion L);
+//   accfree[b] 512 arrivals: accumulator b read by the epilogue of layer L
+//              (b = L % 2, completion L / 2);
+//   hb[kc]     512 arrivals: K-chunk kc of the activations written by a
+//              hidden-layer epilogue (completion 3 i + l);
+//   a0r        512 arrivals: the tile's input block written (completion i);
 //   full/empty[stage]  weight ring (bulk-copy bytes / MMA commit).
 // Every wait is bounded: a wait that runs out sets the abort flag and the
 // error flag, every role then leaves its loop, the copies and MMAs in flight
@@ -409,13 +417,17 @@ __global__ void k_to_bf16(const float *__restrict__ W, int rows, int cols, bf16 
 // tanh approximation (relative error about 2^-11, far below the BF16
 // rounding of the activation it produces).
 
-constexpr int F_THREADS = 320;
-constexpr int F_STAGES = 5;
-constexpr int F_CHUNK = 16384;                 // bytes of one weight chunk
-constexpr int F_NCHUNK = 19;                   // W1: 2, W2: 8, W3: 8, W4: 1 (8 KB)
-constexpr int F_HBYTES = 4 * 16384;            // activations of one tile: 4 K-chunks of 128 x 64 BF16
+constexpr int F_EW = 16;                         // epilogue warps
+constexpr int F_ET = F_EW * 32;                  // epilogue threads
+constexpr int F_THREADS = F_ET + 64;             // + weight producer warp + MMA warp
+constexpr int F_CHUNK = 16384;                   // bytes of one 128-row x 64-K weight block
+constexpr int F_NCHUNK = 19;                     // blocks: W1 2, W2 8, W3 8, W4 1 (8 KB)
+constexpr int F_COPY = 2 * F_CHUNK;              // bytes of one copy: both 128-row halves of a K-chunk
+constexpr int F_NCOPY = 10;                      // copies per tile: W1 1, W2 4, W3 4, W4 1 (8 KB)
+constexpr int F_HBYTES = 4 * 16384;              // activations of one tile: 4 K-chunks of 128 x 64 BF16
 constexpr int F_BIAS_FLOATS = 3 * 256 + 16;
-constexpr size_t F_SMEM = 2 * F_HBYTES + F_STAGES * F_CHUNK + F_BIAS_FLOATS * 4;
+constexpr int F_STAGES = (227 * 1024 - 1024 - F_HBYTES - F_BIAS_FLOATS * 4) / F_COPY;
+constexpr size_t F_SMEM = F_HBYTES + F_STAGES * F_COPY + F_BIAS_FLOATS * 4;
 constexpr size_t F_WPACK_BYTES = 18 * (size_t)F_CHUNK + 8192;
 
 __device__ __forceinline__ float tanh_approx(float x) {
@@ -440,9 +452,10 @@ __device__ __forceinline__ bool fwait(uint64_t *bar, uint32_t parity, volatile i
   }
 }
 
-__host__ __device__ constexpr int f_first_chunk(int l) { return l == 0 ? 0 : (l == 1 ? 2 : (l == 2 ? 10 : 18)); }
-__host__ __device__ constexpr int f_nchunks(int l) { return l == 0 ? 2 : (l == 3 ? 1 : 8); }
-static_assert(f_first_chunk(3) + f_nchunks(3) == F_NCHUNK, "weight stream length");
+// copies of layer l: 1, 4, 4, 1 (copy j covers blocks 2j and 2j + 1)
+__host__ __device__ constexpr int f_ncopies(int l) { return (l == 0 || l == 3) ? 1 : 4; }
+static_assert(2 * (F_NCOPY - 1) + 1 == F_NCHUNK, "weight stream length");
+static_assert(F_STAGES >= 4, "weight ring depth");
 static_assert(F_SMEM <= 227 * 1024 - 1024, "shared memory of k_mlp_fwd");
 
 // Packed weight stream: chunk j holds, in the canonical K-major layout
@@ -480,17 +493,17 @@ __global__ void __launch_bounds__(F_THREADS, 1)
               const float *__restrict__ b1, const float *__restrict__ b2, const float *__restrict__ b3,
               const float *__restrict__ b4, float *__restrict__ out, int *err) {
   extern __shared__ __align__(1024) uint8_t fsm[];
-  __shared__ __align__(8) uint64_t full[F_STAGES], empty[F_STAGES], afull[2], edone[2], fin;
+  __shared__ __align__(8) uint64_t full[F_STAGES], empty[F_STAGES], afull, accfree[2], hb[4], a0r, fin;
+  static_assert(F_STAGES <= 8, "barrier array size");
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = (N + GM - 1) / GM;
   const int G = gridDim.x;
   const int nk = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles of this CTA
-  const int rounds = (nk + 1) / 2;
-  uint8_t *hbuf = fsm;                                  // 2 x 64 KB activations
-  uint8_t *ring = fsm + 2 * F_HBYTES;                   // weight stages
-  float *sbias = reinterpret_cast<float *>(ring + F_STAGES * F_CHUNK);
+  uint8_t *hbuf = fsm;                                  // 64 KB activations
+  uint8_t *ring = fsm + F_HBYTES;                       // weight stages
+  float *sbias = reinterpret_cast<float *>(ring + F_STAGES * F_COPY);
   volatile int *abort = &s_abort;
 
   if (warp == 0) tc_alloc(&s_tmem, 512);
@@ -499,10 +512,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
     }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(&afull[k], 1);
-      mbar_init(&edone[k], 256);
-    }
+    mbar_init(&afull, 1);
+    for (int k = 0; k < 2; ++k) mbar_init(&accfree[k], F_ET);
+    for (int k = 0; k < 4; ++k) mbar_init(&hb[k], F_ET);
+    mbar_init(&a0r, F_ET);
     mbar_init(&fin, 1);
     s_abort = 0;
     fence_mbar_init();
@@ -513,176 +526,187 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  auto tile_of = [&](int r, int s) { return (int)blockIdx.x + (2 * r + s) * G; };
+  auto tile_of = [&](int i) { return (int)blockIdx.x + i * G; };
 
-  if (warp == 8) {
+  if (warp == F_EW) {
     // ------------------------------------------------ weight producer
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
-      for (int r = 0; r < rounds && ok; ++r)
-        for (int l = 0; l < 4 && ok; ++l)
-          for (int s = 0; s < 2 && ok; ++s) {
-            if (2 * r + s >= nk) continue;
-            for (int j = f_first_chunk(l); j < f_first_chunk(l) + f_nchunks(l); ++j, ++g) {
-              const uint32_t st = g % F_STAGES;
-              if (g >= F_STAGES && !fwait(&empty[st], ((g / F_STAGES) - 1) & 1, abort)) {
-                ok = false;
-                break;
-              }
-              const uint32_t bytes = j == 18 ? 8192u : (uint32_t)F_CHUNK;
-              mbar_arrive_expect_tx(&full[st], bytes);
-              bulk_g2s(ring + st * F_CHUNK, reinterpret_cast<const uint8_t *>(wpack) + (size_t)j * F_CHUNK, bytes,
-                       &full[st]);
-            }
+      for (int i = 0; i < nk && ok; ++i)
+        for (int j = 0; j < F_NCOPY; ++j, ++g) {
+          const uint32_t st = g % F_STAGES;
+          if (g >= F_STAGES && !fwait(&empty[st], ((g / F_STAGES) - 1) & 1, abort)) {
+            ok = false;
+            break;
           }
+          const uint32_t bytes = j == F_NCOPY - 1 ? 8192u : (uint32_t)F_COPY;
+          mbar_arrive_expect_tx(&full[st], bytes);
+          bulk_g2s(ring + st * F_COPY, reinterpret_cast<const uint8_t *>(wpack) + (size_t)j * F_COPY, bytes,
+                   &full[st]);
+        }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
       // the copies still in flight land before the CTA may exit
       for (uint32_t k = g > F_STAGES ? g - F_STAGES : 0; k < g; ++k)
         mbar_wait_bounded(&full[k % F_STAGES], (k / F_STAGES) & 1, VDS_WAIT_LIMIT_NS);
     }
-  } else if (warp == 9) {
+  } else if (warp == F_EW + 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id128 = tc_idesc(TC_FMT_BF16, GM, 128), id16 = tc_idesc(TC_FMT_BF16, GM, 16);
+      const uint32_t id256 = tc_idesc(TC_FMT_BF16, GM, 256), id16 = tc_idesc(TC_FMT_BF16, GM, 16);
       const uint32_t hb0 = smem_u32(hbuf), rb = smem_u32(ring);
       uint32_t g = 0;
       bool ok = true;
-      for (int r = 0; r < rounds && ok; ++r)
-        for (int l = 0; l < 4 && ok; ++l)
-          for (int s = 0; s < 2 && ok; ++s) {
-            if (2 * r + s >= nk) continue;
-            if (!fwait(&edone[s], (uint32_t)(l & 1), abort)) {
+      for (int i = 0; i < nk && ok; ++i)
+        for (int l = 0; l < 4 && ok; ++l) {
+          const int L = 4 * i + l, b = L & 1;
+          const uint32_t d = tmem + (uint32_t)(b * 256);
+          // the epilogue of layer L - 2 has read this accumulator
+          if (L >= 2 && !fwait(&accfree[b], (uint32_t)(((L >> 1) - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          if (l == 0 && !fwait(&a0r, (uint32_t)(i & 1), abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t hpar = (uint32_t)((3 * i + l - 1) & 1);  // hidden epilogue 3 i + l - 1
+          for (int jj = 0; jj < f_ncopies(l) && ok; ++jj, ++g) {
+            const uint32_t st = g % F_STAGES;
+            if (!fwait(&full[st], (g / F_STAGES) & 1, abort)) {
               ok = false;
               break;
             }
-            tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(s * 256), hb = hb0 + (uint32_t)(s * F_HBYTES);
-            for (int jj = 0; jj < f_nchunks(l); ++jj, ++g) {
-              const uint32_t st = g % F_STAGES;
-              if (!fwait(&full[st], (g / F_STAGES) & 1, abort)) {
+            const uint32_t wb = rb + st * F_COPY;
+            if (l == 3) {
+#pragma unroll 1
+              for (int kc = 0; kc < 4 && ok; ++kc) {
+                if (!fwait(&hb[kc], hpar, abort)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  tc_mma_bf16(d, tc_sdesc(hb0 + kc * 16384 + k * 256), tc_sdesc(wb + kc * 2048 + k * 256), id16,
+                              (kc > 0 || k > 0) ? 1 : 0);
+              }
+            } else {
+              const int kc = jj;  // K-chunk; the copy holds both 128-row halves of the weights
+              if (l > 0 && !fwait(&hb[kc], hpar, abort)) {
                 ok = false;
                 break;
               }
               tc_fence_after();
-              const uint32_t wb = rb + st * F_CHUNK;
-              if (l == 3) {
+              // rows 128..255 of the weights follow rows 0..127 at the next
+              // 8-row group (F_CHUNK bytes on): one operand of 256 rows
 #pragma unroll
-                for (int kc = 0; kc < 4; ++kc)
-#pragma unroll
-                  for (int k = 0; k < 4; ++k)
-                    tc_mma_bf16(d, tc_sdesc(hb + kc * 16384 + k * 256), tc_sdesc(wb + kc * 2048 + k * 256), id16,
-                                (kc > 0 || k > 0) ? 1 : 0);
-              } else {
-                const int kc = l == 0 ? 0 : jj >> 1, nh = l == 0 ? jj : jj & 1;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                  tc_mma_bf16(d + (uint32_t)(nh * 128), tc_sdesc(hb + kc * 16384 + k * 256), tc_sdesc(wb + k * 256),
-                              id128, (kc > 0 || k > 0) ? 1 : 0);
-              }
-              tc_commit(&empty[st]);
+              for (int k = 0; k < 4; ++k)
+                tc_mma_bf16(d, tc_sdesc(hb0 + kc * 16384 + k * 256), tc_sdesc(wb + k * 256), id256,
+                            (kc > 0 || k > 0) ? 1 : 0);
             }
-            if (ok) tc_commit(&afull[s]);
+            tc_commit(&empty[st]);
           }
+          if (ok) tc_commit(&afull);
+        }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
     }
   } else {
-    // ------------------------------------------------ epilogue warps 0-7
-    const int q = warp & 3, half = warp >> 2;
+    // ------------------------------------------------ epilogue warps 0-15
+    const int q = warp & 3, cp = warp >> 2;
     const int rl = q * 32 + lane;                       // accumulator row of this thread
-    const int ar = tid & 127, ag = tid >> 7;            // A0 row and 8-column group of this thread
-    float xp[2][8];
-    auto fetch_x = [&](int tile, float (&xv)[8]) {
+    const int ar = tid & 127, ag = tid >> 7;            // input row and 8-column group (ag, ag + 4)
+    float xp[8];
+    auto fetch_x = [&](int tile) {
       const int row = tile * GM + ar;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int k = ag * 8 + i;
-        xv[i] = (row < N && k < D) ? x[(size_t)row * D + k] : 0.f;
+      for (int u = 0; u < 8; ++u) {
+        const int k = ag * 8 + u;
+        xp[u] = (row < N && k < D && ag < 2) ? x[(size_t)row * D + k] : 0.f;
       }
     };
-    // A0 = bf16(x) padded to 64 columns, into K-chunk 0 of the slot's buffer
-    auto put_a0 = [&](int s, const float (&xv)[8]) {
-      uint8_t *h = hbuf + s * F_HBYTES + (ar >> 3) * 1024 + (ar & 7) * 16;
+    // A0 = bf16(x) padded to 64 columns, into K-chunk 0 of the activations
+    auto put_a0 = [&]() {
+      uint8_t *h = hbuf + (ar >> 3) * 1024 + (ar & 7) * 16;
       uint32_t pk[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const __nv_bfloat162 t = __floats2bfloat162_rn(xv[2 * i], xv[2 * i + 1]);
-        pk[i] = *reinterpret_cast<const uint32_t *>(&t);
+      for (int u = 0; u < 4; ++u) {
+        const __nv_bfloat162 t = __floats2bfloat162_rn(xp[2 * u], xp[2 * u + 1]);
+        pk[u] = *reinterpret_cast<const uint32_t *>(&t);
       }
       *reinterpret_cast<uint4 *>(h + ag * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-#pragma unroll
-      for (int c = 1; c < 4; ++c) *reinterpret_cast<uint4 *>(h + (ag + 2 * c) * 128) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4 *>(h + (ag + 4) * 128) = make_uint4(0, 0, 0, 0);
     };
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-      if (s < nk) {
-        fetch_x(tile_of(0, s), xp[s]);
-        put_a0(s, xp[s]);
-        fence_proxy_async_smem();
-        mbar_arrive(&edone[s]);
-      }
+    if (nk > 0) {
+      fetch_x(tile_of(0));
+      put_a0();
+      fence_proxy_async_smem();
+      mbar_arrive(&a0r);
+    }
     bool ok = true;
-    for (int r = 0; r < rounds && ok; ++r)
-      for (int l = 0; l < 4 && ok; ++l)
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-          if (!ok || 2 * r + s >= nk) continue;
-          ok = __all_sync(0xffffffffu, fwait(&afull[s], (uint32_t)(l & 1), abort));
-          if (!ok) continue;
-          tc_fence_after();
-          const uint32_t ta = tmem + (uint32_t)(s * 256) + ((uint32_t)(q * 32) << 16);
-          const bool next = 2 * (r + 1) + s < nk;
-          if (l < 3) {
-            if (l == 2 && next) fetch_x(tile_of(r + 1, s), xp[s]);
-            const float *bias = sbias + l * 256;
-            uint8_t *h = hbuf + s * F_HBYTES + (rl >> 3) * 1024 + (rl & 7) * 16;
+    for (int i = 0; i < nk && ok; ++i)
+      for (int l = 0; l < 4 && ok; ++l) {
+        const int L = 4 * i + l, b = L & 1;
+        ok = __all_sync(0xffffffffu, fwait(&afull, (uint32_t)(L & 1), abort));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t ta = tmem + (uint32_t)(b * 256) + ((uint32_t)(q * 32) << 16);
+        const bool next = i + 1 < nk;
+        if (l < 3) {
+          if (l == 2 && next) fetch_x(tile_of(i + 1));
+          const float *bias = sbias + l * 256;
+          uint8_t *h = hbuf + (rl >> 3) * 1024 + (rl & 7) * 16 + cp * 2 * 128;
 #pragma unroll 1
-            for (int kc = 0; kc < 4; ++kc) {
-              uint32_t v[32];
-              const int c0 = kc * 64 + half * 32;
-              tc_ld32(ta + (uint32_t)c0, v);
-              uint32_t pk[16];
+          for (int kc = 0; kc < 4; ++kc) {
+            uint32_t v[16];
+            const int c0 = kc * 64 + cp * 16;
+            tc_ld16(ta + (uint32_t)c0, v);
+            uint32_t pk[8];
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const float z0 = __uint_as_float(v[2 * i]) + bias[c0 + 2 * i];
-                const float z1 = __uint_as_float(v[2 * i + 1]) + bias[c0 + 2 * i + 1];
-                const float h0 = 0.5f * z0, h1 = 0.5f * z1;
-                const __nv_bfloat162 t =
-                    __floats2bfloat162_rn(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
-                pk[i] = *reinterpret_cast<const uint32_t *>(&t);
-              }
-              uint8_t *hk = h + kc * 16384 + half * 4 * 128;
-#pragma unroll
-              for (int i = 0; i < 4; ++i)
-                *reinterpret_cast<uint4 *>(hk + i * 128) =
-                    make_uint4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+            for (int u = 0; u < 8; ++u) {
+              const float z0 = __uint_as_float(v[2 * u]) + bias[c0 + 2 * u];
+              const float z1 = __uint_as_float(v[2 * u + 1]) + bias[c0 + 2 * u + 1];
+              const float h0 = 0.5f * z0, h1 = 0.5f * z1;
+              const __nv_bfloat162 t =
+                  __floats2bfloat162_rn(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
+              pk[u] = *reinterpret_cast<const uint32_t *>(&t);
             }
-          } else {
-            // the layer-4 MMAs have read the activations: the next tile's A0 may go in
-            if (next) put_a0(s, xp[s]);
-            if (half == 0) {
-              uint32_t v[16];
-              tc_ld16(ta, v);
-              const int row = tile_of(r, s) * GM + rl;
-              if (row < N) {
-                const float *bias = sbias + 768;
+            uint8_t *hk = h + kc * 16384;
+            *reinterpret_cast<uint4 *>(hk) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4 *>(hk + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            // this K-chunk is the next layer's operand as soon as every thread wrote it
+            fence_proxy_async_smem();
+            mbar_arrive(&hb[kc]);
+          }
+        } else {
+          // the output layer's MMAs have read the activations: the next tile's input may go in
+          if (next) {
+            put_a0();
+            fence_proxy_async_smem();
+            mbar_arrive(&a0r);
+          }
+          if (cp == 0) {
+            uint32_t v[16];
+            tc_ld16(ta, v);
+            const int row = tile_of(i) * GM + rl;
+            if (row < N) {
+              const float *bias = sbias + 768;
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                  if (j < D) out[(size_t)row * D + j] = __uint_as_float(v[j]) + bias[j];
-              }
+              for (int j = 0; j < 16; ++j)
+                if (j < D) out[(size_t)row * D + j] = __uint_as_float(v[j]) + bias[j];
             }
           }
-          fence_proxy_async_smem();
-          tc_fence_before();
-          mbar_arrive(&edone[s]);
         }
+        tc_fence_before();
+        mbar_arrive(&accfree[b]);
+      }
     if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
   }
   // every role has left its loop; the MMAs issued are complete before the
   // tensor memory is released
   tc_fence_before();
   __syncthreads();
-  if (warp == 9 && lane == 0) {
+  if (warp == F_EW + 1 && lane == 0) {
     tc_commit(&fin);
     mbar_wait_bounded(&fin, 0, VDS_WAIT_LIMIT_NS);
   }
