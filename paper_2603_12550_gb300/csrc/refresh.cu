@@ -317,53 +317,80 @@ __global__ void __launch_bounds__(RC_NT, 1)
       return true;
     };
     int flushed = 0;  // segments added into registers
-    for (int ch = 0; ch < nch && ok; ++ch) {
-      const int z = ch % NZ;
-      if (!__all_sync(0xffffffffu, rc_wait(&full[z], (uint32_t)((ch / NZ) & 1), abort))) {
-        ok = false;
-        break;
-      }
-      uint8_t *slot = sm + (size_t)z * L::SLOT;
-      if constexpr (TA) {
-        tc_fence_after();  // the MMAs that read this Z slot have completed
-        // two K per f32x2 instruction: the squared distance of the row to
-        // records u and u + 1 in the two halves of a packed register
-        const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + cq * 8 * DP;
-        uint32_t hv[8], lv[8];
+    // Z of one chunk (TA) for this thread's row and 8 K, two K per f32x2
+    // instruction: the squared distances to records u and u + 1 in the two
+    // halves of a packed register
+    auto z_chunk = [&](const uint8_t *slot, uint32_t (&hv)[8], uint32_t (&lv)[8]) {
+      const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + cq * 8 * DP;
 #pragma unroll
-        for (int u = 0; u < 8; u += 2) {
-          unsigned long long r2 = f2_pack(0.f, 0.f);
+      for (int u = 0; u < 8; u += 2) {
+        unsigned long long r2 = f2_pack(0.f, 0.f);
 #pragma unroll
-          for (int d = 0; d < D; ++d) {
-            const unsigned long long dd = f2_sub(xi2[d], f2_pack(rs[u * DP + d], rs[(u + 1) * DP + d]));
-            r2 = f2_fma(dd, dd, r2);
-          }
-          float r2a, r2b;
-          f2_unpack(r2, r2a, r2b);
-          const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
-          const float ha = to_tf32(za), hb = to_tf32(zb);
-          hv[u] = __float_as_uint(ha);
-          hv[u + 1] = __float_as_uint(hb);
-          lv[u] = __float_as_uint(to_tf32(za - ha));
-          lv[u + 1] = __float_as_uint(to_tf32(zb - hb));
+        for (int d = 0; d < D; ++d) {
+          const unsigned long long dd = f2_sub(xi2[d], f2_pack(rs[u * DP + d], rs[(u + 1) * DP + d]));
+          r2 = f2_fma(dd, dd, r2);
         }
-        const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 64 * z + 8 * cq);
-        tc_st8(zt, hv);
-        tc_st8(zt + 32u, lv);
+        float r2a, r2b;
+        f2_unpack(r2, r2a, r2b);
+        const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
+        const float ha = to_tf32(za), hb = to_tf32(zb);
+        hv[u] = __float_as_uint(ha);
+        hv[u + 1] = __float_as_uint(hb);
+        lv[u] = __float_as_uint(to_tf32(za - ha));
+        lv[u + 1] = __float_as_uint(to_tf32(zb - hb));
+      }
+    };
+    if constexpr (TA) {
+      // two chunks per pass (nch is a multiple of the 16-chunk segment, so
+      // even): twice the independent work between the waits and stores
+      for (int ch = 0; ch < nch && ok; ch += 2) {
+        const int z0 = ch % NZ, z1 = (ch + 1) % NZ;
+        if (!__all_sync(0xffffffffu, rc_wait(&full[z0], (uint32_t)((ch / NZ) & 1), abort) &&
+                                         rc_wait(&full[z1], (uint32_t)(((ch + 1) / NZ) & 1), abort))) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();  // the MMAs that read these Z slots have completed
+        uint32_t hv0[8], lv0[8], hv1[8], lv1[8];
+        z_chunk(sm + (size_t)z0 * L::SLOT, hv0, lv0);
+        z_chunk(sm + (size_t)z1 * L::SLOT, hv1, lv1);
+        const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 8 * cq);
+        tc_st8(zt + (uint32_t)(64 * z0), hv0);
+        tc_st8(zt + (uint32_t)(64 * z0 + 32), lv0);
+        tc_st8(zt + (uint32_t)(64 * z1), hv1);
+        tc_st8(zt + (uint32_t)(64 * z1 + 32), lv1);
         tc_wait_st();
         tc_fence_before();
-      } else {
+        mbar_arrive(&zready[z0]);
+        mbar_arrive(&zready[z1]);
+        // segment g - 1 is added into registers part-way through segment g
+        if ((ch + 1) % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
+          if (!flush(ch / RC_SEG - 1)) {
+            ok = false;
+            break;
+          }
+          ++flushed;
+        }
+      }
+    } else {
+      for (int ch = 0; ch < nch && ok; ++ch) {
+        const int z = ch % NZ;
+        if (!__all_sync(0xffffffffu, rc_wait(&full[z], (uint32_t)((ch / NZ) & 1), abort))) {
+          ok = false;
+          break;
+        }
+        uint8_t *slot = sm + (size_t)z * L::SLOT;
         const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + jg * 4 * DP;
         float zz[2][4];
-  #pragma unroll
+#pragma unroll
         for (int u = 0; u < 4; ++u) {
           float xj[D];
-  #pragma unroll
+#pragma unroll
           for (int d = 0; d < D; ++d) xj[d] = rs[u * DP + d];
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < 2; ++m) {
             float r2 = 0.f;
-  #pragma unroll
+#pragma unroll
             for (int d = 0; d < D; ++d) {
               const float dd = xi[m][d] - xj[d];
               r2 = fmaf(dd, dd, r2);
@@ -371,7 +398,7 @@ __global__ void __launch_bounds__(RC_NT, 1)
             zz[m][u] = ex2_approx(-r2);
           }
         }
-  #pragma unroll
+#pragma unroll
         for (int m = 0; m < 2; ++m) {
           const int row = rg + 32 * (2 * mh + m);
           const size_t off = (size_t)(row >> 3) * 1024 + (row & 7) * 16 + jg * 128;
@@ -388,15 +415,15 @@ __global__ void __launch_bounds__(RC_NT, 1)
           *reinterpret_cast<float4 *>(slot + RC_ZOP + off) = l;
         }
         fence_proxy_async_smem();
-      }
-      mbar_arrive(&zready[z]);
-      // segment g - 1 is added into registers part-way through segment g
-      if (ch % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
-        if (!flush(ch / RC_SEG - 1)) {
-          ok = false;
-          break;
+        mbar_arrive(&zready[z]);
+        // segment g - 1 is added into registers part-way through segment g
+        if (ch % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
+          if (!flush(ch / RC_SEG - 1)) {
+            ok = false;
+            break;
+          }
+          ++flushed;
         }
-        ++flushed;
       }
     }
     for (; ok && flushed < nseg; ++flushed)
