@@ -96,6 +96,22 @@ def test_fused_inference_per_tile(vds, ctx, N):
     assert _rel(got, s_o) <= 2e-2
 
 
+@pytest.mark.parametrize("D", [2, 6, 16])
+def test_fused_inference_other_dimensions(vds, ctx, D):
+    # the input block holds D <= 16 coordinates in its first two 8-column
+    # groups and the output layer stores the first D of its 16 columns
+    layers = _layers(21 + D, D=D)
+    net = vds.Score(ctx, D, layers)
+    N = 3 * 128 + 5
+    x = np.random.default_rng(D).standard_normal((N, D)).astype(np.float32)
+    out = torch.empty((N, D), device="cuda")
+    net.eval(torch.from_numpy(x).cuda(), out)
+    got = out.cpu().numpy()
+    ref = _forward_bf16_points(layers, x)
+    for t0 in range(0, N, 128):
+        assert _rel(got[t0:t0 + 128], ref[t0:t0 + 128]) <= 6e-3
+
+
 def test_inference_follows_parameter_updates(vds, ctx):
     # the packed weight stream of the inference kernel is rebuilt after a
     # training step and after set_params
