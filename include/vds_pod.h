@@ -84,11 +84,14 @@ VDS_API int pod_step(vds_ctx *ctx, const pod_basis *b, float *P, int N, int D,
  * entropy gradient S replaced by the network's score at the lifted state,
  * mean-centred over the particles (the exact S sums to zero):
  *   Pdot = Phi^T [kappa q~ - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi(q~))].
- * Every check_every steps (0: never) the exact S is evaluated (full density
- * and gradient passes) and compared on check_n particles (every
- * (N/check_n)-th) by ||s - mean s - S|| / ||S||; above check_tol that step
- * uses the exact S (fallback).  check_err (host, may be NULL) receives the
- * largest relative error seen, fallbacks (host, may be NULL) their number. */
+ * Every check_every steps (0: never) the exact S of check_n particles (every
+ * (N/check_n)-th) is evaluated (a full density pass, then the gradient of
+ * those rows only) and compared by ||s - mean s - S|| / ||S||; above
+ * check_tol that step uses the exact S of every particle (fallback).
+ * check_err (host, may be NULL) receives the largest relative error seen,
+ * fallbacks (host, may be NULL) their number.  The steps between checks
+ * (after the first step of the call) replay one CUDA graph captured on a
+ * private stream and launched on the context's stream. */
 #ifndef VDS_SCORE_TYPEDEF
 #define VDS_SCORE_TYPEDEF
 typedef struct vds_score vds_score;

@@ -33,7 +33,12 @@ VDS_API int vds_score_create(vds_ctx *ctx, int D, int width, const float *params
 VDS_API void vds_score_free(vds_score *s);
 VDS_API int vds_score_set_params(vds_ctx *ctx, vds_score *s, const float *params);
 VDS_API int vds_score_get_params(vds_ctx *ctx, const vds_score *s, float *params);
-/* out (device, N x D) = s_theta(x) for x (device, N x D). */
+/* out (device, N x D) = s_theta(x) for x (device, N x D), all four layers
+ * in one persistent tensor-core launch (the activations of each 128-row
+ * tile stay on chip).  Its SiLU uses the hardware tanh, z sigma(z) =
+ * h (1 + tanh h) with h = z/2, so outputs differ from the training forward's
+ * by far less than the BF16 rounding of the activations.  The first call
+ * after the parameters change repacks the BF16 weights (one extra launch). */
 VDS_API int vds_score_eval(vds_ctx *ctx, vds_score *s, const float *x, int N, float *out);
 /* Denoising score-matching loss on a batch of M rows (M a multiple of 128):
  * L = (1/M) sum_m |s_theta(x_m + sigma eps_m) + eps_m/sigma|^2 and its
