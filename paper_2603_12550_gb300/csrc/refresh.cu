@@ -292,9 +292,11 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
 #pragma unroll
     for (int j = 0; j < QC; ++j) tot[j] = 0.f;
-    unsigned long long xi2[TA ? D : 1];  // TA: the row's coordinates duplicated in both halves
+    unsigned long long xi2[D];  // TA: the row's coordinates duplicated in both halves
+    if constexpr (TA) {
 #pragma unroll
-    for (int d = 0; d < (TA ? D : 1); ++d) xi2[d] = f2_pack(xi[0][d], xi[0][d]);
+      for (int d = 0; d < D; ++d) xi2[d] = f2_pack(xi[0][d], xi[0][d]);
+    }
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
