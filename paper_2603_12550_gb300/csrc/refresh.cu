@@ -80,8 +80,14 @@ struct RcLayout {
 // tensor cores' K-major operand: element (c, k) at byte (c/8)*1024 +
 // (k/4)*128 + (c%8)*16 + (k%4)*4 of the hi tile, the lo tile BOP bytes after
 // it; image (cb, ch) at float offset ((cb * nch + ch) * 2 NCP RC_KC).
+//
+// recp (may be NULL) receives the records again, interleaved by pairs of
+// particles: particle k of a 32-particle chunk, pair p = k/2, half k%2,
+// coordinate d at float (chunk * 32 + 2 p) * DP + 2 d + k%2, so that one
+// 64-bit shared load gives coordinate d of both particles of a pair as the
+// two halves of an f32x2 operand.
 __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int rr, const float *__restrict__ rec,
-                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bimg) {
+                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bimg, float *__restrict__ recp) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y, cb = blockIdx.z;
   if (K >= Npad) return;
@@ -106,6 +112,10 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
   const float h = to_tf32(v);
   bimg[o] = h;
   bimg[o + tile] = to_tf32(v - h);
+  if (recp && c == 0 && cb == 0) {
+    float *dst = recp + ((size_t)ch * RC_KC + (k & ~1)) * DP + (k & 1);
+    for (int d = 0; d < DP; ++d) dst[2 * d] = rec[(size_t)K * DP + d];
+  }
 }
 
 // Packed pairs of FP32 values (f32x2 instructions: one issue slot for two
@@ -156,7 +166,8 @@ __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile
 //   accfree[b] RC_PT arrivals: segment g added into registers (completion v).
 template <int D, int NCP>
 __global__ void __launch_bounds__(RC_NT, 1)
-    k_refresh_tc(const float *__restrict__ rec, int N, int Npad, const float *__restrict__ bimg,
+    k_refresh_tc(const float *__restrict__ rec, const float *__restrict__ recp, int N, int Npad,
+                 const float *__restrict__ bimg,
                  const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
                  float *__restrict__ U2, int nsplit, float *__restrict__ part, int *err) {
   using L = RcLayout<D, NCP>;
@@ -224,7 +235,8 @@ __global__ void __launch_bounds__(RC_NT, 1)
         }
         uint8_t *slot = sm + (size_t)z * L::SLOT;
         mbar_arrive_expect_tx(&full[z], (uint32_t)(L::REC_BYTES + 2 * L::BOP));
-        bulk_g2s(slot + L::ROFF, rec + (size_t)(c0 + ch) * RC_KC * DP, L::REC_BYTES, &full[z]);
+        // the tensor-memory path reads the records interleaved by pairs
+        bulk_g2s(slot + L::ROFF, (TA ? recp : rec) + (size_t)(c0 + ch) * RC_KC * DP, L::REC_BYTES, &full[z]);
         bulk_g2s(slot + L::BOFF, bsrc + (size_t)ch * 2 * NCP * RC_KC, 2 * L::BOP, &full[z]);
       }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
@@ -323,13 +335,16 @@ __global__ void __launch_bounds__(RC_NT, 1)
     // instruction: the squared distances to records u and u + 1 in the two
     // halves of a packed register
     auto z_chunk = [&](const uint8_t *slot, uint32_t (&hv)[8], uint32_t (&lv)[8]) {
-      const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + cq * 8 * DP;
+      // records interleaved by pairs: coordinate d of particles u and u + 1
+      // is one 64-bit word
+      const unsigned long long *rs =
+          reinterpret_cast<const unsigned long long *>(slot + L::ROFF) + cq * 4 * DP;
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         unsigned long long r2 = f2_pack(0.f, 0.f);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const unsigned long long dd = f2_sub(xi2[d], f2_pack(rs[u * DP + d], rs[(u + 1) * DP + d]));
+          const unsigned long long dd = f2_sub(xi2[d], rs[(u / 2) * DP + d]);
           r2 = f2_fma(dd, dd, r2);
         }
         float r2a, r2b;
@@ -505,14 +520,14 @@ __global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, in
 }
 
 template <int D, int NCP>
-int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg, int nsplit,
-                   float *part, float *U1, float *U2) {
+int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
+                   const float *recp, int nsplit, float *part, float *U1, float *U2) {
   using L = RcLayout<D, NCP>;
   VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L::SMEM));
   const int ntiles = (N + RC_M - 1) / RC_M;
   dim3 grid(ntiles * nsplit, ncb);
-  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, N, Npad, bimg, b->phi,
+  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recp, N, Npad, bimg, b->phi,
                                                              b->ld, b->r, b->s, rr, U1, U2, nsplit,
                                                              nsplit > 1 ? part : nullptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
@@ -561,18 +576,19 @@ int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
   const int ntiles = (N + RC_M - 1) / RC_M;
   const int nsplit = refresh_splits(ntiles, ncb, (Npad / RC_KC + RC_SEG - 1) / RC_SEG, c->num_sms);
   const size_t npart = nsplit > 1 ? (size_t)ncb * ntiles * nsplit * RC_M * NCP : 0;
-  VDS_TRY(vds_ensure(c, c->gbuf, (2 * nbt + npart) * sizeof(float)));
-  float *bimg = (float *)c->gbuf.ptr, *part = bimg + 2 * nbt;
+  const size_t nrecp = NCP <= 64 ? (size_t)Npad * Rec<D>::DP : 0;  // pair-interleaved records (TA path)
+  VDS_TRY(vds_ensure(c, c->gbuf, (2 * nbt + npart + nrecp) * sizeof(float)));
+  float *bimg = (float *)c->gbuf.ptr, *part = bimg + 2 * nbt, *recp = nrecp ? part + npart : nullptr;
   k_rc_bt<<<dim3((Npad + 255) / 256, NCP, ncb), 256, 0, c->stream>>>(b->phi, b->ld, r, s, rr,
                                                                      (const float *)c->rec.ptr, Rec<D>::DP, D,
-                                                                     N, Npad, NCP, bimg);
+                                                                     N, Npad, NCP, bimg, recp);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   switch (NCP) {
-    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
-    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
-    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
-    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, nsplit, part, U1, U2);
+    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
+    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
+    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
+    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
   }
 }
 
