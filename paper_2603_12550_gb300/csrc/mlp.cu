@@ -430,6 +430,33 @@ constexpr int F_STAGES = (227 * 1024 - 1024 - F_HBYTES - F_BIAS_FLOATS * 4) / F_
 constexpr size_t F_SMEM = F_HBYTES + F_STAGES * F_COPY + F_BIAS_FLOATS * 4;
 constexpr size_t F_WPACK_BYTES = 18 * (size_t)F_CHUNK + 8192;
 
+// Packed pairs of FP32 values (f32x2 instructions; each half rounded as the
+// scalar instruction).
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 __device__ __forceinline__ float tanh_approx(float x) {
   float y;
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -662,13 +689,19 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             const int c0 = kc * 64 + cp * 16;
             tc_ld16(ta + (uint32_t)c0, v);
             uint32_t pk[8];
+            // two columns per f32x2 instruction (each half rounded as the
+            // scalar operation): adjacent accumulator columns and biases
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              const float z0 = __uint_as_float(v[2 * u]) + bias[c0 + 2 * u];
-              const float z1 = __uint_as_float(v[2 * u + 1]) + bias[c0 + 2 * u + 1];
-              const float h0 = 0.5f * z0, h1 = 0.5f * z1;
-              const __nv_bfloat162 t =
-                  __floats2bfloat162_rn(fmaf(h0, tanh_approx(h0), h0), fmaf(h1, tanh_approx(h1), h1));
+              const unsigned long long b2 = *reinterpret_cast<const unsigned long long *>(bias + c0 + 2 * u);
+              const unsigned long long h2 =
+                  f2_mul(f2_add(f2_pack(__uint_as_float(v[2 * u]), __uint_as_float(v[2 * u + 1])), b2),
+                         f2_pack(0.5f, 0.5f));
+              float h0, h1;
+              f2_unpack(h2, h0, h1);
+              float y0, y1;
+              f2_unpack(f2_fma(h2, f2_pack(tanh_approx(h0), tanh_approx(h1)), h2), y0, y1);
+              const __nv_bfloat162 t = __floats2bfloat162_rn(y0, y1);
               pk[u] = *reinterpret_cast<const uint32_t *>(&t);
             }
             uint8_t *hk = h + kc * 16384;
