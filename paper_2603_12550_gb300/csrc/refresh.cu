@@ -56,13 +56,16 @@ struct RcLayout {
   static constexpr int DP = Rec<D>::DP;
   static constexpr bool TA = NCP <= 64;                  // Z tiles in tensor memory
   static constexpr int BOP = NCP * RC_KC * 4;            // one B operand tile
-  static constexpr int REC_BYTES = RC_KC * DP * 4;       // records of one chunk
+  // records of one chunk as staged: interleaved by particle pairs (TA) or
+  // with every coordinate duplicated (shared-memory Z path), so that a
+  // 64-bit shared load is a ready f32x2 operand either way
+  static constexpr int REC_BYTES = RC_KC * DP * 4 * (TA ? 1 : 2);
   static constexpr int REC = ((REC_BYTES + 127) / 128) * 128;
   static constexpr int ZB = TA ? 0 : 2 * RC_ZOP;         // Z tiles of a slot
   static constexpr int BOFF = ZB;                        // B hi, then B lo
   static constexpr int ROFF = ZB + 2 * BOP;              // records
   static constexpr int SLOT = ((ZB + 2 * BOP + REC + 1023) / 1024) * 1024;
-  static constexpr int NZ = TA ? 4 : ((200 * 1024 / SLOT) < 4 ? (200 * 1024 / SLOT) : 4);
+  static constexpr int NZ = TA ? 4 : ((216 * 1024 / SLOT) < 4 ? (216 * 1024 / SLOT) : 4);
   static constexpr int TOT_LD = NCP + 1;                 // epilogue row stride (floats)
   static constexpr size_t RING = (size_t)NZ * SLOT;
   static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
@@ -81,13 +84,16 @@ struct RcLayout {
 // (k/4)*128 + (c%8)*16 + (k%4)*4 of the hi tile, the lo tile BOP bytes after
 // it; image (cb, ch) at float offset ((cb * nch + ch) * 2 NCP RC_KC).
 //
-// recp (may be NULL) receives the records again, interleaved by pairs of
-// particles: particle k of a 32-particle chunk, pair p = k/2, half k%2,
+// recs receives the records again as the refresh stages them.  NCP <= 64
+// (Z in tensor memory, one row per thread): interleaved by pairs of
+// particles, particle k of a 32-particle chunk, pair p = k/2, half k%2,
 // coordinate d at float (chunk * 32 + 2 p) * DP + 2 d + k%2, so that one
 // 64-bit shared load gives coordinate d of both particles of a pair as the
-// two halves of an f32x2 operand.
+// two halves of an f32x2 operand.  NCP > 64 (two rows per thread): every
+// coordinate duplicated, particle K's coordinate d at floats
+// 2 (K DP + d) and 2 (K DP + d) + 1, the operand against a pair of rows.
 __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int rr, const float *__restrict__ rec,
-                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bimg, float *__restrict__ recp) {
+                        int DP, int D, int N, int Npad, int NCP, float *__restrict__ bimg, float *__restrict__ recs) {
   const int K = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y, cb = blockIdx.z;
   if (K >= Npad) return;
@@ -112,9 +118,14 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
   const float h = to_tf32(v);
   bimg[o] = h;
   bimg[o + tile] = to_tf32(v - h);
-  if (recp && c == 0 && cb == 0) {
-    float *dst = recp + ((size_t)ch * RC_KC + (k & ~1)) * DP + (k & 1);
-    for (int d = 0; d < DP; ++d) dst[2 * d] = rec[(size_t)K * DP + d];
+  if (c == 0 && cb == 0) {
+    if (NCP <= 64) {
+      float *dst = recs + ((size_t)ch * RC_KC + (k & ~1)) * DP + (k & 1);
+      for (int d = 0; d < DP; ++d) dst[2 * d] = rec[(size_t)K * DP + d];
+    } else {
+      float *dst = recs + (size_t)K * 2 * DP;
+      for (int d = 0; d < DP; ++d) dst[2 * d] = dst[2 * d + 1] = rec[(size_t)K * DP + d];
+    }
   }
 }
 
@@ -166,7 +177,7 @@ __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile
 //   accfree[b] RC_PT arrivals: segment g added into registers (completion v).
 template <int D, int NCP>
 __global__ void __launch_bounds__(RC_NT, 1)
-    k_refresh_tc(const float *__restrict__ rec, const float *__restrict__ recp, int N, int Npad,
+    k_refresh_tc(const float *__restrict__ rec, const float *__restrict__ recs, int N, int Npad,
                  const float *__restrict__ bimg,
                  const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
                  float *__restrict__ U2, int nsplit, float *__restrict__ part, int *err) {
@@ -235,8 +246,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
         }
         uint8_t *slot = sm + (size_t)z * L::SLOT;
         mbar_arrive_expect_tx(&full[z], (uint32_t)(L::REC_BYTES + 2 * L::BOP));
-        // the tensor-memory path reads the records interleaved by pairs
-        bulk_g2s(slot + L::ROFF, (TA ? recp : rec) + (size_t)(c0 + ch) * RC_KC * DP, L::REC_BYTES, &full[z]);
+        // the records as staged for the producers' f32x2 operands (k_rc_bt)
+        bulk_g2s(slot + L::ROFF, reinterpret_cast<const uint8_t *>(recs) + (size_t)(c0 + ch) * L::REC_BYTES,
+                 L::REC_BYTES, &full[z]);
         bulk_g2s(slot + L::BOFF, bsrc + (size_t)ch * 2 * NCP * RC_KC, 2 * L::BOP, &full[z]);
       }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
@@ -304,10 +316,15 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
 #pragma unroll
     for (int j = 0; j < QC; ++j) tot[j] = 0.f;
-    unsigned long long xi2[D];  // TA: the row's coordinates duplicated in both halves
+    // TA: the row's coordinates duplicated in both halves; otherwise the two
+    // rows of the thread side by side
+    unsigned long long xi2[D], xi2r[D];
     if constexpr (TA) {
 #pragma unroll
       for (int d = 0; d < D; ++d) xi2[d] = f2_pack(xi[0][d], xi[0][d]);
+    } else {
+#pragma unroll
+      for (int d = 0; d < D; ++d) xi2r[d] = f2_pack(xi[0][d], xi[RPT - 1][d]);
     }
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
@@ -397,23 +414,23 @@ __global__ void __launch_bounds__(RC_NT, 1)
           break;
         }
         uint8_t *slot = sm + (size_t)z * L::SLOT;
-        const float *rs = reinterpret_cast<const float *>(slot + L::ROFF) + jg * 4 * DP;
+        // the thread's two rows in the halves of one f32x2 operand against
+        // the duplicated coordinates of each record
+        const unsigned long long *rs =
+            reinterpret_cast<const unsigned long long *>(slot + L::ROFF) + jg * 4 * DP;
         float zz[2][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          float xj[D];
+          unsigned long long r2 = f2_pack(0.f, 0.f);
 #pragma unroll
-          for (int d = 0; d < D; ++d) xj[d] = rs[u * DP + d];
-#pragma unroll
-          for (int m = 0; m < 2; ++m) {
-            float r2 = 0.f;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              const float dd = xi[m][d] - xj[d];
-              r2 = fmaf(dd, dd, r2);
-            }
-            zz[m][u] = ex2_approx(-r2);
+          for (int d = 0; d < D; ++d) {
+            const unsigned long long dd = f2_sub(xi2r[d], rs[u * DP + d]);
+            r2 = f2_fma(dd, dd, r2);
           }
+          float r2a, r2b;
+          f2_unpack(r2, r2a, r2b);
+          zz[0][u] = ex2_approx(-r2a);
+          zz[1][u] = ex2_approx(-r2b);
         }
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
@@ -521,13 +538,13 @@ __global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, in
 
 template <int D, int NCP>
 int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
-                   const float *recp, int nsplit, float *part, float *U1, float *U2) {
+                   const float *recs, int nsplit, float *part, float *U1, float *U2) {
   using L = RcLayout<D, NCP>;
   VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)L::SMEM));
   const int ntiles = (N + RC_M - 1) / RC_M;
   dim3 grid(ntiles * nsplit, ncb);
-  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recp, N, Npad, bimg, b->phi,
+  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recs, N, Npad, bimg, b->phi,
                                                              b->ld, b->r, b->s, rr, U1, U2, nsplit,
                                                              nsplit > 1 ? part : nullptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
@@ -576,19 +593,20 @@ int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
   const int ntiles = (N + RC_M - 1) / RC_M;
   const int nsplit = refresh_splits(ntiles, ncb, (Npad / RC_KC + RC_SEG - 1) / RC_SEG, c->num_sms);
   const size_t npart = nsplit > 1 ? (size_t)ncb * ntiles * nsplit * RC_M * NCP : 0;
-  const size_t nrecp = NCP <= 64 ? (size_t)Npad * Rec<D>::DP : 0;  // pair-interleaved records (TA path)
-  VDS_TRY(vds_ensure(c, c->gbuf, (2 * nbt + npart + nrecp) * sizeof(float)));
-  float *bimg = (float *)c->gbuf.ptr, *part = bimg + 2 * nbt, *recp = nrecp ? part + npart : nullptr;
+  // records as staged: pair-interleaved (NCP <= 64) or duplicated (NCP > 64)
+  const size_t nrecs = (size_t)Npad * Rec<D>::DP * (NCP <= 64 ? 1 : 2);
+  VDS_TRY(vds_ensure(c, c->gbuf, (2 * nbt + npart + nrecs) * sizeof(float)));
+  float *bimg = (float *)c->gbuf.ptr, *part = bimg + 2 * nbt, *recs = part + npart;
   k_rc_bt<<<dim3((Npad + 255) / 256, NCP, ncb), 256, 0, c->stream>>>(b->phi, b->ld, r, s, rr,
                                                                      (const float *)c->rec.ptr, Rec<D>::DP, D,
-                                                                     N, Npad, NCP, bimg, recp);
+                                                                     N, Npad, NCP, bimg, recs);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   switch (NCP) {
-    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
-    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
-    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
-    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, recp, nsplit, part, U1, U2);
+    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
+    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
+    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
+    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
   }
 }
 
