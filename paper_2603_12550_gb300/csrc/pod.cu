@@ -268,12 +268,22 @@ __global__ void __launch_bounds__(256)
 
 constexpr int TR = 32;  // rows per tile
 
-// partial[blk][64x64] = sum over the block's rows of A[row,:]^T B[row,:]
+// partial[blk][64x64] = sum over the block's rows of A[row,:]^T B[row,:] for
+// the leading W x W corner, W = 4 TT >= r (the rest of the 64 x 64 slot is
+// left unwritten).  TT x TT threads of 4 x 4 outputs each cover the corner;
+// the 256 / TT^2 such groups take every RG-th row of a tile and are summed
+// in a fixed order at the end, so the FP64 work per row is W^2 rather than
+// 64^2 for small r.  Rows are staged in shared memory already in FP64.
+template <int TT>
 __global__ void __launch_bounds__(256)
     k_tsgram(const float *__restrict__ A, const float *__restrict__ B, long Ns, int ld, long rchunk,
              double *__restrict__ part) {
-  __shared__ float As[TR][64], Bs[TR][64];
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  constexpr int W = 4 * TT, NG = TT * TT, RG = 256 / NG;
+  static_assert(2 * TR * W <= 4096 && RG * W * W == 4096, "tsgram shared memory");
+  __shared__ double sm[4096];  // As, Bs while accumulating, then the group partials
+  double *As = sm, *Bs = sm + TR * W;
+  const int tid = threadIdx.x, g = tid % NG, tx = g % TT, ty = g / TT, rg = tid / NG;
+  const int wc = min(ld, W);
   const long r0 = (long)blockIdx.x * rchunk, r1 = min(Ns, r0 + rchunk);
   double acc[4][4];
 #pragma unroll
@@ -281,21 +291,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
   for (long rb = r0; rb < r1; rb += TR) {
-    for (int e = tid; e < TR * 64; e += 256) {
-      const int rr = e / 64, c = e - (e / 64) * 64;
+    for (int e = tid; e < TR * W; e += 256) {
+      const int rr = e / W, c = e - (e / W) * W;
       const long row = rb + rr;
-      const bool ok = row < r1 && c < ld;
-      As[rr][c] = ok ? A[row * ld + c] : 0.f;
-      Bs[rr][c] = ok ? B[row * ld + c] : 0.f;
+      const bool ok = row < r1 && c < wc;
+      As[e] = ok ? (double)A[row * ld + c] : 0.0;
+      Bs[e] = ok ? (double)B[row * ld + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll 4
-    for (int rr = 0; rr < TR; ++rr) {
+    for (int rr = rg; rr < TR; rr += RG) {
       double a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        a[i] = (double)As[rr][tx * 4 + i];
-        b[i] = (double)Bs[rr][ty * 4 + i];
+        a[i] = As[rr * W + tx * 4 + i];
+        b[i] = Bs[rr * W + ty * 4 + i];
       }
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -304,21 +314,33 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
   }
-  double *dst = part + (size_t)blockIdx.x * 4096;
+  double *red = sm + (size_t)rg * W * W;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) dst[(tx * 4 + i) * 64 + ty * 4 + j] = acc[i][j];
+    for (int j = 0; j < 4; ++j) red[(tx * 4 + i) * W + ty * 4 + j] = acc[i][j];
+  __syncthreads();
+  double *dst = part + (size_t)blockIdx.x * 4096;
+  for (int o = tid; o < W * W; o += 256) {
+    double v = 0.0;
+    for (int q = 0; q < RG; ++q) v += sm[(size_t)q * W * W + o];
+    dst[(o / W) * 64 + o % W] = v;
+  }
 }
 
+// G[i][j] = sum over the blocks' partials: one warp per output, the lanes
+// taking every 32nd block and a fixed shuffle tree combining them, so the
+// order (and the result) does not depend on scheduling.
 __global__ void k_tsgram_reduce(const double *__restrict__ part, int nblk, int r,
                                 double *__restrict__ G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (idx >= r * r) return;
   const int i = idx / r, j = idx - (idx / r) * r;
   double v = 0.0;
-  for (int b = 0; b < nblk; ++b) v += part[(size_t)b * 4096 + i * 64 + j];
-  G[idx] = v;
+  for (int b = lane; b < nblk; b += 32) v += part[(size_t)b * 4096 + i * 64 + j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) G[idx] = v;
 }
 
 // Cholesky G = L L^T (FP64, one thread) and Linv = L^-1; failure flags.
@@ -525,9 +547,14 @@ struct TmpBufs {
 
 int tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *part,
            int nblk, long rchunk, double *G) {
-  k_tsgram<<<nblk, 256, 0, c->stream>>>(A, B, Ns, ld, rchunk, part);
+  if (r <= 16)
+    k_tsgram<4><<<nblk, 256, 0, c->stream>>>(A, B, Ns, ld, rchunk, part);
+  else if (r <= 32)
+    k_tsgram<8><<<nblk, 256, 0, c->stream>>>(A, B, Ns, ld, rchunk, part);
+  else
+    k_tsgram<16><<<nblk, 256, 0, c->stream>>>(A, B, Ns, ld, rchunk, part);
   VDS_CUDA_TRY(cudaGetLastError());
-  k_tsgram_reduce<<<(r * r + 255) / 256, 256, 0, c->stream>>>(part, nblk, r, G);
+  k_tsgram_reduce<<<(r * r + 7) / 8, 256, 0, c->stream>>>(part, nblk, r, G);
   VDS_CUDA_TRY(cudaGetLastError());
   c->launches += 2;
   return VDS_OK;
