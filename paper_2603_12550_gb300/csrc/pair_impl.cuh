@@ -35,6 +35,14 @@ constexpr int NSTAGE = VDS_PAIR_NSTAGE;  // shared-memory ring depth
 // 384 x 3: 2.46 + 3.86 ms against 2.51 + 3.99 ms for 256 x 4 in both); other
 // D keep 256 threads, 4 particles per thread, 2 for the gradient above D = 9
 // (255 registers).
+// Small clouds (the paper's P = 1000 workloads, the 2D dumbbell): with the
+// shapes below the (i-tile, j-chunk) items would cover fewer than half the
+// SMs (N = 1000 gives 4 items), so such passes take 128 threads of one
+// particle and 64-record j-tiles instead (N = 1000: 128 items).  Explicit
+// step on GB300: N = 1000, D = 9 131 -> 50 us; N = 512, D = 2 40 -> 23 us;
+// N = 4096, D = 9 142 -> 102 us.
+constexpr int NT_SMALL = 128, RI_SMALL = 1, TJ_SMALL = 64;
+
 template <int D>
 struct PairCfg {
   static constexpr int NT_DENS = (D == 9) ? 512 : 256;
@@ -45,13 +53,14 @@ struct PairCfg {
 
 // ------------------------------------------------------------- pair kernel
 
-template <int D, int RI, int NT, bool GRAD>
+template <int D, int RI, int NT, bool GRAD, int TJK = TJ>
 __global__ void __launch_bounds__(NT)
     k_pair(const float *__restrict__ rec, const float *__restrict__ reci, Sched sc,
            double *__restrict__ part, int *__restrict__ err) {
+  static_assert(TJ % TJK == 0, "j-tiles divide the record padding");
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
-  constexpr uint32_t TILE_FLOATS = TJ * DP;
+  constexpr uint32_t TILE_FLOATS = TJK * DP;
   constexpr uint32_t TILE_BYTES = TILE_FLOATS * 4;
   extern __shared__ __align__(128) float tiles[];  // NSTAGE * TILE_FLOATS
   __shared__ __align__(8) uint64_t full[NSTAGE];
@@ -125,7 +134,7 @@ __global__ void __launch_bounds__(NT)
       for (int a = 0; a < ACC; ++a) acc[k][a] = 0.f;
 
 #pragma unroll 2
-    for (int j = 0; j < TJ; ++j) {
+    for (int j = 0; j < TJK; ++j) {
       float xj[DP];
       const float4 *pj = reinterpret_cast<const float4 *>(tj + j * DP);
 #pragma unroll
@@ -602,27 +611,27 @@ __global__ void k_flow(KParams kp, const float *__restrict__ q, float *__restric
 
 // i points: the Ni records at reci (the particles themselves unless a query
 // pass); j points: the N particle records in c->rec.
-template <int D, int RI, int NT, bool GRAD>
+template <int D, int RI, int NT, bool GRAD, int TJK = TJ>
 int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
   constexpr int TI = NT * RI;
-  const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
+  const size_t smem = (size_t)NSTAGE * TJK * DP * sizeof(float);
   // per device: the attribute is a property of the function on that device
   static int occ_dev[VDS_MAX_DEVICES] = {};
   int &occ = occ_dev[c->device < VDS_MAX_DEVICES ? c->device : 0];
   if (occ <= 0 || c->device >= VDS_MAX_DEVICES) {
     // large D needs more than the default 48 KB of dynamic shared memory
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD, TJK>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int o = 0;
-    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, NT, GRAD>, NT, smem));
+    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, NT, GRAD, TJK>, NT, smem));
     occ = o > 0 ? o : 1;
   }
   sc.TI = TI;
   sc.Npad = (N + TJ - 1) / TJ * TJ;
   sc.Nipad = (Ni + TJ - 1) / TJ * TJ;
-  sc.nchunk = sc.Npad / TJ;
+  sc.nchunk = sc.Npad / TJK;
   sc.n_itiles = (Ni + TI - 1) / TI;
   sc.items = (long long)sc.n_itiles * sc.nchunk;
   const long long cap = (long long)c->num_sms * occ;
@@ -637,8 +646,8 @@ int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   VDS_TRY(vds_ensure(c, c->part, (size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double)));
   const int pk = GRAD ? PK_GRADIENT : PK_DENSITY;
   VDS_TRY(vds_time_begin(c, pk));
-  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, reci, sc,
-                                                           (double *)c->part.ptr, c->err);
+  k_pair<D, RI, NT, GRAD, TJK><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, reci, sc,
+                                                                (double *)c->part.ptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   VDS_TRY(vds_time_end(c, pk));
   ++c->launches;
@@ -657,12 +666,22 @@ int prep_impl(vds_ctx *c, const KParams &kp, const float *base, const float *del
   return VDS_OK;
 }
 
+// One pair pass with the pass's shape, or the small-cloud shape when the
+// former's items would cover fewer than half the SMs.
+template <int D, bool GRAD>
+int launch_pass(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
+  constexpr int RI = GRAD ? PairCfg<D>::RI_GRAD : PairCfg<D>::RI_DENS;
+  constexpr int NT = GRAD ? PairCfg<D>::NT_GRAD : PairCfg<D>::NT_DENS;
+  const long long items = (long long)((Ni + NT * RI - 1) / (NT * RI)) * ((N + TJ - 1) / TJ);
+  if (2 * items < c->num_sms) return launch_pair<D, RI_SMALL, NT_SMALL, GRAD, TJ_SMALL>(c, N, sc, Ni, reci);
+  return launch_pair<D, RI, NT, GRAD>(c, N, sc, Ni, reci);
+}
+
 template <int D>
 int density_impl(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
                  const float *ybase, const float *ydelta, const float *qa, const float *qb) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc, kp.N,
-                                                                             (const float *)c->rec.ptr)));
+  VDS_TRY((launch_pass<D, false>(c, kp.N, sc, kp.N, (const float *)c->rec.ptr)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   k_dens_finish<D><<<nb, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, (float *)c->rec.ptr,
@@ -678,8 +697,7 @@ template <int D>
 int grad_impl(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,
               const float *ydelta, const float *qa, const float *qb, float *q_io) {
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(c, kp.N, sc, kp.N,
-                                                                           (const float *)c->rec.ptr)));
+  VDS_TRY((launch_pass<D, true>(c, kp.N, sc, kp.N, (const float *)c->rec.ptr)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   const double *pp = (const double *)c->part.ptr;
@@ -731,8 +749,7 @@ int query_impl(vds_ctx *c, const KParams &kp, const float *q, const float *y, in
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   Sched sc;
-  VDS_TRY((launch_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(c, kp.N, sc, M,
-                                                                             (const float *)c->recq.ptr)));
+  VDS_TRY((launch_pass<D, false>(c, kp.N, sc, M, (const float *)c->recq.ptr)));
   k_query_finish<D><<<(M + NT_FIN - 1) / NT_FIN, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, M,
                                                                          exp(kp.lnorm), f_out, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
