@@ -667,13 +667,18 @@ int prep_impl(vds_ctx *c, const KParams &kp, const float *base, const float *del
 }
 
 // One pair pass with the pass's shape, or the small-cloud shape when the
-// former's items would cover fewer than half the SMs.
+// former's items would cover fewer than half the SMs.  Between the two
+// (fewer than 8 items per SM), the pass's shape takes 64-record j-chunks:
+// four times the items, so that the last round of the stream-K split is
+// not a large fraction of the pass (N = 10000 at D = 9: 200 and 360 items
+// per pass at 256 records).
 template <int D, bool GRAD>
 int launch_pass(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   constexpr int RI = GRAD ? PairCfg<D>::RI_GRAD : PairCfg<D>::RI_DENS;
   constexpr int NT = GRAD ? PairCfg<D>::NT_GRAD : PairCfg<D>::NT_DENS;
   const long long items = (long long)((Ni + NT * RI - 1) / (NT * RI)) * ((N + TJ - 1) / TJ);
   if (2 * items < c->num_sms) return launch_pair<D, RI_SMALL, NT_SMALL, GRAD, TJ_SMALL>(c, N, sc, Ni, reci);
+  if (items < 8LL * c->num_sms) return launch_pair<D, RI, NT, GRAD, TJ_SMALL>(c, N, sc, Ni, reci);
   return launch_pair<D, RI, NT, GRAD>(c, N, sc, Ni, reci);
 }
 
