@@ -35,14 +35,6 @@ constexpr int NSTAGE = VDS_PAIR_NSTAGE;  // shared-memory ring depth
 // 384 x 3: 2.46 + 3.86 ms against 2.51 + 3.99 ms for 256 x 4 in both); other
 // D keep 256 threads, 4 particles per thread, 2 for the gradient above D = 9
 // (255 registers).
-// Small clouds (the paper's P = 1000 workloads, the 2D dumbbell): with the
-// shapes below the (i-tile, j-chunk) items would cover fewer than half the
-// SMs (N = 1000 gives 4 items), so such passes take 128 threads of one
-// particle and 64-record j-tiles instead (N = 1000: 128 items).  Explicit
-// step on GB300: N = 1000, D = 9 131 -> 50 us; N = 512, D = 2 40 -> 23 us;
-// N = 4096, D = 9 142 -> 102 us.
-constexpr int NT_SMALL = 128, RI_SMALL = 1, TJ_SMALL = 64;
-
 template <int D>
 struct PairCfg {
   static constexpr int NT_DENS = (D == 9) ? 512 : 256;
@@ -50,6 +42,14 @@ struct PairCfg {
   static constexpr int NT_GRAD = (D == 9) ? 384 : 256;
   static constexpr int RI_GRAD = (D <= 6) ? 4 : (D == 9 ? 3 : (D <= 9 ? 4 : 2));
 };
+
+// Small clouds (the paper's P = 1000 workloads, the 2D dumbbell): with the
+// shapes above the (i-tile, j-chunk) items would cover fewer than half the
+// SMs (N = 1000 gives 4 items), so such passes take 128 threads of one
+// particle and 64-record j-tiles instead (N = 1000: 128 items).  Explicit
+// step on GB300: N = 1000, D = 9 131 -> 50 us; N = 512, D = 2 40 -> 23 us;
+// N = 4096, D = 9 142 -> 102 us.
+constexpr int NT_SMALL = 128, RI_SMALL = 1, TJ_SMALL = 64;
 
 // ------------------------------------------------------------- pair kernel
 

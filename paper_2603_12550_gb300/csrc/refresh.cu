@@ -13,9 +13,12 @@
 // particle K): the shape of attention's P V.  Z never exists in memory.  One
 // CTA per 128 particles I (and per column chunk of B), warp-specialised:
 //   warps 0-15  form Z_IK = exp2(-|q^_I - q^_K|^2) for a chunk of 32
-//               particles K (2D FP32 ops and one ex2 per pair, 2 x 4 pairs
-//               per thread), split it into two TF32 parts and store them in
-//               the tensor cores' K-major layout;
+//               particles K (2D FP32 ops and one ex2 per pair, two pairs
+//               per f32x2 instruction), split it into Z_hi = tf32(Z) and
+//               Z_lo = Z - Z_hi (passed unrounded: the MMA uses its TF32
+//               bits) and store both in tensor memory, one row per thread
+//               (2 s r + 1 <= 64), or in shared memory in the tensor cores'
+//               K-major layout;
 //   warp 16     stages each chunk's 32 records and its B slice (hi and lo
 //               TF32 parts, pre-arranged in global memory as the exact
 //               shared-memory image) with 1-D bulk copies (TMA engine);

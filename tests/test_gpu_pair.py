@@ -183,3 +183,29 @@ def test_full_size_chain4_sampled_rows(orc, vds, ctx):
     g_o = orc.entropy_grad_rows(q64, h, rho_o, rows) + orc.spring_grad(q64[rows], po)
     g_g = g.cpu().numpy()[rows].astype(np.float64)
     assert np.max(np.abs(g_g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+
+
+@pytest.mark.parametrize("N", [3001, 10000, 20001])
+def test_chain4_every_pass_shape_matches_oracle(orc, vds, ctx, N):
+    # The pair passes pick their shape from the number of (i-tile, j-chunk)
+    # items: 128 threads of one particle and 64-record chunks for small clouds
+    # (N = 3001), the large shapes with 64-record chunks in between (N =
+    # 10000 for both passes, N = 20001 for the density pass), and with
+    # 256-record chunks above (the gradient pass at N = 20001).  Full density
+    # and sampled gradient rows against the oracle at ragged N.
+    nb, s = 3, 3
+    q32 = inputs.equilibrium_cloud(N, nb, s, seed=N)
+    q64 = q32.astype(np.float64)
+    h = 0.9
+    po, pg = _both_params(orc, vds, nb=nb, s=s, h=h)
+    q = _dev(q32)
+    g = torch.empty_like(q)
+    rho = torch.empty(N, device="cuda")
+    ctx.vds_energy_grad(q, pg, g=g, rho=rho)
+    rho_o = orc.density(q64, h)
+    assert np.max(np.abs(rho.cpu().numpy() - rho_o) / rho_o) <= 1e-5
+    rows = np.random.default_rng(N).choice(N, 96, replace=False)
+    rows[:3] = [0, N - 1, N // 2]
+    g_o = orc.entropy_grad_rows(q64, h, rho_o, rows) + orc.spring_grad(q64[rows], po)
+    g_g = g.cpu().numpy()[rows].astype(np.float64)
+    assert np.max(np.abs(g_g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
