@@ -248,13 +248,70 @@ int vds_density_at(vds_ctx *c, const float *q, int N, int D, const vds_params *p
   return pass_density_at(c, kp, q, y, M, f);
 }
 
+// Explicit steps.  After the first (launched directly; it sizes every buffer
+// a step uses), the steps replay one captured CUDA graph of a step (density
+// pass, its epilogue, gradient pass, the fused update: four kernels with the
+// same arguments every step), which takes the per-launch host cost out of
+// small clouds.  With phase timing on (its events belong to single
+// launches), or if the capture fails, the steps are launched one by one.
 static int step_explicit(vds_ctx *c, float *q, const KParams &kp, int nsteps) {
   VDS_TRY(pass_prep(c, kp, q, nullptr, nullptr, 0.f, nullptr));
-  for (int n = 0; n < nsteps; ++n) {
+  auto one_step = [&]() -> int {
     VDS_TRY(pass_density(c, kp, nullptr, false, q, nullptr, nullptr, nullptr));
-    VDS_TRY(pass_grad(c, kp, GM_EXPLICIT, nullptr, q, nullptr, nullptr, nullptr, q));
+    return pass_grad(c, kp, GM_EXPLICIT, nullptr, q, nullptr, nullptr, nullptr, q);
+  };
+  int n = 0;
+  if (nsteps > 0) {
+    VDS_TRY(one_step());
+    ++n;
   }
-  return vds_sync_status(c);
+  cudaGraphExec_t gexec = nullptr;
+  long per_step = 0;
+  if (nsteps - n >= 2 && !(c->timing && c->timing->on)) {
+    // captured on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured), launched on the caller's stream
+    const long l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaStream_t cs = nullptr, user = c->stream;
+    int st = VDS_OK;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      st = VDS_ECUDA;
+    } else if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = VDS_ECUDA;
+    } else {
+      c->stream = cs;
+      st = one_step();
+      c->stream = user;
+      const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+      if (st == VDS_OK && ec != cudaSuccess) st = VDS_ECUDA;
+    }
+    c->stream = user;
+    if (cs) cudaStreamDestroy(cs);
+    if (st == VDS_OK && cudaGraphInstantiate(&gexec, g, 0) != cudaSuccess) {
+      gexec = nullptr;
+      st = VDS_ECUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+    per_step = c->launches - l0;
+    c->launches = l0;
+    if (st != VDS_OK) {
+      (void)cudaGetLastError();  // a failed capture leaves its status behind
+      if (gexec) cudaGraphExecDestroy(gexec);
+      gexec = nullptr;
+    }
+  }
+  int st = VDS_OK;
+  for (; n < nsteps && gexec; ++n) {
+    if (cudaGraphLaunch(gexec, c->stream) != cudaSuccess) {
+      st = VDS_ECUDA;
+      break;
+    }
+    c->launches += per_step;
+  }
+  for (; st == VDS_OK && n < nsteps; ++n) st = one_step();
+  const int sst = vds_sync_status(c);  // the replays have finished before the graph goes
+  if (gexec) cudaGraphExecDestroy(gexec);
+  return st != VDS_OK ? st : sst;
 }
 
 // Implicit Euler step as the minimiser of J (see vds.h).  y = q* + d is

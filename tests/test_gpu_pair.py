@@ -209,3 +209,19 @@ def test_chain4_every_pass_shape_matches_oracle(orc, vds, ctx, N):
     g_o = orc.entropy_grad_rows(q64, h, rho_o, rows) + orc.spring_grad(q64[rows], po)
     g_g = g.cpu().numpy()[rows].astype(np.float64)
     assert np.max(np.abs(g_g - g_o)) <= 1e-5 * np.max(np.abs(g_o))
+
+
+@pytest.mark.parametrize("N,nb,s", [(1000, 3, 3), (512, 1, 2), (20001, 3, 3)])
+def test_explicit_graph_replay_is_bit_identical(orc, vds, ctx, N, nb, s):
+    # vds_step replays a captured graph of one explicit step after the first;
+    # with phase timing on it launches every step directly.  Same kernels,
+    # same arguments: the states after 7 steps agree bit for bit.
+    q32 = inputs.equilibrium_cloud(N, nb, s, seed=5)
+    _, pg = _both_params(orc, vds, nb=nb, s=s, h=0.7, dt=1e-3, kappa=inputs.shear_kappa(s, 1.0))
+    qa, qb = _dev(q32), _dev(q32)
+    ctx.vds_step(qa, pg, 7)
+    ctx.vds_timing(True)
+    ctx.vds_step(qb, pg, 7)
+    ctx.vds_timing(False)
+    assert torch.equal(qa, qb)
+    assert not torch.equal(qa, _dev(q32))
