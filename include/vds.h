@@ -112,7 +112,12 @@ VDS_API int vds_energy_grad(vds_ctx *ctx, const float *q, int N, int D,
  *   q+ = q* - (dt/zeta)(A (x) I_s) g(q+),  q* = q + dt kappa q,
  * solved as the minimiser of J above by preconditioned descent with FP64
  * Armijo acceptance (unit step = fixed-point iteration).  iters_out (host,
- * nsteps ints, may be NULL) receives gradient evaluations per step. */
+ * nsteps ints, may be NULL) receives gradient evaluations per step.
+ * Explicit calls of three or more steps capture the second step as a CUDA
+ * graph (on a private stream) and replay it for the rest, launched on the
+ * context stream; results are bit-identical to launching every step, which
+ * is what happens while vds_timing is on.  The call synchronises the
+ * context stream before it returns. */
 VDS_API int vds_step(vds_ctx *ctx, float *q, int N, int D, const vds_params *p,
              int nsteps, int *iters_out);
 
