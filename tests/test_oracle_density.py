@@ -157,3 +157,19 @@ def test_grid_points_and_density_error():
     assert oracle.grid_points(9).shape == (3 ** 9, 9)
     e2, einf = oracle.density_error([1.0, 2.0, 2.0], [1.0, 2.0, 4.0])
     assert np.isclose(e2, 2.0 / np.sqrt(21.0)) and np.isclose(einf, 0.5)
+
+
+@pytest.mark.parametrize("spring", [0, 1])
+def test_sampled_rows_agree_with_the_full_gradient(orc, spring):
+    # The full-size GPU tests compare sampled rows with entropy_grad_rows +
+    # spring_grad; both must give exactly the rows of the full g = kBT S +
+    # grad Psi at kBT = 1, whose derivative property is pinned above.
+    N, nb, s = 300, 3, 3
+    q = _cloud(N, nb, s, seed=12)
+    if spring == 1:
+        q *= 0.5
+    p = orc.params(nb, s, H=[1.0, 2.0, 1.5], kBT=1.0, h=0.7, spring=spring, b=20.0)
+    _, g, rho = orc.energy_grad(q, p)
+    rows = np.array([0, 7, 150, N - 1])
+    g_rows = orc.entropy_grad_rows(q, 0.7, rho, rows) + orc.spring_grad(q[rows], p)
+    np.testing.assert_allclose(g_rows, g[rows], rtol=1e-12, atol=1e-12 * np.max(np.abs(g)))
