@@ -288,6 +288,38 @@ def median_bandwidth(q):
     return median_pairdist(q) / np.sqrt(2.0 * np.log(N))
 
 
+def median_pairdist_count(q):
+    """The same lower median of the N(N-1)/2 pair distances (Eq.
+    model_bandwidth) where sorting them does not fit in memory: the k-th
+    smallest squared distance, k = (M-1)/2 + 1 counted from one, is the least
+    r2 with #{J<K : |q_J - q_K|^2 <= r2} >= k.  Found by bisection on r2 over
+    the doubles, each probe one FP64 pair count, until lo and hi are adjacent
+    doubles; hi is then the order statistic itself."""
+    q = np.asarray(q, dtype=np.float64)
+    N = q.shape[0]
+    M = N * (N - 1) // 2
+    k = (M - 1) // 2 + 1
+    lo, hi = 0.0, 1.0
+    while count_pairs(q, hi)[1] < k:
+        lo, hi = hi, 2.0 * hi
+    if count_pairs(q, 0.0)[1] >= k:
+        return 0.0
+    while True:
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if count_pairs(q, mid)[1] >= k:
+            hi = mid
+        else:
+            lo = mid
+    return float(np.sqrt(hi))
+
+
+def median_bandwidth_count(q):
+    """median_bandwidth through median_pairdist_count (large N)."""
+    return median_pairdist_count(q) / np.sqrt(2.0 * np.log(q.shape[0]))
+
+
 def count_pairs(q, r2):
     q, qp = _d(q)
     N, D = q.shape

@@ -109,3 +109,81 @@ def test_fit_gradient_matches_finite_differences():
         dn[l][0][idx] -= 1e-6
         fd = (mlp.fit_grad(up, x, t)[0] - mlp.fit_grad(dn, x, t)[0]) / 2e-6
         assert abs(fd - grads[l][0][idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------ score_rhs (mode iii RHS)
+# Pins of the oracle's reduced right-hand side with the learned score in
+# place of the entropy gradient, each against the Galerkin RHS (mode i),
+# whose parts are pinned separately (closed forms of the spring and flow
+# terms, the linear kBT = 0 steps):
+#   * kBT = 0: the score drops out, so the two RHS agree for any network;
+#   * a constant network (zero weights, nonzero output bias) has mean-centred
+#     score exactly zero, so at kBT = 1 it agrees with the kBT = 0 Galerkin RHS;
+#   * a network realising s(x) = -x + c on a zero-mean lifted cloud makes the
+#     entropic term kBT s = -(q~) (after centring), which is the force of a
+#     Hookean spring of stiffness -kBT: at kBT = 1 with no springs it agrees
+#     with the kBT = 0 Galerkin RHS with H = -1.  A sign error on the kBT
+#     term, a transposed Rouse coupling or a dropped centring fails one of them.
+
+def _zero_mean_basis(N, s, r, seed):
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((N, s, r))
+    Y -= Y.mean(axis=0, keepdims=True)
+    Q, _ = np.linalg.qr(Y.reshape(N * s, r))
+    return Q
+
+
+def _affine_net(D, a, c, B=40.0):
+    # SiLU(z) = z sigma(z) equals z to within |z| e^{-z} for large z, so three
+    # SiLU layers fed x + B pass it through; the last layer maps to a x + c
+    I = np.eye(D)
+    return [(I.copy(), np.full(D, B)), (I.copy(), np.zeros(D)), (I.copy(), np.zeros(D)),
+            (a * I, c - a * B * np.ones(D))]
+
+
+@pytest.mark.parametrize("nb,s", [(1, 2), (3, 3)])
+def test_score_rhs_without_temperature_is_galerkin(orc, nb, s):
+    N, r = 300, 5
+    Phi = _zero_mean_basis(N, s, r, seed=nb)
+    Phi[:, 0] += 0.05  # a nonzero-mean cloud: the score must not matter at kBT = 0
+    Phi, _ = np.linalg.qr(Phi)
+    P = np.random.default_rng(4).standard_normal((r, nb)) * 3.0
+    kap = inputs.shear_kappa(s, 1.3)
+    p = orc.params(nb, s, H=[1.0 + k for k in range(nb)], kBT=0.0, zeta=4.0, h=0.5, kappa=kap)
+    layers = mlp.as64(inputs.mlp_init((nb * s, 32, 32, 32, nb * s), seed=2))
+    np.testing.assert_allclose(orc.score_rhs(P, Phi, p, layers), orc.galerkin_rhs(P, Phi, p),
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_score_rhs_of_a_constant_network_drops_the_entropy(orc):
+    nb, s, N, r = 3, 3, 400, 6
+    Phi, _ = np.linalg.qr(np.random.default_rng(8).standard_normal((N * s, r)))
+    P = np.random.default_rng(9).standard_normal((r, nb)) * 4.0
+    kap = inputs.shear_kappa(s, 1.0)
+    layers = [(np.zeros((16, 9)), np.zeros(16)), (np.zeros((16, 16)), np.zeros(16)),
+              (np.zeros((16, 16)), np.zeros(16)),
+              (np.zeros((9, 16)), np.linspace(-2.0, 3.0, 9))]
+    p1 = orc.params(nb, s, H=1.0, kBT=1.0, zeta=4.0, h=0.5, kappa=kap)
+    p0 = orc.params(nb, s, H=1.0, kBT=0.0, zeta=4.0, h=0.5, kappa=kap)
+    np.testing.assert_allclose(orc.score_rhs(P, Phi, p1, layers), orc.galerkin_rhs(P, Phi, p0),
+                               rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("nb,s,kBT", [(1, 3, 1.0), (3, 3, 1.0), (3, 3, 2.5)])
+def test_score_rhs_of_a_linear_score_is_a_negative_spring(orc, nb, s, kBT):
+    N, r, D = 500, 7, nb * s
+    Phi = _zero_mean_basis(N, s, r, seed=10 + nb)
+    P = np.random.default_rng(11).standard_normal((r, nb)) * 5.0
+    kap = inputs.shear_kappa(s, 0.7)
+    # s(x) = -x / kBT + c  =>  kBT (s - mean s) = -(q~ - mean q~) = -q~
+    layers = _affine_net(D, -1.0 / kBT, np.linspace(0.5, 1.5, D))
+    p_score = orc.params(nb, s, H=0.0, kBT=kBT, zeta=4.0, h=0.5, kappa=kap)
+    p_spring = orc.params(nb, s, H=-1.0, kBT=0.0, zeta=4.0, h=0.5, kappa=kap)
+    got = orc.score_rhs(P, Phi, p_score, layers)
+    want = orc.galerkin_rhs(P, Phi, p_spring)
+    np.testing.assert_allclose(got, want, rtol=1e-10, atol=1e-10 * np.abs(want).max())
+    # and the entropic part pushes outwards: with kBT > 0 the reduced state
+    # grows faster than without the score (the score of a centred cloud
+    # points inwards, the entropy force against it)
+    p_flow = orc.params(nb, s, H=0.0, kBT=0.0, zeta=4.0, h=0.5, kappa=kap)
+    assert np.sum(P * (got - orc.galerkin_rhs(P, Phi, p_flow))) > 0

@@ -20,6 +20,19 @@ def test_median_pair_distance_is_lower_median(orc, N, D):
     assert orc.median_bandwidth(q) == pytest.approx(d[(M - 1) // 2] / np.sqrt(2 * np.log(N)), rel=1e-15)
 
 
+@pytest.mark.parametrize("N,D,dup", [(57, 9, False), (64, 2, False), (200, 3, True), (2, 4, False)])
+def test_median_by_counting_equals_sorted_median(orc, N, D, dup):
+    # the bisection on pair counts must land on the very order statistic that
+    # sorting all pair distances (scipy pdist) gives, ties included
+    q = np.random.default_rng(N + 11).standard_normal((N, D))
+    if dup:
+        q[N // 2:] = q[:N - N // 2]
+    d = np.sort(pdist(q))
+    M = N * (N - 1) // 2
+    assert orc.median_pairdist_count(q) == d[(M - 1) // 2]
+    assert orc.median_bandwidth_count(q) == orc.median_bandwidth(q)
+
+
 def test_pair_counts_bracket_the_order_statistic(orc):
     q = np.random.default_rng(5).standard_normal((300, 9))
     med = orc.median_pairdist(q)
