@@ -152,12 +152,16 @@ VDS_API int vds_density_at(vds_ctx *ctx, const float *q, int N, int D, const vds
  * (q_star = NULL): E (host, may be NULL), g (device N x D, may be NULL) and
  * rho (device N, may be NULL) for the device array q (N x D), on the given
  * stream (a cudaStream_t of the current device; NULL = legacy default
- * stream), and synchronises that stream before returning.
+ * stream), and synchronises that stream before returning, also when it
+ * returns an error.
  *  - No context and no allocation: all scratch lives in one fixed-size static
  *    device array of the library (about 4.7 MiB, held by every GPU that loads
  *    the library until the process exits); the caller passes inputs and
  *    outputs only.
- *  - N must not exceed VDS_NOALLOC_MAX_N; larger N returns VDS_ESIZE.
+ *  - N must not exceed VDS_NOALLOC_MAX_N; larger N returns VDS_ESIZE.  Near
+ *    that limit the gradient pass runs on fewer CTAs than vds_energy_grad
+ *    uses (its partial sums must fit the fixed array), so it is slower there;
+ *    results agree within the library's FP32 tolerance.
  *  - The first call on each device looks up the array's device address with
  *    that device current (the call's one-time set-up); make that first call
  *    before any stream capture on the device.

@@ -36,8 +36,8 @@ def _sources():
 
 def _tag():
     h = hashlib.sha1()
-    for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-            os.path.join(ROOT, "include", "vds.h")]:
+    for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
+            glob.glob(os.path.join(ROOT, "include", "*.h"))):
         with open(p, "rb") as f:
             h.update(os.path.basename(p).encode())
             h.update(f.read())

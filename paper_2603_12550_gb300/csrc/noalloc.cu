@@ -12,8 +12,15 @@
 // device, with that device current, the entry point asks the runtime for the
 // array's device address (cudaGetSymbolAddress) and caches it per device.
 // Calls that overlap on the GPU share the array and race; the entry point
-// synchronises its stream before returning, so calls made one after another
-// from one thread do not overlap.
+// synchronises its stream before returning, on success and on every error
+// return, so calls made one after another from one thread do not overlap.
+//
+// Pass shapes follow vds_energy_grad's choice (small clouds take the
+// 128-thread, 64-record shape; mid-size clouds 64-record j-chunks when their
+// partial sums fit), except that a stream-K grid whose partial sums would not
+// fit the fixed buffer is cut down until they do: at N near
+// VDS_NOALLOC_MAX_N the gradient pass runs on fewer CTAs than the context
+// path (about a quarter of the SMs at D = 9), so it is slower there.
 #include <mutex>
 
 #include "pair_impl.cuh"
@@ -24,7 +31,7 @@ namespace {
 
 constexpr size_t kHeadBytes = 8192;  // err | tickets | scalars | reduction slots
 constexpr size_t kErrOff = 0, kTicketOff = 256, kScalOff = 512, kRedOff = 512 + SC_COUNT * 8;
-constexpr int kMaxDP = 20;           // Rec<16>::DP
+constexpr int kMaxDP = Rec<VDS_MAXD>::DP;  // widest record of any accepted D
 constexpr size_t kRecBytes =
     (size_t)((VDS_NOALLOC_MAX_N + vds_pair::TJ - 1) / vds_pair::TJ * vds_pair::TJ) * kMaxDP * sizeof(float);
 constexpr size_t kPartBytes = (size_t)4 << 20;
@@ -73,24 +80,29 @@ int setup_device(int dev, DevState **out) {
   return VDS_OK;
 }
 
-// One pair pass into the fixed partial buffer: the stream-K grid is shrunk
-// until the partial sums fit.
-template <int D, int RI, int NT, bool GRAD>
-int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double *part, int *err,
-            Sched &sc) {
+// Plans one pass shape's stream-K grid over the fixed partial buffer and
+// launches it.  With `shrink` the grid is cut by a quarter at a time until
+// the partial sums fit; without it a shape whose partials do not fit at the
+// full grid is declined (done = false, nothing launched).
+template <int D, int RI, int NT, bool GRAD, int TJK>
+int na_try(const DevState &s, int N, cudaStream_t st, const float *rec, double *part, int *err,
+           Sched &sc, bool shrink, bool &done) {
   using namespace vds_pair;
+  static_assert(Rec<D>::DP <= kMaxDP, "record area sized for the widest D");
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
   constexpr int TI = NT * RI;
-  const size_t smem = (size_t)NSTAGE * TJ * DP * sizeof(float);
+  const size_t smem = (size_t)NSTAGE * TJK * DP * sizeof(float);
+  done = false;
   int occ = 0;
-  VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<D, RI, NT, GRAD>, NT, smem));
+  VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD, TJK>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pair<D, RI, NT, GRAD, TJK>, NT, smem));
   if (occ < 1) occ = 1;
   sc.TI = TI;
   sc.Npad = (N + TJ - 1) / TJ * TJ;
   sc.Nipad = sc.Npad;
-  sc.nchunk = sc.Npad / TJ;
+  sc.nchunk = sc.Npad / TJK;
   sc.n_itiles = (N + TI - 1) / TI;
   sc.items = (long long)sc.n_itiles * sc.nchunk;
   long long G = (long long)s.num_sms * occ;
@@ -104,14 +116,36 @@ int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double 
       if (l - f + 1 > maxseg) maxseg = l - f + 1;
     }
     sc.maxseg = maxseg;
-    if ((size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double) <= kPartBytes || G == 1) break;
+    if ((size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double) <= kPartBytes) break;
+    if (!shrink) return VDS_OK;
+    if (G == 1) return VDS_ESIZE;
     G = G * 3 / 4;
     if (G < 1) G = 1;
   }
-  if ((size_t)sc.n_itiles * sc.maxseg * TI * ACC * sizeof(double) > kPartBytes) return VDS_ESIZE;
-  k_pair<D, RI, NT, GRAD><<<sc.G, NT, smem, st>>>(rec, rec, sc, part, err);
+  k_pair<D, RI, NT, GRAD, TJK><<<sc.G, NT, smem, st>>>(rec, rec, sc, part, err);
   VDS_CUDA_TRY(cudaGetLastError());
+  done = true;
   return VDS_OK;
+}
+
+// One pair pass, shaped as vds_energy_grad shapes it (small-cloud shape below
+// half the SMs' worth of items, 64-record j-chunks below 8 items per SM if
+// their partials fit, otherwise 256-record j-chunks).
+template <int D, bool GRAD>
+int na_pair(const DevState &s, int N, cudaStream_t st, const float *rec, double *part, int *err,
+            Sched &sc) {
+  using namespace vds_pair;
+  constexpr int RI = GRAD ? PairCfg<D>::RI_GRAD : PairCfg<D>::RI_DENS;
+  constexpr int NT = GRAD ? PairCfg<D>::NT_GRAD : PairCfg<D>::NT_DENS;
+  const long long items = (long long)((N + NT * RI - 1) / (NT * RI)) * ((N + TJ - 1) / TJ);
+  bool done = false;
+  if (2 * items < s.num_sms)
+    return na_try<D, RI_SMALL, NT_SMALL, GRAD, TJ_SMALL>(s, N, st, rec, part, err, sc, true, done);
+  if (items < 8LL * s.num_sms) {
+    VDS_TRY((na_try<D, RI, NT, GRAD, TJ_SMALL>(s, N, st, rec, part, err, sc, false, done)));
+    if (done) return VDS_OK;
+  }
+  return na_try<D, RI, NT, GRAD, TJ>(s, N, st, rec, part, err, sc, true, done);
 }
 
 template <int D>
@@ -132,13 +166,13 @@ int na_energy_grad(const DevState &s, const float *q, const KParams &kp, double 
   k_prep<D><<<(Npad + 255) / 256, 256, 0, st>>>(N, Npad, kp.c, q, nullptr, nullptr, 0.f, nullptr, rec);
   VDS_CUDA_TRY(cudaGetLastError());
   Sched sd, sg;
-  VDS_TRY((na_pair<D, PairCfg<D>::RI_DENS, PairCfg<D>::NT_DENS, false>(s, N, st, rec, part, err, sd)));
+  VDS_TRY((na_pair<D, false>(s, N, st, rec, part, err, sd)));
   const int nb = (N + NT_FIN - 1) / NT_FIN;
   k_dens_finish<D><<<nb, NT_FIN, 0, st>>>(sd, part, rec, rho, kp, E ? 1 : 0, q, nullptr, nullptr, nullptr,
                                          red, ticket + TK_DENS, scal, err);
   VDS_CUDA_TRY(cudaGetLastError());
   if (g) {
-    VDS_TRY((na_pair<D, PairCfg<D>::RI_GRAD, PairCfg<D>::NT_GRAD, true>(s, N, st, rec, part, err, sg)));
+    VDS_TRY((na_pair<D, true>(s, N, st, rec, part, err, sg)));
     k_grad_finish<D, GM_OUT><<<nb, NT_FIN, 0, st>>>(sg, part, rec, kp, g, q, nullptr, nullptr, nullptr,
                                                    nullptr, red, ticket + TK_GRAD, scal, err);
     VDS_CUDA_TRY(cudaGetLastError());
@@ -172,18 +206,23 @@ extern "C" int vds_energy_grad_noalloc(const float *q, int N, int D, const vds_p
   VDS_TRY(setup_device(dev, &s));
   const KParams kp = make_kparams(p, N, D);
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  int r = VDS_EARG;
   switch (D) {
-    case 2: return na_energy_grad<2>(*s, q, kp, E, g, rho, st);
-    case 3: return na_energy_grad<3>(*s, q, kp, E, g, rho, st);
-    case 4: return na_energy_grad<4>(*s, q, kp, E, g, rho, st);
-    case 6: return na_energy_grad<6>(*s, q, kp, E, g, rho, st);
-    case 8: return na_energy_grad<8>(*s, q, kp, E, g, rho, st);
-    case 9: return na_energy_grad<9>(*s, q, kp, E, g, rho, st);
-    case 10: return na_energy_grad<10>(*s, q, kp, E, g, rho, st);
-    case 12: return na_energy_grad<12>(*s, q, kp, E, g, rho, st);
-    case 14: return na_energy_grad<14>(*s, q, kp, E, g, rho, st);
-    case 15: return na_energy_grad<15>(*s, q, kp, E, g, rho, st);
-    case 16: return na_energy_grad<16>(*s, q, kp, E, g, rho, st);
+    case 2: r = na_energy_grad<2>(*s, q, kp, E, g, rho, st); break;
+    case 3: r = na_energy_grad<3>(*s, q, kp, E, g, rho, st); break;
+    case 4: r = na_energy_grad<4>(*s, q, kp, E, g, rho, st); break;
+    case 6: r = na_energy_grad<6>(*s, q, kp, E, g, rho, st); break;
+    case 8: r = na_energy_grad<8>(*s, q, kp, E, g, rho, st); break;
+    case 9: r = na_energy_grad<9>(*s, q, kp, E, g, rho, st); break;
+    case 10: r = na_energy_grad<10>(*s, q, kp, E, g, rho, st); break;
+    case 12: r = na_energy_grad<12>(*s, q, kp, E, g, rho, st); break;
+    case 14: r = na_energy_grad<14>(*s, q, kp, E, g, rho, st); break;
+    case 15: r = na_energy_grad<15>(*s, q, kp, E, g, rho, st); break;
+    case 16: r = na_energy_grad<16>(*s, q, kp, E, g, rho, st); break;
     default: return VDS_EARG;
   }
+  // An error after the first launch can leave kernels queued on the shared
+  // scratch: wait for them, so that the next call cannot race with them.
+  if (r != VDS_OK) (void)cudaStreamSynchronize(st);
+  return r;
 }
