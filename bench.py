@@ -46,7 +46,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
-    ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate,paper_tables",
+    ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate,paper_tables,surrogate_n262144",
                     help="comma-separated subset of the secondary measurements to run")
     return ap.parse_args()
 
@@ -401,12 +401,27 @@ def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
     rf_ms, rf_n, _ = ctx.vds_timing_read()
     ctx.vds_timing(False)
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
+    # the refresh pass against its CUDA-core floor: the kernel values Z_IK
+    # (2D + 1 FP32 lane-ops per ordered pair; the contraction Z B runs on the
+    # tensor cores) at SMs x 128 lanes x the measured maximum SM clock
+    peaks, src = _peaks()
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak_tops = nsm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    rf_t = rf_ms[3] / max(1, rf_n[3]) / 1e3
+    ops = float(N) * N * (2 * D + 1)
+    refresh_roof = {"bound": "alu", "kernel": "k_refresh_ta (X^B refresh, Z on CUDA cores, Z B on tensor cores)",
+                    "ops_per_pair": 2 * D + 1, "achieved": ops / rf_t / 1e12, "peak": peak_tops,
+                    "unit": "TOP/s (FP32 lane-ops)", "frac": ops / rf_t / 1e12 / peak_tops,
+                    "floor_ms": ops / (peak_tops * 1e12) * 1e3, "launch_ms": rf_t * 1e3,
+                    "peak_note": f"{nsm} SMs x 128 FP32 lanes x {src} sm_max_mhz; the time includes the "
+                                 "B-image and split-sum kernels of a refresh"}
     out = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
                   "build_phases_ms": {"gram": ph_ms[4], "eigensolve": ph_ms[5], "basis": ph_ms[6]},
                   "jacobi_sweeps": basis.sweeps(),
                   "eigenvalues_top": basis.eigenvalues()[:8].tolist(),
                   "mode2_steps_per_s": 240 / sec2, "mode2_refresh_every": 60,
                   "mode2_refresh_ms": rf_ms[3] / max(1, rf_n[3]), "mode2_refreshes": rf_n[3],
+                  "refresh_roofline": refresh_roof,
                   "mode1_galerkin_steps_per_s": 3 / sec3, "snapshot_run_s": snap_s}
     del X
     basis.free()
@@ -462,7 +477,61 @@ def _extra_batched(ctx, vds, inputs, torch, timed):
     return out
 
 
-def _extras_surrogate(ctx, vds, inputs, torch, wl, h, N=None, snaps_per_rate=21, snap_every=10, fit_every=1):
+ISO_LEVELS = (0.02, 0.03, 0.05, 0.10, 0.20)
+
+
+def _iso_error(ctx, vds, torch, timed, X, N, nb, s, D, p, kap, q0, q_ref, tau_ref, K, nets, r_energy, ranks):
+    """Points (method, rank, knob, steps/s, stress error of the lifted state
+    against the full-order run after K steps) and, per error level, the
+    fastest point of each method within it."""
+    pts = []
+    qt = torch.empty_like(q0)
+    for rk in sorted(set(int(x) for x in ranks(r_energy))):
+        basis, r_used = ctx.pod_build(X, N * s, X.shape[0], s, energy=0.9999, r_max=64, r_fixed=rk, kappa=kap)
+        P0 = torch.empty((r_used, nb), device="cuda")
+        ctx.pod_project(basis, q0, P0)
+
+        def err(P):
+            ctx.pod_lift(basis, P, qt)
+            tau, _ = ctx.vds_stress(qt, p)
+            return float(np.linalg.norm(tau - tau_ref) / np.linalg.norm(tau_ref))
+
+        def add(method, knob, fn):
+            P = P0.clone()
+            sec, extra = timed(lambda: fn(P))
+            pt = {"method": method, "rank": r_used, "knob": knob, "steps_per_s": K / sec, "stress_rel_err": err(P)}
+            if isinstance(extra, tuple):
+                pt["fallbacks"] = extra[1]
+            pts.append(pt)
+
+        add("galerkin_exact", None, lambda P: ctx.pod_step(basis, P, N, D, p, nsteps=K, mode=1))
+        for kf in (5, 20, 60):
+            add("frozen_mode2", {"refresh_every": kf},
+                lambda P, kf=kf: ctx.pod_step(basis, P, N, D, p, nsteps=K, refresh_every=kf, mode=2))
+        for name, net in nets.items():
+            for ce in (10, 40):
+                add(name, {"check_every": ce, "check_n": 4096, "check_tol": 0.5},
+                    lambda P, net=net, ce=ce: ctx.pod_step_score(basis, net, P, N, D, p, nsteps=K, check_every=ce,
+                                                                 check_n=4096, check_tol=0.5))
+        basis.free()
+    best = {}
+    for lv in ISO_LEVELS:
+        row = {}
+        for m in ["galerkin_exact", "frozen_mode2"] + list(nets):
+            ok = [x for x in pts if x["method"] == m and x["stress_rel_err"] <= lv]
+            row[m] = max(ok, key=lambda x: x["steps_per_s"]) if ok else None
+        for m in nets:
+            for ref in ("frozen_mode2", "galerkin_exact"):
+                if row[m] and row[ref]:
+                    row[f"{m}_over_{ref}"] = row[m]["steps_per_s"] / row[ref]["steps_per_s"]
+        best[f"{lv:g}"] = row
+    return {"points": pts, "best_within_error": best, "K": K,
+            "note": "stress error of the lifted state against the full-order run at the same time; ranks "
+                    "by r_fixed around the energy rule's rank; full order itself has zero error by definition"}
+
+
+def _extras_surrogate(ctx, vds, inputs, torch, wl, h, N=None, snaps_per_rate=21, snap_every=10, fit_every=1,
+                      iso_ranks=lambda r: (max(2, r - 3), r, r + 4)):
     """Learned score surrogate: trained by DSM (sigma = h) on VDS snapshots of
     the 4-bead chain at shear rates 0.5, 1, 2 (snaps_per_rate snapshots per
     rate, snap_every steps apart); run inside the reduced step at the held-out
@@ -576,6 +645,12 @@ def _extras_surrogate(ctx, vds, inputs, torch, wl, h, N=None, snaps_per_rate=21,
     e = final_err(P)
     res["surrogate_fit_exact_S"] = {"train_seconds": fit_s, "steps_per_s": K / sec, "stress_rel_err": e[0],
                                     "err_mor": e[1], "worst_check_rel_err": cerr, "fallbacks": nf}
+    # iso-error comparison: every reduced method's final stress error against
+    # its steps/s, over the POD rank and the method's own accuracy knob (the
+    # frozen step's refresh interval, the surrogate's check interval), and per
+    # error level the fastest configuration of each method that reaches it
+    res["iso_error"] = _iso_error(ctx, vds, torch, timed, X, N, nb, s, D, p, kap, q0, q, tau_ref, K,
+                                  {"surrogate_fit_exact_S": net2, "surrogate_dsm": net}, r, iso_ranks)
     # one network evaluation on all N particles (k_mlp_fwd, one launch), the
     # step's only O(N) tensor-core work: CUDA events over back-to-back calls
     xs, out = pool[:N], torch.empty((N, D), device="cuda")
@@ -604,7 +679,7 @@ def _extras_surrogate(ctx, vds, inputs, torch, wl, h, N=None, snaps_per_rate=21,
     for k in ("galerkin_exact", "surrogate", "surrogate_no_check", "frozen_mode2", "surrogate_fit_exact_S"):
         res[k]["time_fraction_of_full_order"] = full / res[k]["steps_per_s"]
     res["run"]["dof_fraction"] = r * nb / float(N * D)
-    res["paper_context"] = ("Sec. 3.2, 4-bead chain in shear, P=1000 and P=10000, R=20, CPU (i7-13700K): "
+    res["paper_context"] = ("Sec. 3.3, 4-bead chain in shear, P=1000 and P=10000, R=20, CPU (i7-13700K): "
                             "T_mor/T_ref 6.9 %, err_MOR 5.7-6.0 %, DoF about 0.1 %")
     res["train"]["fit_snapshots"] = int(pool_fit.shape[0] // N)
     res["run"]["N"] = N
@@ -752,15 +827,17 @@ def main():
         if "surrogate" in which:
             extras["surrogate"] = _extras_surrogate(ctx, vds, inputs, torch, wl, h)
         if "surrogate_n262144" in which:
-            # the surrogate workload at its own size (opt-in, minutes): N=262144,
-            # 2001 training snapshots (one per step, 667 per rate), median-rule h
-            # of its initial cloud, exact-S fit on every 10th snapshot
+            # the surrogate workload at its own size (about five minutes):
+            # N=262144, 2001 training snapshots (one per step, 667 per rate),
+            # median-rule h of its initial cloud, exact-S fit on every 10th
+            # snapshot; the iso-error sweep at two ranks
             N5 = 262144
             q5 = torch.from_numpy(inputs.equilibrium_cloud(N5, wl["nb"], wl["s"], H=wl["H"], seed=100)).cuda()
             h5 = ctx.vds_bandwidth(q5, 0)
             del q5
             extras["surrogate_n262144"] = _extras_surrogate(ctx, vds, inputs, torch, wl, h5, N=N5,
-                                                            snaps_per_rate=667, snap_every=1, fit_every=10)
+                                                            snaps_per_rate=667, snap_every=1, fit_every=10,
+                                                            iso_ranks=lambda r: (r, r + 4))
 
     cpu = None
     if not a.no_cpu_baseline:

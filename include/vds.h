@@ -142,6 +142,33 @@ VDS_API int vds_stress(vds_ctx *ctx, const float *q, int N, int D, const vds_par
 VDS_API int vds_density_at(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
                            const float *y, int M, float *f);
 
+/* Row-range evaluation: the pieces of one evaluation split over ranks by
+ * particle rows.  The paper's cost is the O(P^2) pair sums (Sec. 1.2, The
+ * VDS Scheme and its Limitation); each of G ranks takes a contiguous range
+ * of rows I against all N columns J, and two all-gathers per evaluation
+ * (q before the density pass, rho before the gradient pass) give every rank
+ * the whole state.  The library does the per-rank pair work; the exchange is
+ * the caller's (paper_2603_12550_gb300/shard.py uses torch.distributed).
+ *
+ * vds_density_rows: rho_rows[i] = sum_J exp(-|q_(row0+i) - q_J|^2 / 2h^2)
+ * (self term included) for i < nrows, from the device array q (N x D, all
+ * particles).  rho_rows: device, nrows FP32.
+ * vds_grad_rows: given rho (device, N FP32: the density of every particle),
+ * the gradient pass for the rows row0 .. row0+nrows-1, then
+ *   mode 0: out = kBT S + grad Psi of those rows (Eq. model_DymRepPar);
+ *   mode 1: out = their explicit Euler update q + dt [kappa q - (1/zeta)
+ *           (A (x) I) g] (Appendix A, explicit scheme);
+ * out: device nrows x D FP32 (must not overlap q).
+ * Both are asynchronous on the context stream; VDS_EARG for NULL pointers,
+ * nrows < 1, a range outside [0, N) or invalid parameters; VDS_ENAN (at the
+ * next synchronising call) for a non-finite density.  Row-range sums are
+ * split over CTAs differently from vds_energy_grad's, so results agree with
+ * it within FP32 rounding, not bit for bit. */
+VDS_API int vds_density_rows(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p, int row0,
+                             int nrows, float *rho_rows);
+VDS_API int vds_grad_rows(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p, const float *rho,
+                          int row0, int nrows, int mode, float *out);
+
 /* Allocation-free density and gradient evaluation.  The paper has no
  * counterpart; this entry point exists for callers that cannot allocate
  * device memory at the point of the call: a flow solver that couples one VDS

@@ -488,6 +488,30 @@ def velocity(q, p: OrParams):
     return v.reshape(N, D)
 
 
+def velocity_rows(q, p: OrParams, rho, rows):
+    """The particle velocity of Eq. model_DymRepPar for the particles in
+    ``rows`` only, given the density rho of all particles:
+    v_{k,I} = kappa q_{k,I} - (1/zeta) sum_j A_kj g_{I,j}, g = kBT S + grad Psi."""
+    q = np.asarray(q, dtype=np.float64)
+    rows = np.asarray(rows, dtype=np.int64)
+    s, nb = p.s, p.nb
+    g = p.kBT * entropy_grad_rows(q, p.h, rho, rows) + spring_grad(q[rows], p)
+    A = rouse(nb)
+    kap = np.array(p.kappa[:s * s]).reshape(s, s)
+    n = len(rows)
+    qb = q[rows].reshape(n, nb, s)
+    gb = g.reshape(n, nb, s)
+    v = np.einsum("ab,Ikb->Ika", kap, qb) - np.einsum("kj,Ija->Ika", A, gb) / p.zeta
+    return v.reshape(n, nb * s)
+
+
+def explicit_step_rows(q, p: OrParams, rho, rows):
+    """One explicit Euler step (Appendix A) of the particles in ``rows``,
+    given the density rho of all particles: q_I + dt v_I."""
+    q = np.asarray(q, dtype=np.float64)
+    return q[np.asarray(rows, dtype=np.int64)] + p.dt * velocity_rows(q, p, rho, rows)
+
+
 def score_rhs(P, Phi, p: OrParams, layers):
     """Reduced RHS with the learned score in place of the entropy gradient:
     Pdot = U^T [kappa q~ - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi)],

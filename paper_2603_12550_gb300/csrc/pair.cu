@@ -99,6 +99,29 @@ int vds_stress_16(vds_ctx *, const KParams &, const float *, double *, double *)
 int vds_flow_16(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_16(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 
+int vds_rowsdens_2(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_2(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_3(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_3(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_4(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_4(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_6(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_6(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_8(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_8(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_9(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_9(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_10(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_10(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_12(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_12(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_14(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_14(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_15(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_15(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+int vds_rowsdens_16(vds_ctx *, const KParams &, const float *, int, int, float *);
+int vds_rowsgrad_16(vds_ctx *, const KParams &, const float *, const float *, int, int, int, float *);
+
 KParams make_kparams(const vds_params *p, int N, int D) {
   KParams k;
   k.N = N;
@@ -157,6 +180,19 @@ int pass_flow(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
 
 int pass_density_at(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M, float *f_out) {
 #define CALL(DD) vds_query_##DD(c, kp, q, y, M, f_out)
+  VDS_DISPATCH_D(kp.D, CALL)
+#undef CALL
+}
+
+int pass_density_rows(vds_ctx *c, const KParams &kp, const float *q, int row0, int nrows, float *rho) {
+#define CALL(DD) vds_rowsdens_##DD(c, kp, q, row0, nrows, rho)
+  VDS_DISPATCH_D(kp.D, CALL)
+#undef CALL
+}
+
+int pass_grad_rows(vds_ctx *c, const KParams &kp, const float *q, const float *rho, int row0, int nrows,
+                   int mode, float *out) {
+#define CALL(DD) vds_rowsgrad_##DD(c, kp, q, rho, row0, nrows, mode, out)
   VDS_DISPATCH_D(kp.D, CALL)
 #undef CALL
 }

@@ -82,3 +82,10 @@ int pass_density_at(vds_ctx *c, const KParams &kp, const float *q, const float *
 int pass_axpy(vds_ctx *c, int n, const float *base, const float *delta, float *out);
 // qs = q + dt kappa q (per bond).
 int pass_flow(vds_ctx *c, const KParams &kp, const float *q, float *qs);
+
+// Row-range passes (rows row0 .. row0 + nrows - 1 against all N columns):
+// rho of the rows; and, given rho of all N particles, g of the rows (mode 0)
+// or their explicit Euler update (mode 1) into out (nrows x D).
+int pass_density_rows(vds_ctx *c, const KParams &kp, const float *q, int row0, int nrows, float *rho);
+int pass_grad_rows(vds_ctx *c, const KParams &kp, const float *q, const float *rho, int row0, int nrows,
+                   int mode, float *out);

@@ -762,6 +762,103 @@ int query_impl(vds_ctx *c, const KParams &kp, const float *q, const float *y, in
   return VDS_OK;
 }
 
+// ------------------------------------------------- row-range passes
+//
+// The pair passes restricted to the particles row0 .. row0 + nrows - 1 as
+// the rows I (all N particles as the columns J): the pieces of one
+// evaluation split over ranks by rows (each rank holds all of q, and all of
+// rho before its gradient pass).
+
+// w = 1/rho of every particle into its record, from a gathered rho array.
+template <int D>
+__global__ void k_set_w(int N, const float *__restrict__ rho, float *__restrict__ rec, int *err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float r = rho[i];
+  if (!(r >= 0.5f && r <= 3.0e38f)) vds_flag(err, VDS_ENAN);
+  rec[(size_t)i * Rec<D>::DP + D] = (float)(1.0 / (double)r);
+}
+
+// The records of nrows consecutive particles (src already offset to row0)
+// copied into their own array padded to Mpad rows, so a pass reads its i
+// records from a buffer whose padding rows are far away (kernel value 0).
+template <int D>
+__global__ void k_copy_rows(int nrows, int Mpad, const float *__restrict__ src, float *__restrict__ dst) {
+  constexpr int DP = Rec<D>::DP;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Mpad) return;
+  float4 *d = reinterpret_cast<float4 *>(dst + (size_t)i * DP);
+  if (i < nrows) {
+    const float4 *s = reinterpret_cast<const float4 *>(src + (size_t)i * DP);
+#pragma unroll
+    for (int v = 0; v < DP / 4; ++v) d[v] = s[v];
+  } else {
+    float o[DP];
+#pragma unroll
+    for (int a = 0; a < D; ++a) o[a] = VDS_PAD_COORD;
+#pragma unroll
+    for (int a = D; a < DP; ++a) o[a] = 0.f;
+#pragma unroll
+    for (int v = 0; v < DP / 4; ++v) d[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+  }
+}
+
+template <int D>
+int rows_records(vds_ctx *c, int row0, int nrows) {
+  const int Mpad = (nrows + TJ - 1) / TJ * TJ;
+  VDS_TRY(vds_ensure(c, c->recq, (size_t)Mpad * Rec<D>::DP * sizeof(float)));
+  k_copy_rows<D><<<(Mpad + 255) / 256, 256, 0, c->stream>>>(nrows, Mpad, (const float *)c->rec.ptr +
+                                                                             (size_t)row0 * Rec<D>::DP,
+                                                           (float *)c->recq.ptr);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+// rho of the rows (FP32) from the density pass over all N columns.
+template <int D>
+int rows_density_impl(vds_ctx *c, const KParams &kp, const float *q, int row0, int nrows, float *rho_rows) {
+  VDS_TRY(prep_impl<D>(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  VDS_TRY(rows_records<D>(c, row0, nrows));
+  Sched sc;
+  VDS_TRY((launch_pass<D, false>(c, kp.N, sc, nrows, (const float *)c->recq.ptr)));
+  k_query_finish<D><<<(nrows + NT_FIN - 1) / NT_FIN, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr,
+                                                                             nrows, 1.0, rho_rows, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
+// With rho of all N particles: the gradient pass for the rows, then either
+// g = kBT S + grad Psi of the rows (mode 0) or their explicit Euler update
+// (mode 1) into out (nrows x D).
+template <int D>
+int rows_grad_impl(vds_ctx *c, const KParams &kp, const float *q, const float *rho, int row0, int nrows,
+                   int mode, float *out) {
+  VDS_TRY(prep_impl<D>(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  k_set_w<D><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp.N, rho, (float *)c->rec.ptr, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  VDS_TRY(rows_records<D>(c, row0, nrows));
+  Sched sc;
+  VDS_TRY((launch_pass<D, true>(c, kp.N, sc, nrows, (const float *)c->recq.ptr)));
+  KParams kl = kp;
+  kl.N = nrows;
+  const int nb = (nrows + NT_FIN - 1) / NT_FIN;
+  const double *pp = (const double *)c->part.ptr;
+  float *rq = (float *)c->recq.ptr;
+  const float *y = q + (size_t)row0 * D;
+  if (mode == 0)
+    k_grad_finish<D, GM_OUT><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rq, kl, out, y, nullptr, nullptr, nullptr,
+                                                          nullptr, nullptr, nullptr, c->scal, c->err);
+  else
+    k_grad_finish<D, GM_EXPLICIT><<<nb, NT_FIN, 0, c->stream>>>(sc, pp, rq, kl, nullptr, y, nullptr, nullptr,
+                                                               nullptr, out, nullptr, nullptr, c->scal, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
 template <int D>
 int stress_impl(vds_ctx *c, const KParams &kp, const float *q, double *tau, double *qq) {
   const int ne = kp.s * kp.s + D * D;
@@ -816,4 +913,12 @@ int flow_impl(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
   int vds_query_##DD(vds_ctx *c, const KParams &kp, const float *q, const float *y, int M,     \
                      float *f) {                                                              \
     return vds_pair::query_impl<DD>(c, kp, q, y, M, f);                                       \
+  }                                                                                           \
+  int vds_rowsdens_##DD(vds_ctx *c, const KParams &kp, const float *q, int row0, int nrows,    \
+                        float *rho) {                                                         \
+    return vds_pair::rows_density_impl<DD>(c, kp, q, row0, nrows, rho);                       \
+  }                                                                                           \
+  int vds_rowsgrad_##DD(vds_ctx *c, const KParams &kp, const float *q, const float *rho,       \
+                        int row0, int nrows, int mode, float *out) {                          \
+    return vds_pair::rows_grad_impl<DD>(c, kp, q, rho, row0, nrows, mode, out);               \
   }

@@ -51,24 +51,22 @@ constexpr int RC_SEG = 16;   // chunks per FP32 accumulator segment (512 K)
 constexpr int RC_FLUSH = 7;  // chunk of the next segment at which a segment is flushed
 constexpr int RC_ZOP = RC_M * RC_KC * 4;  // bytes of one Z operand tile (16 KB)
 
-// Shared memory: NZ slots of [Z hi | Z lo | B hi | B lo | records] (no Z
-// tiles when Z goes to tensor memory, TA); the epilogue reuses it for the
+// Shared memory of the wide-B kernel (2 s r + 1 > 64): NZ slots of
+// [Z hi | Z lo | B hi | B lo | records]; the epilogue reuses it for the
 // per-particle totals.
 template <int D, int NCP>
 struct RcLayout {
   static constexpr int DP = Rec<D>::DP;
-  static constexpr bool TA = NCP <= 64;                  // Z tiles in tensor memory
   static constexpr int BOP = NCP * RC_KC * 4;            // one B operand tile
-  // records of one chunk as staged: interleaved by particle pairs (TA) or
-  // with every coordinate duplicated (shared-memory Z path), so that a
-  // 64-bit shared load is a ready f32x2 operand either way
-  static constexpr int REC_BYTES = RC_KC * DP * 4 * (TA ? 1 : 2);
+  // records of one chunk as staged, every coordinate duplicated, so that a
+  // 64-bit shared load is a ready f32x2 operand against a pair of rows
+  static constexpr int REC_BYTES = RC_KC * DP * 4 * 2;
   static constexpr int REC = ((REC_BYTES + 127) / 128) * 128;
-  static constexpr int ZB = TA ? 0 : 2 * RC_ZOP;         // Z tiles of a slot
+  static constexpr int ZB = 2 * RC_ZOP;                  // Z tiles of a slot
   static constexpr int BOFF = ZB;                        // B hi, then B lo
   static constexpr int ROFF = ZB + 2 * BOP;              // records
   static constexpr int SLOT = ((ZB + 2 * BOP + REC + 1023) / 1024) * 1024;
-  static constexpr int NZ = TA ? 4 : ((216 * 1024 / SLOT) < 4 ? (216 * 1024 / SLOT) : 4);
+  static constexpr int NZ = (216 * 1024 / SLOT) < 4 ? (216 * 1024 / SLOT) : 4;
   static constexpr int TOT_LD = NCP + 1;                 // epilogue row stride (floats)
   static constexpr size_t RING = (size_t)NZ * SLOT;
   static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
@@ -170,6 +168,46 @@ __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile
   }
 }
 
+// Epilogue of a refresh CTA: the Z-forming threads' totals (row 32 (warp %
+// 4) + lane, column quarter warp / 4) through shared memory, then U1, U2 per
+// (I, a, t), or this K split's totals into part (summed over the splits by
+// k_rc_fin).
+template <int D, int NCP, int QC>
+__device__ __forceinline__ void rc_epilogue(uint8_t *sm, int tot_ld, const float (&tot)[QC], int tid, int warp,
+                                            int lane, int i0, int cb, int N, const float *__restrict__ rec,
+                                            const float *__restrict__ phi, int ld, int r, int s, int rr,
+                                            float *__restrict__ U1, float *__restrict__ U2,
+                                            float *__restrict__ part) {
+  constexpr int DP = Rec<D>::DP;
+  float *T = reinterpret_cast<float *>(sm);
+  if (tid < RC_PT) {
+    const int il = (warp & 3) * 32 + lane, cq = warp >> 2;
+#pragma unroll
+    for (int j = 0; j < QC; ++j) T[il * tot_ld + cq * QC + j] = tot[j];
+  }
+  __syncthreads();
+  if (part) {
+    float *dst = part + (((size_t)cb * gridDim.x + blockIdx.x) * RC_M) * NCP;
+    for (int e = tid; e < RC_M * NCP; e += RC_NT) dst[e] = T[(e / NCP) * tot_ld + e % NCP];
+    return;
+  }
+  const int t0 = cb * rr;
+  const int rc = min(rr, r - t0);
+  const int per = s * rc;
+  for (int e = tid; e < RC_M * per; e += RC_NT) {
+    const int row = e / per, rem = e - row * per;
+    const int a = rem / rc, u = rem - a * rc;
+    const int I = i0 + row;
+    if (I >= N) continue;
+    const float *Tr = T + row * tot_ld;
+    const float wI = rec[(size_t)I * DP + D];
+    const size_t o = ((size_t)I * s + a) * ld + t0 + u;
+    const float f = phi[o];
+    U1[o] = f - Tr[a * rc + u] * wI;
+    U2[o] = Tr[2 * per] * f - Tr[per + a * rc + u];
+  }
+}
+
 // Synchronisation per ring slot z (chunk ch uses slot ch % NZ; counts are
 // completions, u = ch / NZ):
 //   full[z]   bulk-copy bytes of records + B of chunk ch (completion u);
@@ -193,11 +231,8 @@ __global__ void __launch_bounds__(RC_NT, 1)
   // accumulator are added at the flush.  NCP = 256: three MMAs of N = NCP.
   constexpr bool FB = NCP <= 128;
   constexpr int ACW = FB ? 2 * NCP : NCP;  // accumulator columns per buffer
-  // NCP <= 64 (TA): Z goes to tensor memory (tcgen05.st) and is the MMAs' A
-  // operand there, slot z at columns 2 ACW + 64 z (hi) and + 32 (lo); shared
-  // memory then carries only B and the records
-  constexpr bool TA = L::TA;
-  constexpr int TCOLS = TA ? 512 : 2 * ACW;
+  static_assert(NCP >= 128, "narrower B slices run k_refresh_ta");
+  constexpr int TCOLS = 2 * ACW;
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t full[NZ], zready[NZ], sfree[NZ], segdone[2], accfree[2], fin;
   __shared__ uint32_t s_tmem;
@@ -276,16 +311,12 @@ __global__ void __launch_bounds__(RC_NT, 1)
         tc_fence_after();
         const uint32_t zh = sbase + (uint32_t)(z * L::SLOT), zl = zh + RC_ZOP;
         const uint32_t b_hi = zh + L::BOFF, b_lo = b_hi + L::BOP;
-        const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * z);  // TA: Z hi columns, lo at + 32
         const uint32_t acc = tmem + (uint32_t)(b * ACW);
 #pragma unroll
         for (int k = 0; k < RC_KC / 8; ++k) {
           const uint32_t o = (uint32_t)k * 256u;
           const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
-          if constexpr (TA) {
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, 1);
-          } else if constexpr (FB) {
+          if constexpr (FB) {
             // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
             tc_mma_tf32(acc, tc_sdesc(zh + o), tc_sdesc(b_hi + o), idesc2, first);
             tc_mma_tf32(acc, tc_sdesc(zl + o), tc_sdesc(b_hi + o), idesc, 1);
@@ -302,33 +333,26 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
   } else {
     // ---------------------------------------------------- Z formation
-    // TA: thread = row 32 (warp % 4) + lane (its tensor-memory lane), the 8 K
-    // of quarter warp / 4 of each chunk.  Otherwise rows rg + 32 (2 mh + m)
-    // (m < 2) and the 4 K of k-group jg of each chunk; element (row i, k) of
-    // a shared-memory Z tile at (i/8)*1024 + (k/4)*128 + (i%8)*16 + (k%4)*4,
-    // so a row's 4 K of one k-group are one float4
-    constexpr int RPT = TA ? 1 : 2;  // rows per thread
+    // rows rg + 32 (2 mh + m) (m < 2) and the 4 K of k-group jg of each
+    // chunk; element (row i, k) of a shared-memory Z tile at (i/8)*1024 +
+    // (k/4)*128 + (i%8)*16 + (k%4)*4, so a row's 4 K of one k-group are one
+    // float4
+    constexpr int RPT = 2;  // rows per thread
     const int rg = lane, jg = warp & 7, mh = warp >> 3;
-    const int q4 = warp & 3, cq = warp >> 2;  // flush (and TA rows): TMEM lanes 32 q4 .., column quarter cq
+    const int q4 = warp & 3, cq = warp >> 2;  // flush: TMEM lanes 32 q4 .., column quarter cq
     float xi[RPT][D];
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
-      const int i = min(i0 + (TA ? 32 * q4 + lane : rg + 32 * (2 * mh + m)), Npad - 1);
+      const int i = min(i0 + rg + 32 * (2 * mh + m), Npad - 1);
 #pragma unroll
       for (int d = 0; d < D; ++d) xi[m][d] = rec[(size_t)i * DP + d];
     }
 #pragma unroll
     for (int j = 0; j < QC; ++j) tot[j] = 0.f;
-    // TA: the row's coordinates duplicated in both halves; otherwise the two
-    // rows of the thread side by side
-    unsigned long long xi2[D], xi2r[D];
-    if constexpr (TA) {
+    // the two rows of the thread side by side
+    unsigned long long xi2r[D];
 #pragma unroll
-      for (int d = 0; d < D; ++d) xi2[d] = f2_pack(xi[0][d], xi[0][d]);
-    } else {
-#pragma unroll
-      for (int d = 0; d < D; ++d) xi2r[d] = f2_pack(xi[0][d], xi[RPT - 1][d]);
-    }
+    for (int d = 0; d < D; ++d) xi2r[d] = f2_pack(xi[0][d], xi[RPT - 1][d]);
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
@@ -351,70 +375,7 @@ __global__ void __launch_bounds__(RC_NT, 1)
       return true;
     };
     int flushed = 0;  // segments added into registers
-    // Z of one chunk (TA) for this thread's row and 8 K, two K per f32x2
-    // instruction: the squared distances to records u and u + 1 in the two
-    // halves of a packed register
-    auto z_chunk = [&](const uint8_t *slot, uint32_t (&hv)[8], uint32_t (&lv)[8]) {
-      // records interleaved by pairs: coordinate d of particles u and u + 1
-      // is one 64-bit word
-      const unsigned long long *rs =
-          reinterpret_cast<const unsigned long long *>(slot + L::ROFF) + cq * 4 * DP;
-#pragma unroll
-      for (int u = 0; u < 8; u += 2) {
-        unsigned long long r2 = f2_pack(0.f, 0.f);
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const unsigned long long dd = f2_sub(xi2[d], rs[(u / 2) * DP + d]);
-          r2 = f2_fma(dd, dd, r2);
-        }
-        float r2a, r2b;
-        f2_unpack(r2, r2a, r2b);
-        const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
-        const float ha = to_tf32(za), hb = to_tf32(zb);
-        hv[u] = __float_as_uint(ha);
-        hv[u + 1] = __float_as_uint(hb);
-        // the low parts stay unrounded: the MMA reads only their TF32 bits
-        // (the dropped bits are below 2^-21 of Z; the X^B errors against the
-        // FP64 oracle did not change in their first three digits)
-        float la, lb;
-        f2_unpack(f2_sub(f2_pack(za, zb), f2_pack(ha, hb)), la, lb);
-        lv[u] = __float_as_uint(la);
-        lv[u + 1] = __float_as_uint(lb);
-      }
-    };
-    if constexpr (TA) {
-      // two chunks per pass (nch is a multiple of the 16-chunk segment, so
-      // even): twice the independent work between the waits and stores
-      for (int ch = 0; ch < nch && ok; ch += 2) {
-        const int z0 = ch % NZ, z1 = (ch + 1) % NZ;
-        if (!__all_sync(0xffffffffu, rc_wait(&full[z0], (uint32_t)((ch / NZ) & 1), abort) &&
-                                         rc_wait(&full[z1], (uint32_t)(((ch + 1) / NZ) & 1), abort))) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();  // the MMAs that read these Z slots have completed
-        uint32_t hv0[8], lv0[8], hv1[8], lv1[8];
-        z_chunk(sm + (size_t)z0 * L::SLOT, hv0, lv0);
-        z_chunk(sm + (size_t)z1 * L::SLOT, hv1, lv1);
-        const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 8 * cq);
-        tc_st8(zt + (uint32_t)(64 * z0), hv0);
-        tc_st8(zt + (uint32_t)(64 * z0 + 32), lv0);
-        tc_st8(zt + (uint32_t)(64 * z1), hv1);
-        tc_st8(zt + (uint32_t)(64 * z1 + 32), lv1);
-        tc_wait_st();
-        tc_fence_before();
-        mbar_arrive(&zready[z0]);
-        mbar_arrive(&zready[z1]);
-        // segment g - 1 is added into registers part-way through segment g
-        if ((ch + 1) % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
-          if (!flush(ch / RC_SEG - 1)) {
-            ok = false;
-            break;
-          }
-          ++flushed;
-        }
-      }
-    } else {
+    {
       for (int ch = 0; ch < nch && ok; ++ch) {
         const int z = ch % NZ;
         if (!__all_sync(0xffffffffu, rc_wait(&full[z], (uint32_t)((ch / NZ) & 1), abort))) {
@@ -486,35 +447,279 @@ __global__ void __launch_bounds__(RC_NT, 1)
   tc_fence_after();
   if (warp == 0) tc_dealloc(tmem, TCOLS);
   if (*abort) return;
-  // epilogue: totals through shared memory, then U1, U2 per (I, a, t), or
-  // this split's totals into part (summed over the splits by k_rc_fin)
-  float *T = reinterpret_cast<float *>(sm);
-  if (tid < RC_PT) {
-    const int il = (warp & 3) * 32 + lane, cq = warp >> 2;
-#pragma unroll
-    for (int j = 0; j < QC; ++j) T[il * L::TOT_LD + cq * QC + j] = tot[j];
+  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part);
+}
+
+// ------------------------------------------------ Z in tensor memory (NCP <= 64)
+//
+// The same contraction with Z in tensor memory and the staging decoupled
+// from it: shared memory holds NS2 pair slots, each the B images of two
+// consecutive 32-particle chunks (one 32 KB bulk copy at NCP = 64) and their
+// 64 records (one copy), each with its own mbarrier, so the Z-forming warps
+// wait only for the records and the tensor cores only for B; tensor memory
+// holds two pair slots of Z (4 chunks).  The copies run up to NS2 pairs of
+// chunks ahead of the tensor cores, the Z-forming warps up to two.
+//
+// Barriers (pass c2 = chunks 2 c2 and 2 c2 + 1; pair slot j = c2 % NS2,
+// completion u = c2 / NS2; Z pair zp = c2 & 1, completion c2 >> 1):
+//   rfull[j]  bulk-copy bytes of the pass's records;
+//   bfull[j]  bulk-copy bytes of the pass's B images;
+//   sfree[j]  tcgen05.commit after the pass's MMAs (slot j may be refilled);
+//   zready[zp] one arrival per Z-forming warp: Z of the pass stored;
+//   zfree[zp]  tcgen05.commit after the pass's MMAs (Z pair may be rewritten);
+//   segdone[b], accfree[b] as in k_refresh_tc (accfree: one per warp).
+template <int D, int NCP>
+struct TaLayout {
+  static constexpr int DP = Rec<D>::DP;
+  static constexpr int BOP = NCP * RC_KC * 4;        // one B operand tile
+  static constexpr int BCH = 2 * BOP;                // B hi + lo of one chunk
+  static constexpr int REC_BYTES = RC_KC * DP * 4;   // one chunk's records
+  static constexpr int ROFF = 2 * BCH;               // records of the pair
+  static constexpr int SLOT = ((2 * BCH + 2 * REC_BYTES + 1023) / 1024) * 1024;
+  static constexpr int NS2 = (200 * 1024 / SLOT) < 8 ? (200 * 1024 / SLOT) : 8;
+  static constexpr int TOT_LD = NCP + 1;
+  static constexpr size_t RING = (size_t)NS2 * SLOT;
+  static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
+  static_assert(NCP <= 64, "Z in tensor memory needs 2 s r + 1 <= 64");
+  static_assert(NS2 >= 2, "refresh ring depth");
+  static_assert(SMEM <= 227 * 1024 - 1024, "refresh shared memory");
+};
+
+template <int D, int NCP>
+__global__ void __launch_bounds__(RC_NT, 1)
+    k_refresh_ta(const float *__restrict__ rec, const float *__restrict__ recs, int N, int Npad,
+                 const float *__restrict__ bimg,
+                 const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
+                 float *__restrict__ U2, int nsplit, float *__restrict__ part, int *err) {
+  using L = TaLayout<D, NCP>;
+  constexpr int DP = L::DP;
+  constexpr int NS2 = L::NS2;
+  constexpr int QC = NCP / 4;           // accumulator columns per thread in a flush
+  constexpr int ACW = 2 * NCP;          // Z_hi against [B_hi; B_lo]: N = 2 NCP
+  constexpr int TCOLS = 512;            // 2 ACW accumulator columns + 4 Z slots of 64
+  static_assert(2 * ACW + 4 * 64 <= TCOLS, "tensor memory columns");
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t rfull[NS2], bfull[NS2], sfree[NS2], zready[2], zfree[2], segdone[2],
+      accfree[2], fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+  const int i0 = tile * RC_M;
+  const int cb = blockIdx.y;
+  const int nch_all = Npad / RC_KC, nseg_all = (nch_all + RC_SEG - 1) / RC_SEG;
+  const int sg0 = split * nseg_all / nsplit, sg1 = (split + 1) * nseg_all / nsplit;
+  const int c0 = sg0 * RC_SEG;                       // first chunk of this CTA
+  const int nch = min(sg1 * RC_SEG, nch_all) - c0;   // a multiple of 8: Npad is of 256
+  const int npass = nch / 2;
+  const int nseg = sg1 - sg0;
+  volatile int *abort = &s_abort;
+  if (warp == 0) tc_alloc(&s_tmem, TCOLS);
+  if (tid == 0) {
+    for (int j = 0; j < NS2; ++j) {
+      mbar_init(&rfull[j], 1);
+      mbar_init(&bfull[j], 1);
+      mbar_init(&sfree[j], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&zready[b], RC_PW);
+      mbar_init(&zfree[b], 1);
+      mbar_init(&segdone[b], 1);
+      mbar_init(&accfree[b], RC_PW);
+    }
+    mbar_init(&fin, 1);
+    s_abort = 0;
+    fence_mbar_init();
   }
+  tc_fence_before();
   __syncthreads();
-  if (part) {
-    float *dst = part + (((size_t)cb * gridDim.x + blockIdx.x) * RC_M) * NCP;
-    for (int e = tid; e < RC_M * NCP; e += RC_NT) dst[e] = T[(e / NCP) * L::TOT_LD + e % NCP];
-    return;
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = smem_u32(sm);
+  float tot[QC];
+  bool ok = true;
+
+  if (warp == RC_PW) {
+    // ---------------------------------------------------- bulk copies
+    if (lane == 0) {
+      const uint8_t *bsrc = reinterpret_cast<const uint8_t *>(bimg) + ((size_t)cb * nch_all + c0) * L::BCH;
+      const uint8_t *rsrc = reinterpret_cast<const uint8_t *>(recs) + (size_t)c0 * L::REC_BYTES;
+      int c2 = 0;
+      for (; c2 < npass; ++c2) {
+        const int j = c2 % NS2;
+        if (c2 >= NS2 && !rc_wait(&sfree[j], (uint32_t)((c2 / NS2 - 1) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        uint8_t *slot = sm + (size_t)j * L::SLOT;
+        // records first: the Z-forming warps wait for them only
+        mbar_arrive_expect_tx(&rfull[j], (uint32_t)(2 * L::REC_BYTES));
+        bulk_g2s(slot + L::ROFF, rsrc + (size_t)(2 * c2) * L::REC_BYTES, 2 * L::REC_BYTES, &rfull[j]);
+        mbar_arrive_expect_tx(&bfull[j], (uint32_t)(2 * L::BCH));
+        bulk_g2s(slot, bsrc + (size_t)(2 * c2) * L::BCH, 2 * L::BCH, &bfull[j]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      // the copies still in flight land before the CTA may exit
+      for (int k = c2 > NS2 ? c2 - NS2 : 0; k < c2; ++k) {
+        mbar_wait_bounded(&rfull[k % NS2], (uint32_t)((k / NS2) & 1), VDS_WAIT_LIMIT_NS);
+        mbar_wait_bounded(&bfull[k % NS2], (uint32_t)((k / NS2) & 1), VDS_WAIT_LIMIT_NS);
+      }
+    }
+  } else if (warp == RC_PW + 1) {
+    // ---------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP), idesc2 = tc_idesc(TC_FMT_TF32, RC_M, ACW);
+      for (int c2 = 0; c2 < npass && ok; ++c2) {
+        const int j = c2 % NS2, zp = c2 & 1;
+        if (!rc_wait(&zready[zp], (uint32_t)((c2 >> 1) & 1), abort) ||
+            !rc_wait(&bfull[j], (uint32_t)((c2 / NS2) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int e = 0; e < 2 && ok; ++e) {
+          const int ch = 2 * c2 + e, g = ch / RC_SEG, b = g & 1;
+          if (ch % RC_SEG == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t b_hi = sbase + (uint32_t)(j * L::SLOT + e * L::BCH);
+          const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * (2 * zp + e));  // Z hi; lo at + 32
+          const uint32_t acc = tmem + (uint32_t)(b * ACW);
+#pragma unroll
+          for (int k = 0; k < RC_KC / 8; ++k) {
+            const uint32_t o = (uint32_t)k * 256u;
+            const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
+            // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, 1);
+          }
+          if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
+        }
+        tc_commit(&sfree[j]);
+        tc_commit(&zfree[zp]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      // every MMA this thread issued has completed before the tensor memory
+      // and shared memory are released (also after an abort)
+      tc_commit(&fin);
+      mbar_wait_bounded(&fin, 0, VDS_WAIT_LIMIT_NS);
+    }
+  } else {
+    // ---------------------------------------------------- Z formation
+    // thread = row 32 (warp % 4) + lane (its tensor-memory lane), the 8 K of
+    // quarter warp / 4 of each chunk
+    const int q4 = warp & 3, cq = warp >> 2;
+    float xi[D];
+    {
+      const int i = min(i0 + 32 * q4 + lane, Npad - 1);
+#pragma unroll
+      for (int d = 0; d < D; ++d) xi[d] = rec[(size_t)i * DP + d];
+    }
+#pragma unroll
+    for (int j = 0; j < QC; ++j) tot[j] = 0.f;
+    unsigned long long xi2[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) xi2[d] = f2_pack(xi[d], xi[d]);
+    auto flush = [&](int g) -> bool {
+      const int b = g & 1;
+      if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
+      tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * ACW + cq * QC);
+      // the two halves of the accumulator (Z_hi B_hi + Z_lo B_hi, Z_hi B_lo)
+      if constexpr (QC == 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld16(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[j] += __uint_as_float(v[j]);
+        }
+      } else {
+        static_assert(QC == 8, "accumulator columns per thread");
+        uint32_t v[8];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld8(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tot[j] += __uint_as_float(v[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[b]);
+      return true;
+    };
+    int flushed = 0;  // segments added into registers
+    // Z of one chunk for this thread's row and 8 K, two K per f32x2
+    // instruction: the squared distances to records u and u + 1 in the two
+    // halves of a packed register (records interleaved by particle pairs)
+    auto z_chunk = [&](const uint8_t *recs_ch, uint32_t (&hv)[8], uint32_t (&lv)[8]) {
+      const unsigned long long *rs = reinterpret_cast<const unsigned long long *>(recs_ch) + cq * 4 * DP;
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        unsigned long long r2 = f2_pack(0.f, 0.f);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const unsigned long long dd = f2_sub(xi2[d], rs[(u / 2) * DP + d]);
+          r2 = f2_fma(dd, dd, r2);
+        }
+        float r2a, r2b;
+        f2_unpack(r2, r2a, r2b);
+        const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
+        const float ha = to_tf32(za), hb = to_tf32(zb);
+        hv[u] = __float_as_uint(ha);
+        hv[u + 1] = __float_as_uint(hb);
+        // the low parts stay unrounded: the MMA reads only their TF32 bits
+        float la, lb;
+        f2_unpack(f2_sub(f2_pack(za, zb), f2_pack(ha, hb)), la, lb);
+        lv[u] = __float_as_uint(la);
+        lv[u + 1] = __float_as_uint(lb);
+      }
+    };
+    for (int c2 = 0; c2 < npass && ok; ++c2) {
+      const int j = c2 % NS2, zp = c2 & 1;
+      if (!__all_sync(0xffffffffu, rc_wait(&rfull[j], (uint32_t)((c2 / NS2) & 1), abort) &&
+                                       (c2 < 2 || rc_wait(&zfree[zp], (uint32_t)(((c2 >> 1) - 1) & 1), abort)))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();  // the MMAs that read this Z pair have completed
+      const uint8_t *rp = sm + (size_t)j * L::SLOT + L::ROFF;
+      uint32_t hv0[8], lv0[8], hv1[8], lv1[8];
+      z_chunk(rp, hv0, lv0);
+      z_chunk(rp + L::REC_BYTES, hv1, lv1);
+      const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 128 * zp + 8 * cq);
+      tc_st8(zt, hv0);
+      tc_st8(zt + 32u, lv0);
+      tc_st8(zt + 64u, hv1);
+      tc_st8(zt + 96u, lv1);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&zready[zp]);
+      // segment g - 1 is added into registers part-way through segment g
+      const int ch = 2 * c2;
+      if ((ch + 1) % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
+        if (!flush(ch / RC_SEG - 1)) {
+          ok = false;
+          break;
+        }
+        ++flushed;
+      }
+    }
+    for (; ok && flushed < nseg; ++flushed)
+      if (!flush(flushed)) ok = false;
+    if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
   }
-  const int t0 = cb * rr;
-  const int rc = min(rr, r - t0);
-  const int per = s * rc;
-  for (int e = tid; e < RC_M * per; e += RC_NT) {
-    const int row = e / per, rem = e - row * per;
-    const int a = rem / rc, u = rem - a * rc;
-    const int I = i0 + row;
-    if (I >= N) continue;
-    const float *Tr = T + row * L::TOT_LD;
-    const float wI = rec[(size_t)I * DP + D];
-    const size_t o = ((size_t)I * s + a) * ld + t0 + u;
-    const float f = phi[o];
-    U1[o] = f - Tr[a * rc + u] * wI;
-    U2[o] = Tr[2 * per] * f - Tr[per + a * rc + u];
-  }
+  // every role has left its loop (the MMA issuer after its MMAs completed,
+  // the copy issuer after its copies landed)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, TCOLS);
+  if (*abort) return;
+  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part);
 }
 
 // U1, U2 from the totals of the nsplit K splits of every row tile, summed in
@@ -548,14 +753,24 @@ __global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, in
 template <int D, int NCP>
 int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
                    const float *recs, int nsplit, float *part, float *U1, float *U2) {
-  using L = RcLayout<D, NCP>;
-  VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)L::SMEM));
   const int ntiles = (N + RC_M - 1) / RC_M;
   dim3 grid(ntiles * nsplit, ncb);
-  k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recs, N, Npad, bimg, b->phi,
-                                                             b->ld, b->r, b->s, rr, U1, U2, nsplit,
-                                                             nsplit > 1 ? part : nullptr, c->err);
+  float *pp = nsplit > 1 ? part : nullptr;
+  if constexpr (NCP <= 64) {
+    using L = TaLayout<D, NCP>;
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_ta<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)L::SMEM));
+    k_refresh_ta<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recs, N, Npad, bimg,
+                                                               b->phi, b->ld, b->r, b->s, rr, U1, U2, nsplit, pp,
+                                                               c->err);
+  } else {
+    using L = RcLayout<D, NCP>;
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_tc<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)L::SMEM));
+    k_refresh_tc<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, recs, N, Npad, bimg,
+                                                               b->phi, b->ld, b->r, b->s, rr, U1, U2, nsplit, pp,
+                                                               c->err);
+  }
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   if (nsplit > 1) {

@@ -239,6 +239,29 @@ int vds_energy_grad(vds_ctx *c, const float *q, int N, int D, const vds_params *
   return VDS_OK;
 }
 
+int vds_density_rows(vds_ctx *c, const float *q, int N, int D, const vds_params *p, int row0, int nrows,
+                     float *rho_rows) {
+  if (!c || !q || !rho_rows || row0 < 0 || nrows < 1) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  if ((long)row0 + nrows > N) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  VDS_TRY(pass_density_rows(c, kp, q, row0, nrows, rho_rows));
+  return VDS_OK;
+}
+
+int vds_grad_rows(vds_ctx *c, const float *q, int N, int D, const vds_params *p, const float *rho, int row0,
+                  int nrows, int mode, float *out) {
+  if (!c || !q || !rho || !out || row0 < 0 || nrows < 1 || (mode != 0 && mode != 1)) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  if ((long)row0 + nrows > N) return VDS_EARG;
+  if (mode == 1 && !(p->dt > 0.0)) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  VDS_TRY(pass_grad_rows(c, kp, q, rho, row0, nrows, mode, out));
+  return VDS_OK;
+}
+
 int vds_density_at(vds_ctx *c, const float *q, int N, int D, const vds_params *p, const float *y, int M,
                    float *f) {
   if (!c || !q || !y || !f || M < 1) return VDS_EARG;

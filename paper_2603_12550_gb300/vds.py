@@ -79,6 +79,8 @@ _SIGS = {
     "vds_step": ([_vp, _vp, _i, _i, _pp, _i, _ip], _i),
     "vds_stress": ([_vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "vds_density_at": ([_vp, _vp, _i, _i, _pp, _vp, _i, _vp], _i),
+    "vds_density_rows": ([_vp, _vp, _i, _i, _pp, _i, _i, _vp], _i),
+    "vds_grad_rows": ([_vp, _vp, _i, _i, _pp, _vp, _i, _i, _i, _vp], _i),
     "vds_timing": ([_vp, _i], _i),
     "vds_energy_grad_noalloc": ([_vp, _i, _i, _pp, _dp, _vp, _vp, _vp], _i),
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
@@ -227,6 +229,16 @@ class Context:
         N, D = q.shape
         M = int(y.shape[0])
         _check(lib.vds_density_at(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(y), M, _ptr(f)))
+
+    def vds_density_rows(self, q, p: VdsParams, row0, nrows, rho_rows):
+        N, D = q.shape
+        _check(lib.vds_density_rows(self.h, _ptr(q), N, D, ctypes.byref(p), int(row0), int(nrows),
+                                    _ptr(rho_rows)))
+
+    def vds_grad_rows(self, q, p: VdsParams, rho, row0, nrows, out, mode=0):
+        N, D = q.shape
+        _check(lib.vds_grad_rows(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(rho), int(row0), int(nrows),
+                                 int(mode), _ptr(out)))
 
     def pod_build(self, X, Ns, M, s, energy=0.9999, r_max=64, r_fixed=0, kappa=None):
         kap = np.zeros(9) if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64).ravel()

@@ -1,5 +1,5 @@
 """Writes the FP64 oracle's reference trajectories of the 4-bead chain in shear
-(Sec. 3.2's chain in simple shear; Appendix A's explicit scheme) that the GPU
+(Sec. 3.3, the chain in simple shear; Appendix A, explicit scheme) that the GPU
 tests compare final-time stresses against.
 
 Calls only ``oracle`` and the seeded input generator; nothing here touches the
@@ -66,7 +66,7 @@ def run(name):
     out = dict(
         _source="FP64 oracle (oracle/vds_oracle.c explicit steps), written by "
                 "tests/golden/make_chain4_trajectories.py; Appendix A explicit scheme, "
-                "Sec. 3.2 shear set-up, stress of Sec. 2.1",
+                "Sec. 3.3 shear set-up, stress of Sec. 2.1",
         N=N, nb=NB, s=S, H=[1.0, 1.0, 1.0], kBT=1.0, zeta=4.0, dt=DT, rate=RATE,
         spring=c["spring"], b=c["b"], seed=SEED, h=h, steps=c["steps"],
         checkpoints=ckpt, rows=rows, q_rows=q[rows].tolist(),

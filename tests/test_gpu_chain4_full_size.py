@@ -1,4 +1,4 @@
-"""The 4-bead chain in shear at its full size (N = 65536, D = 9; Sec. 3.2's
+"""The 4-bead chain in shear at its full size (N = 65536, D = 9; Sec. 3.3's
 set-up, Appendix A's schemes) against the FP64 oracle, in the launch
 configurations the benchmark times:
 

@@ -168,3 +168,36 @@ def test_dumbbell_moment_equation_reaches_oldroyd_b():
         ex = np.array([[1 + 2 * rate ** 2, rate, 0], [rate, 1, 0], [0, 0, 1]])
         np.testing.assert_allclose(C, ex, rtol=1e-9, atol=1e-9)
         np.testing.assert_allclose(dumbbell_cov_exact(rate, 0.0), np.eye(3), atol=1e-15)
+
+
+# ------------------------------------------------ row-restricted explicit step
+# explicit_step_rows (the per-rank piece of a row-sharded step) pinned to the
+# whole-cloud step: the same particles' update for any row subset, the linear
+# (kBT = 0) limit as one factor of the matrix power, and rows from ranks
+# stacked in order equal to the whole step.
+
+@pytest.mark.parametrize("spring", [0, 1])
+def test_explicit_step_rows_equals_the_whole_step(orc, spring):
+    nb, s, N = 3, 3, 257
+    b = 50.0 if spring else 0.0
+    q = inputs.equilibrium_cloud(N, nb, s, seed=9, fene_b=b if spring else None).astype(np.float64)
+    p = orc.params(nb, s, H=[1.0, 2.0, 1.5], h=0.8, dt=0.004, kappa=inputs.shear_kappa(s, 1.3),
+                   spring=spring, b=b)
+    whole = orc.explicit_steps(q, p, 1)
+    rho = orc.density(q, p.h)
+    parts = [orc.explicit_step_rows(q, p, rho, np.arange(a, min(N, a + 100))) for a in range(0, N, 100)]
+    np.testing.assert_allclose(np.concatenate(parts), whole, rtol=1e-13, atol=1e-14)
+    rows = np.array([5, 0, 256, 77])
+    np.testing.assert_allclose(orc.explicit_step_rows(q, p, rho, rows), whole[rows], rtol=1e-13, atol=1e-14)
+
+
+def test_explicit_step_rows_linear_limit(orc):
+    nb, s, N = 3, 3, 40
+    H = np.array([1.0, 2.0, 3.0])
+    kap = inputs.shear_kappa(s, 1.0)
+    q0 = inputs.equilibrium_cloud(N, nb, s, seed=4).astype(np.float64)
+    p = orc.params(nb, s, H=H, kBT=0.0, h=0.5, dt=0.01, kappa=kap)
+    M = np.eye(nb * s) + 0.01 * _linear_operator(nb, s, H, kap, 4.0)
+    rows = np.arange(3, 29)
+    np.testing.assert_allclose(orc.explicit_step_rows(q0, p, orc.density(q0, 0.5), rows), q0[rows] @ M.T,
+                               rtol=1e-13, atol=1e-14)
