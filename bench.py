@@ -10,10 +10,12 @@ fused Euler update of all particles -- through the public C ABI (vds_step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs N independent replicas (one per rank, launched by torchrun): the
-path is replicated, not sharded (weak scaling, no collective on the data
-path).  ``--impl reference`` times the FP64 CPU oracle on a bounded sample of
-the same workload on the host cores (rank 0 only).
+N > 1 (launched by torchrun, one rank per GPU) splits the one cloud by
+particle rows over the ranks: each rank evaluates its rows against all
+particles, with two NCCL all-gathers per step (strong scaling; the job's
+steps/s).  ``--replicas`` runs N independent copies instead (weak scaling).
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
 """
 from __future__ import annotations
 
@@ -44,6 +46,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 GPUs: independent replicas (weak scaling) instead of the row split")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
     ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate,paper_tables,surrogate_n262144",
@@ -706,6 +710,88 @@ def job_rate(world, steps, max_ms):
     return world * steps / (max_ms / 1e3)
 
 
+def run_sharded(a, wl, rank, world, local, dist):
+    """N > 1: one cloud split by particle rows over the ranks (strong scaling):
+    each step every rank evaluates its rows against all particles, with two
+    all-gathers (rho, then the updated rows) over NCCL (paper_2603_12550_gb300
+    /shard.py).  value = the job's steps/s of the one N = 65536 cloud."""
+    import torch
+    from paper_2603_12550_gb300 import inputs, vds
+    from paper_2603_12550_gb300.shard import GpuRows, RowShardedStepper
+
+    N, nb, s = wl["N"], wl["nb"], wl["s"]
+    D = nb * s
+    stream = torch.cuda.current_stream()
+    ctx = vds.Context(local, stream)
+    q0 = inputs.equilibrium_cloud(N, nb, s, H=wl["H"], kBT=wl["kBT"], seed=wl["seed"])
+    qd = torch.from_numpy(q0).cuda()
+    h = ctx.vds_bandwidth(qd, 0)
+    p = vds.params(nb, s, H=wl["H"], kBT=wl["kBT"], zeta=wl["zeta"], h=h, dt=wl["dt"],
+                   kappa=inputs.shear_kappa(s, wl["rate"]), scheme=0)
+    st = RowShardedStepper(GpuRows(ctx, p), N, D, rank, world, dist=dist, device="cuda")
+    st.load(qd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    st.step(max(3, a.warmup))
+    torch.cuda.synchronize()
+    ctx.vds_timing(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    for k in range(a.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        st.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = clk.stop()
+    total_ms = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
+    pass_ms, pass_n, launches = ctx.vds_timing_read()
+    ctx.vds_timing(False)
+    total_ms = max_over_ranks(dist, total_ms, "cuda")
+    value = a.steps / (total_ms / 1e3)
+    # end to end: the whole state from pinned host memory, the step, the own
+    # rows back to the host
+    q_h = torch.from_numpy(q0).pin_memory()
+    rows_h = torch.empty((st.C, D), dtype=torch.float32).pin_memory()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(a.steps):
+        st.q.copy_(q_h, non_blocking=True)
+        st.step(1)
+        rows_h.copy_(st.q_loc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1), "cuda")
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tops = nsm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    t_grad = pass_ms[1] / max(1, pass_n[1]) / 1e3
+    ops_grad = float(N) * st.nrows * (3 * D + 2)
+    roof = {"bound": "alu", "kernel": "k_pair<D=9,GRAD> (gradient pair pass, this rank's rows)",
+            "achieved": ops_grad / t_grad / 1e12, "peak": peak_tops, "unit": "TOP/s (FP32 lane-ops)",
+            "frac": ops_grad / t_grad / 1e12 / peak_tops, "traffic": None, "ops_per_pair": 3 * D + 2,
+            "launch_ms": t_grad * 1e3,
+            "peak_note": f"{nsm} SMs x 128 FP32 lanes x {src} sm_max_mhz"}
+    cfg = _config(wl, h)
+    cfg["parallelism"] = f"rows{world} (particle rows split over ranks, 2 all-gathers per step)"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded equilibrium Gaussian cloud, the paper's initial condition)",
+            "config": cfg, "pair_interactions_per_s": value * N * N,
+            "e2e": {"value": a.steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(q0.nbytes),
+                    "d2h_bytes_per_step": int(st.C * D * 4)},
+            "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -726,6 +812,10 @@ def main():
     from paper_2603_12550_gb300 import build
     build.build()
     from paper_2603_12550_gb300 import vds
+    if world > 1 and not a.replicas:
+        run_sharded(a, wl, rank, world, local, dist)
+        dist.destroy_process_group()
+        return
 
     N, nb, s = wl["N"], wl["nb"], wl["s"]
     D = nb * s

@@ -67,6 +67,25 @@ VDS_API int vds_batch_step(vds_ctx *ctx, vds_batch *b, float *q_all, int nsteps,
 VDS_API int vds_batch_stress(vds_ctx *ctx, vds_batch *b, const float *q_all, double *tau);
 VDS_API int vds_batch_set_kappa(vds_ctx *ctx, vds_batch *b, const double *kappa);
 
+/* Convection (the u . grad_x q term of Eq. model_DymRepPar; for reduced
+ * coordinates the u . grad_x p term of Eq. model_DymReduced).  The
+ * homogeneous-flow experiments of Sec. 3 drop it; a grid of ensembles needs
+ * it.  One first-order upwind step of  dQ/dt + u . grad_x Q = 0  for a field
+ * held at the nodes of a structured macroscopic grid nx x ny x nz, node
+ * g = ix + nx (iy + ny iz), M FP32 values per node, node-major: q_in[g M + m]
+ * (device).  For particle ensembles the field is q_all of ensembles of equal
+ * size N, particle I being the same label at every node (M = N D); for
+ * reduced coordinates it is each node's p (M = r nb).
+ *   q_out[g] = q_in[g] - dt sum_b ( max(u_b,0) (q_in[g] - q_in[g - e_b])
+ *                                  + min(u_b,0) (q_in[g + e_b] - q_in[g]) ) / dx_b
+ * u: device G x 3 FP32 (the velocity at each node; axes of extent 1 are
+ * skipped); dx: host, 3 doubles > 0; dt > 0; bc: 0 periodic, 1 zero gradient
+ * (the node beyond a boundary takes the boundary node's value).  FP32
+ * arithmetic; q_out (device, G x M) must not overlap q_in (VDS_EARG).
+ * Asynchronous on the context stream. */
+VDS_API int vds_convect(vds_ctx *ctx, const float *q_in, float *q_out, int nx, int ny, int nz, long M,
+                        const float *u, const double *dx, double dt, int bc);
+
 /* Tile autotuner (no counterpart in the paper).  The batched pair kernel has
  * VDS_BATCH_CONFIGS candidate shapes: config k runs 128 << (k >> 1) threads
  * per CTA with 2 << (k & 1) particles per thread, so a work item's i-tile is

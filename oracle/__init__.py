@@ -554,6 +554,35 @@ def reduced_run(P0, Phi, p: OrParams, nsteps, refresh_every):
     return P
 
 
+def convect_upwind(Q, u, shape, dx, dt, bc=0):
+    """One first-order upwind step of dQ/dt + u . grad_x Q = 0 (the
+    convection term u . grad_x q of Eq. model_DymRepPar, u . grad_x p of Eq.
+    model_DymReduced) on a structured grid nx x ny x nz of nodes, node
+    g = ix + nx (iy + ny iz); Q is (G, M) (M values per node), u (G, 3).
+    Each axis of extent > 1 contributes
+      max(u_b, 0) (Q[g] - Q[g - e_b]) / dx_b + min(u_b, 0) (Q[g + e_b] - Q[g]) / dx_b,
+    the neighbour beyond a boundary being the opposite boundary node (bc 0,
+    periodic) or the boundary node itself (bc 1, zero gradient)."""
+    nx, ny, nz = shape
+    Q = np.asarray(Q, dtype=np.float64)
+    M = Q.shape[1]
+    F = Q.reshape(nz, ny, nx, M)
+    U = np.asarray(u, dtype=np.float64).reshape(nz, ny, nx, 3)
+    out = F.copy()
+    for b, axis, n in ((0, 2, nx), (1, 1, ny), (2, 0, nz)):
+        if n == 1:
+            continue
+        if bc == 0:
+            lo, hi = np.roll(F, 1, axis=axis), np.roll(F, -1, axis=axis)
+        else:
+            idx = np.arange(n)
+            lo = np.take(F, np.maximum(idx - 1, 0), axis=axis)
+            hi = np.take(F, np.minimum(idx + 1, n - 1), axis=axis)
+        ub = U[..., b][..., None]
+        out = out - dt / dx[b] * (np.maximum(ub, 0.0) * (F - lo) + np.minimum(ub, 0.0) * (hi - F))
+    return out.reshape(-1, M)
+
+
 def err_mor(q_mor, q_ref):
     """Relative L2 MOR error (Sec. 3.1)."""
     q_mor = np.asarray(q_mor, dtype=np.float64)

@@ -102,6 +102,7 @@ _SIGS = {
     "vds_batch_autotune": ([_vp, _vp, _vp, _i, _ip, _dp], _i),
     "vds_batch_stress": ([_vp, _vp, _vp, _dp], _i),
     "vds_batch_set_kappa": ([_vp, _vp, _dp], _i),
+    "vds_convect": ([_vp, _vp, _vp, _i, _i, _i, _l, _vp, _dp, _d, _i], _i),
     "vds_batch_set_config": ([_vp, _vp, _i], _i),
     "vds_batch_get_config": ([_vp, _ip], _i),
     "vds_score_param_count": ([_i, _i], _l),
@@ -239,6 +240,13 @@ class Context:
         N, D = q.shape
         _check(lib.vds_grad_rows(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(rho), int(row0), int(nrows),
                                  int(mode), _ptr(out)))
+
+    def vds_convect(self, q_in, q_out, shape, u, dx, dt, bc=0):
+        """One upwind convection step of a node-major field (include/vds_batch.h)."""
+        nx, ny, nz = (int(v) for v in shape)
+        M = q_in.numel() // (nx * ny * nz)
+        dxs = (ctypes.c_double * 3)(*[float(v) for v in dx])
+        _check(lib.vds_convect(self.h, _ptr(q_in), _ptr(q_out), nx, ny, nz, M, _ptr(u), dxs, float(dt), int(bc)))
 
     def pod_build(self, X, Ns, M, s, energy=0.9999, r_max=64, r_fixed=0, kappa=None):
         kap = np.zeros(9) if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64).ravel()
