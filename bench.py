@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--replicas", action="store_true",
                     help="with N > 1 GPUs: independent replicas (weak scaling) instead of the row split")
+    ap.add_argument("--shard", action="store_true",
+                    help="take the row-split path also with one rank (a one-GPU check of that path)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
     ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate,paper_tables,surrogate_n262144",
@@ -806,13 +808,16 @@ def main():
     import torch
     torch.cuda.set_device(local)
     dist = None
-    if world > 1:
+    if world > 1 or a.shard:
         import torch.distributed as dist
+        if "MASTER_ADDR" not in os.environ:
+            os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=os.environ.get("MASTER_PORT", "29533"),
+                              RANK=str(rank), WORLD_SIZE=str(world))
         dist.init_process_group("nccl")
     from paper_2603_12550_gb300 import build
     build.build()
     from paper_2603_12550_gb300 import vds
-    if world > 1 and not a.replicas:
+    if (world > 1 and not a.replicas) or a.shard:
         run_sharded(a, wl, rank, world, local, dist)
         dist.destroy_process_group()
         return
