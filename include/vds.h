@@ -216,6 +216,17 @@ VDS_API int vds_energy_grad_noalloc(const float *q, int N, int D, const vds_para
 VDS_API int vds_timing(vds_ctx *ctx, int enable);
 VDS_API int vds_timing_read(vds_ctx *ctx, double *ms, long *launches, long *total_launches);
 
+/* Failure detection check (no counterpart in the paper).  Every device-side
+ * wait of the library (bulk-copy and tensor-core completion barriers in the
+ * pair, refresh, Gram and network kernels; the batched queue) is bounded: it
+ * gives up after a time limit, raises VDS_ETIMEOUT in the context's error
+ * flag and lets the kernel return, so the context stays usable.
+ * vds_wait_selftest runs that pattern on two waits that nothing completes
+ * (an mbarrier phase with no arrival, a device flag that no thread sets),
+ * each limited to limit_s seconds (0 < limit_s <= 1), synchronises, and
+ * returns the status the host reads: VDS_ETIMEOUT when the mechanism works. */
+VDS_API int vds_wait_selftest(vds_ctx *ctx, double limit_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -105,7 +105,48 @@ int vds_sync_status(vds_ctx *c) {
   return e;
 }
 
+namespace {
+// The library's bounded-wait pattern run on waits that nothing completes:
+// an mbarrier phase no thread arrives on, and a flag in global memory no
+// thread sets.  Each gives up after limit_ns of globaltimer time and raises
+// VDS_ETIMEOUT, as every wait in the pair, refresh, Gram and network kernels
+// does; the kernel then returns normally.
+__global__ void k_wait_selftest(unsigned long long limit_ns, const volatile int *flag, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) vds_flag(err, VDS_ETIMEOUT);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = global_timer_ns();
+    while (*flag == 0) {
+      if (global_timer_ns() - t0 > limit_ns) {
+        vds_flag(err, VDS_ETIMEOUT);
+        break;
+      }
+    }
+  }
+}
+}  // namespace
+
 extern "C" {
+
+int vds_wait_selftest(vds_ctx *c, double limit_s) {
+  if (!c || !(limit_s > 0.0) || !(limit_s <= 1.0)) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  // the flag: a zeroed word of the reduction scratch that no kernel sets
+  VDS_TRY(vds_ensure(c, c->red, sizeof(double)));
+  VDS_CUDA_TRY(cudaMemsetAsync(c->red.ptr, 0, sizeof(double), c->stream));
+  k_wait_selftest<<<1, 32, 0, c->stream>>>((unsigned long long)(limit_s * 1e9),
+                                           (const volatile int *)c->red.ptr, c->err);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return vds_sync_status(c);
+}
 
 const char *vds_strerror(int st) {
   switch (st) {

@@ -82,6 +82,7 @@ _SIGS = {
     "vds_density_rows": ([_vp, _vp, _i, _i, _pp, _i, _i, _vp], _i),
     "vds_grad_rows": ([_vp, _vp, _i, _i, _pp, _vp, _i, _i, _i, _vp], _i),
     "vds_timing": ([_vp, _i], _i),
+    "vds_wait_selftest": ([_vp, _d], _i),
     "vds_energy_grad_noalloc": ([_vp, _i, _i, _pp, _dp, _vp, _vp, _vp], _i),
     "vds_timing_read": ([_vp, _dp, ctypes.POINTER(_l), ctypes.POINTER(_l)], _i),
     "pod_build": ([_vp, _vp, _l, _i, _i, _d, _i, _i, _dp, ctypes.POINTER(_vp), _ip], _i),
@@ -196,6 +197,10 @@ class Context:
         tot = ctypes.c_long()
         _check(lib.vds_timing_read(self.h, ms, n, ctypes.byref(tot)))
         return list(ms), list(n), tot.value
+
+    def vds_wait_selftest(self, limit_s=0.05) -> int:
+        """Status of two bounded waits that nothing completes (VDS_ETIMEOUT)."""
+        return int(lib.vds_wait_selftest(self.h, float(limit_s)))
 
     def vds_bandwidth(self, q, rule=0) -> float:
         N, D = q.shape

@@ -7,6 +7,9 @@ the host side only (no fault, trap or endless wait on the GPU):
 - an implicit step allowed one minimiser iteration with a tolerance it cannot
   meet reports VDS_ENOCONV (Appendix A's implicit scheme solved by
   iteration: the solve did not finish);
+- the bounded-wait pattern of every device-side wait, run on an mbarrier
+  phase and a flag that nothing completes with a 50 ms limit, gives up and
+  reports VDS_ETIMEOUT (vds_wait_selftest);
 
 and after each, the same context evaluates a clean cloud exactly as the FP64
 oracle does, i.e. the error left no stale flag or state behind.
@@ -99,4 +102,13 @@ def test_minimiser_out_of_iterations_is_reported_and_the_context_survives(orc, v
     ctx.vds_step(q, vds.params(nb, s, h=h, dt=dt, kappa=kap, scheme=1, tol=1e-6), 1)
     q_o, _, _ = orc.implicit_steps(q32.astype(np.float64), orc.params(nb, s, h=h, dt=dt, kappa=kap), 1)
     assert np.max(np.abs(q.cpu().numpy() - q_o)) <= 1e-5 * np.max(np.abs(q_o))
+    _clean_matches_oracle(orc, vds, ctx)
+
+
+def test_bounded_waits_give_up_and_the_context_survives(orc, vds, ctx):
+    import time
+    t0 = time.perf_counter()
+    assert ctx.vds_wait_selftest(0.05) == vds.VDS_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert ctx.vds_wait_selftest(0.01) == vds.VDS_ETIMEOUT
     _clean_matches_oracle(orc, vds, ctx)
