@@ -457,14 +457,11 @@ __global__ void __launch_bounds__(RC_NT, 1)
 // consecutive 32-particle chunks (one 32 KB bulk copy at NCP = 64) and their
 // 64 records (one copy), each with its own mbarrier, so the Z-forming warps
 // wait only for the records and the tensor cores only for B; tensor memory
-// holds three pair slots of Z (6 chunks) beside two accumulators of NCP
-// columns (Z_hi B_hi, Z_hi B_lo and Z_lo B_hi as three MMAs of N = NCP into
-// one accumulator).  The copies run up to NS2 pairs of chunks ahead of the
-// tensor cores, the Z-forming warps up to three, so a warp that runs ahead
-// waits for the tensor cores only when it is three passes ahead.
+// holds two pair slots of Z (4 chunks).  The copies run up to NS2 pairs of
+// chunks ahead of the tensor cores, the Z-forming warps up to two.
 //
 // Barriers (pass c2 = chunks 2 c2 and 2 c2 + 1; pair slot j = c2 % NS2,
-// completion u = c2 / NS2; Z pair zp = c2 % 3, completion c2 / 3):
+// completion u = c2 / NS2; Z pair zp = c2 & 1, completion c2 >> 1):
 //   rfull[j]  bulk-copy bytes of the pass's records;
 //   bfull[j]  bulk-copy bytes of the pass's B images;
 //   sfree[j]  tcgen05.commit after the pass's MMAs (slot j may be refilled);
@@ -498,12 +495,11 @@ __global__ void __launch_bounds__(RC_NT, 1)
   constexpr int DP = L::DP;
   constexpr int NS2 = L::NS2;
   constexpr int QC = NCP / 4;           // accumulator columns per thread in a flush
-  constexpr int ACW = NCP;              // accumulator columns per buffer
-  constexpr int NZP = 3;                // Z pair slots (2 chunks x (hi, lo) x 32 columns each)
-  constexpr int TCOLS = 512;            // 2 ACW accumulator columns + NZP Z pairs of 128
-  static_assert(2 * ACW + NZP * 128 <= TCOLS, "tensor memory columns");
+  constexpr int ACW = 2 * NCP;          // Z_hi against [B_hi; B_lo]: N = 2 NCP
+  constexpr int TCOLS = 512;            // 2 ACW accumulator columns + 4 Z slots of 64
+  static_assert(2 * ACW + 4 * 64 <= TCOLS, "tensor memory columns");
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t rfull[NS2], bfull[NS2], sfree[NS2], zready[NZP], zfree[NZP], segdone[2],
+  __shared__ __align__(8) uint64_t rfull[NS2], bfull[NS2], sfree[NS2], zready[2], zfree[2], segdone[2],
       accfree[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -525,11 +521,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
       mbar_init(&bfull[j], 1);
       mbar_init(&sfree[j], 1);
     }
-    for (int b = 0; b < NZP; ++b) {
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&zready[b], RC_PW);
       mbar_init(&zfree[b], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
       mbar_init(&segdone[b], 1);
       mbar_init(&accfree[b], RC_PW);
     }
@@ -574,10 +568,10 @@ __global__ void __launch_bounds__(RC_NT, 1)
   } else if (warp == RC_PW + 1) {
     // ---------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP);
+      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP), idesc2 = tc_idesc(TC_FMT_TF32, RC_M, ACW);
       for (int c2 = 0; c2 < npass && ok; ++c2) {
-        const int j = c2 % NS2, zp = c2 % NZP;
-        if (!rc_wait(&zready[zp], (uint32_t)((c2 / NZP) & 1), abort) ||
+        const int j = c2 % NS2, zp = c2 & 1;
+        if (!rc_wait(&zready[zp], (uint32_t)((c2 >> 1) & 1), abort) ||
             !rc_wait(&bfull[j], (uint32_t)((c2 / NS2) & 1), abort)) {
           ok = false;
           break;
@@ -589,16 +583,16 @@ __global__ void __launch_bounds__(RC_NT, 1)
             ok = false;
             break;
           }
-          const uint32_t b_hi = sbase + (uint32_t)(j * L::SLOT + e * L::BCH), b_lo = b_hi + L::BOP;
-          const uint32_t zt = tmem + (uint32_t)(2 * ACW + 128 * zp + 64 * e);  // Z hi; lo at + 32
+          const uint32_t b_hi = sbase + (uint32_t)(j * L::SLOT + e * L::BCH);
+          const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * (2 * zp + e));  // Z hi; lo at + 32
           const uint32_t acc = tmem + (uint32_t)(b * ACW);
 #pragma unroll
           for (int k = 0; k < RC_KC / 8; ++k) {
             const uint32_t o = (uint32_t)k * 256u;
             const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, first);
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_lo + o), idesc, 1);
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc, 1);
+            // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, 1);
           }
           if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
         }
@@ -632,17 +626,24 @@ __global__ void __launch_bounds__(RC_NT, 1)
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
       tc_fence_after();
       const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * ACW + cq * QC);
+      // the two halves of the accumulator (Z_hi B_hi + Z_lo B_hi, Z_hi B_lo)
       if constexpr (QC == 16) {
         uint32_t v[16];
-        tc_ld16(ta, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tot[j] += __uint_as_float(v[j]);
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld16(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[j] += __uint_as_float(v[j]);
+        }
       } else {
         static_assert(QC == 8, "accumulator columns per thread");
         uint32_t v[8];
-        tc_ld8(ta, v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) tot[j] += __uint_as_float(v[j]);
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld8(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tot[j] += __uint_as_float(v[j]);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -658,17 +659,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
         unsigned long long r2 = f2_pack(0.f, 0.f);
-        const unsigned long long *rp = rs + (u / 2) * DP;
-        // coordinates d and d + 1 of the pair in one 128-bit shared load
 #pragma unroll
-        for (int d = 0; d + 1 < D; d += 2) {
-          const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(rp + d);
-          const unsigned long long d0 = f2_sub(xi2[d], w.x), d1 = f2_sub(xi2[d + 1], w.y);
-          r2 = f2_fma(d0, d0, r2);
-          r2 = f2_fma(d1, d1, r2);
-        }
-        if constexpr (D % 2 == 1) {
-          const unsigned long long dd = f2_sub(xi2[D - 1], rp[D - 1]);
+        for (int d = 0; d < D; ++d) {
+          const unsigned long long dd = f2_sub(xi2[d], rs[(u / 2) * DP + d]);
           r2 = f2_fma(dd, dd, r2);
         }
         float r2a, r2b;
@@ -685,9 +678,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
       }
     };
     for (int c2 = 0; c2 < npass && ok; ++c2) {
-      const int j = c2 % NS2, zp = c2 % NZP;
+      const int j = c2 % NS2, zp = c2 & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&rfull[j], (uint32_t)((c2 / NS2) & 1), abort) &&
-                                       (c2 < NZP || rc_wait(&zfree[zp], (uint32_t)((c2 / NZP - 1) & 1), abort)))) {
+                                       (c2 < 2 || rc_wait(&zfree[zp], (uint32_t)(((c2 >> 1) - 1) & 1), abort)))) {
         ok = false;
         break;
       }
