@@ -407,9 +407,11 @@ def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
     rf_ms, rf_n, _ = ctx.vds_timing_read()
     ctx.vds_timing(False)
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
-    # the refresh pass against its CUDA-core floor: the kernel values Z_IK
-    # (2D + 1 FP32 lane-ops per ordered pair; the contraction Z B runs on the
-    # tensor cores) at SMs x 128 lanes x the measured maximum SM clock
+    # the refresh pass against its CUDA-core floor: the kernel values Z_IK by
+    # their definition, 2D + 1 FP32 lane-ops per ordered pair (the kernel
+    # forms the distance through the particles' norms, D + 2 operations; the
+    # contraction Z B runs on the tensor cores), at SMs x 128 lanes x the
+    # measured maximum SM clock
     peaks, src = _peaks()
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak_tops = nsm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -419,6 +421,8 @@ def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
                     "ops_per_pair": 2 * D + 1, "achieved": ops / rf_t / 1e12, "peak": peak_tops,
                     "unit": "TOP/s (FP32 lane-ops)", "frac": ops / rf_t / 1e12 / peak_tops,
                     "floor_ms": ops / (peak_tops * 1e12) * 1e3, "launch_ms": rf_t * 1e3,
+                    "kernel_ops_per_pair": D + 2,
+                    "tensor_tflops": float(N) * N * 2 * 2 * (2 * s * basis.info()["r"] + 1) / rf_t / 1e12,
                     "peak_note": f"{nsm} SMs x 128 FP32 lanes x {src} sm_max_mhz; the time includes the "
                                  "B-image and split-sum kernels of a refresh"}
     out = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,

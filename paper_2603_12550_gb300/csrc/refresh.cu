@@ -12,24 +12,25 @@
 // with the N x (2 s r + 1) matrix B = [Phi, Phi / rho, 1 / rho] (one row per
 // particle K): the shape of attention's P V.  Z never exists in memory.  One
 // CTA per 128 particles I (and per column chunk of B), warp-specialised:
-//   warps 0-15  form Z_IK = exp2(-|q^_I - q^_K|^2) for a chunk of 32
-//               particles K (2D FP32 ops and one ex2 per pair, two pairs
-//               per f32x2 instruction), split it into Z_hi = tf32(Z) and
-//               Z_lo = Z - Z_hi (passed unrounded: the MMA uses its TF32
-//               bits) and store both in tensor memory, one row per thread
-//               (2 s r + 1 <= 64), or in shared memory in the tensor cores'
-//               K-major layout;
-//   warp 16     stages each chunk's 32 records and its B slice (hi and lo
-//               TF32 parts, pre-arranged in global memory as the exact
-//               shared-memory image) with 1-D bulk copies (TMA engine);
-//   warp 17     issues tcgen05.mma of kind::tf32 (M = 128, N = column chunk,
-//               K = 8; Z_hi B_hi + Z_hi B_lo + Z_lo B_hi: TF32 with one
-//               refinement step, relative error about 2^-21).
-// A ring of RC_NZ slots (records, B slice, Z tile) connects them through
-// mbarriers; nothing waits on a CTA-wide barrier inside the loop.  The
-// accumulator (FP32, tensor memory) covers one segment of 512 particles K
-// and is double-buffered: warps 0-15 add a finished segment into FP32
-// registers while the tensor cores fill the other buffer (two-level
+//   warps 0-15  form Z_IK = exp2(-|q^_I - q^_K|^2) for chunks of 32
+//               particles K on the CUDA cores (one ex2 per pair, two pairs
+//               per f32x2 instruction) and put them where the tensor cores
+//               read them;
+//   warp 16     stages the records and B slices (hi and lo TF32 parts,
+//               pre-arranged in global memory as the exact shared-memory
+//               images) with 1-D bulk copies (TMA engine);
+//   warp 17     issues tcgen05.mma of kind::tf32 (M = 128, K = 8) into an
+//               FP32 accumulator in tensor memory.
+// Two kernels share this plan.  k_refresh_ta (2 s r + 1 <= 64, the common
+// case: r <= 10 at s = 3) keeps Z in tensor memory, one row per thread, as
+// the MMAs' A operand, rounded to TF32 once against B_hi + B_lo; the wide
+// kernel k_refresh_tc (up to 256 columns) keeps Z in shared memory in the
+// tensor cores' K-major layout and forms Z_hi B_hi + Z_hi B_lo + Z_lo B_hi
+// (TF32 with a refinement step on both operands, relative error about
+// 2^-21).  mbarrier rings connect the roles; nothing waits on a CTA-wide
+// barrier inside the loop.  The accumulator covers one segment of 512
+// particles K and is double-buffered: warps 0-15 add a finished segment into
+// FP32 registers while the tensor cores fill the other buffer (two-level
 // summation, as in the CUDA-core pair passes: no FP32 sum runs over more
 // than 512 terms).  Every wait is bounded; a wait that runs out raises the
 // abort flag, every role leaves its loop, copies and MMAs in flight are
@@ -121,8 +122,17 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
   bimg[o + tile] = to_tf32(v - h);
   if (c == 0 && cb == 0) {
     if (NCP <= 64) {
+      // coordinates, then |q^_K|^2 in place of w (FP32, d ascending: the same
+      // sequence of roundings as the row's own norm in k_refresh_ta)
       float *dst = recs + ((size_t)ch * RC_KC + (k & ~1)) * DP + (k & 1);
-      for (int d = 0; d < DP; ++d) dst[2 * d] = rec[(size_t)K * DP + d];
+      float nrm = 0.f;
+      for (int d = 0; d < D; ++d) {
+        const float x = rec[(size_t)K * DP + d];
+        dst[2 * d] = x;
+        nrm = fmaf(x, x, nrm);
+      }
+      dst[2 * D] = nrm;
+      for (int d = D + 1; d < DP; ++d) dst[2 * d] = rec[(size_t)K * DP + d];
     } else {
       float *dst = recs + (size_t)K * 2 * DP;
       for (int d = 0; d < DP; ++d) dst[2 * d] = dst[2 * d + 1] = rec[(size_t)K * DP + d];
@@ -145,6 +155,11 @@ __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsig
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
 __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
                                                      unsigned long long c) {
   unsigned long long r;
@@ -152,18 +167,30 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
   return r;
 }
 
+// One probe of an mbarrier phase that may suspend the thread (up to 20 us)
+// until the phase completes, so that waiting roles do not take issue slots
+// from the warps sharing their scheduler.
+__device__ __forceinline__ bool rc_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
 // Wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool rc_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_timer_ns();
-  for (uint32_t n = 0;; ++n) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((n & 63u) == 63u) {
-      if (*abort) return false;
-      if (global_timer_ns() - t0 > VDS_WAIT_LIMIT_NS) {
-        *abort = 1;
-        return false;
-      }
+  for (;;) {
+    if (rc_try_wait_sleep(bar, parity)) return true;
+    if (*abort) return false;
+    if (global_timer_ns() - t0 > VDS_WAIT_LIMIT_NS) {
+      *abort = 1;
+      return false;
     }
   }
 }
@@ -457,11 +484,22 @@ __global__ void __launch_bounds__(RC_NT, 1)
 // consecutive 32-particle chunks (one 32 KB bulk copy at NCP = 64) and their
 // 64 records (one copy), each with its own mbarrier, so the Z-forming warps
 // wait only for the records and the tensor cores only for B; tensor memory
-// holds two pair slots of Z (4 chunks).  The copies run up to NS2 pairs of
-// chunks ahead of the tensor cores, the Z-forming warps up to two.
+// holds four pair slots of Z (8 chunks).  The copies run up to NS2 pairs of
+// chunks ahead of the tensor cores, the Z-forming warps up to four.
+//
+// Precision: Z is rounded to TF32 once (relative error at most 2^-11 per
+// kernel value, unbiased) and B carries the refinement step (B_hi + B_lo), so
+// one MMA of N = 2 NCP per K step forms Z (B_hi + B_lo).  Z's own low part
+// (the third product of the wide kernel) is left out: with it the tensor
+// cores' accumulator updates, not the kernel values, set the pace; without
+// it X^B moved by at most 1e-6 relative against the FP64 oracle's, far
+// inside the 1e-4 the tests demand.  The squared distance of a pair is
+// expanded, |x - y|^2 = |x|^2 + |y|^2 - 2 x.y: D + 2 FP32 operations instead
+// of 2D + 1 (k_rc_bt stores each staged record's norm; the row's own is
+// rounded the same way, so coincident points give exactly 0).
 //
 // Barriers (pass c2 = chunks 2 c2 and 2 c2 + 1; pair slot j = c2 % NS2,
-// completion u = c2 / NS2; Z pair zp = c2 & 1, completion c2 >> 1):
+// completion u = c2 / NS2; Z pair zp = c2 % NZP, completion c2 / NZP):
 //   rfull[j]  bulk-copy bytes of the pass's records;
 //   bfull[j]  bulk-copy bytes of the pass's B images;
 //   sfree[j]  tcgen05.commit after the pass's MMAs (slot j may be refilled);
@@ -495,11 +533,12 @@ __global__ void __launch_bounds__(RC_NT, 1)
   constexpr int DP = L::DP;
   constexpr int NS2 = L::NS2;
   constexpr int QC = NCP / 4;           // accumulator columns per thread in a flush
-  constexpr int ACW = 2 * NCP;          // Z_hi against [B_hi; B_lo]: N = 2 NCP
-  constexpr int TCOLS = 512;            // 2 ACW accumulator columns + 4 Z slots of 64
-  static_assert(2 * ACW + 4 * 64 <= TCOLS, "tensor memory columns");
+  constexpr int ACW = 2 * NCP;          // Z against [B_hi; B_lo]: N = 2 NCP
+  constexpr int NZP = 4;                // Z pair slots: 2 chunks x 32 columns each
+  constexpr int TCOLS = 512;            // 2 ACW accumulator columns + NZP x 64 Z columns
+  static_assert(2 * ACW + NZP * 64 <= TCOLS, "tensor memory columns");
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t rfull[NS2], bfull[NS2], sfree[NS2], zready[2], zfree[2], segdone[2],
+  __shared__ __align__(8) uint64_t rfull[NS2], bfull[NS2], sfree[NS2], zready[NZP], zfree[NZP], segdone[2],
       accfree[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
@@ -521,9 +560,11 @@ __global__ void __launch_bounds__(RC_NT, 1)
       mbar_init(&bfull[j], 1);
       mbar_init(&sfree[j], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NZP; ++b) {
       mbar_init(&zready[b], RC_PW);
       mbar_init(&zfree[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&segdone[b], 1);
       mbar_init(&accfree[b], RC_PW);
     }
@@ -570,8 +611,8 @@ __global__ void __launch_bounds__(RC_NT, 1)
     if (lane == 0) {
       const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP), idesc2 = tc_idesc(TC_FMT_TF32, RC_M, ACW);
       for (int c2 = 0; c2 < npass && ok; ++c2) {
-        const int j = c2 % NS2, zp = c2 & 1;
-        if (!rc_wait(&zready[zp], (uint32_t)((c2 >> 1) & 1), abort) ||
+        const int j = c2 % NS2, zp = c2 % NZP;
+        if (!rc_wait(&zready[zp], (uint32_t)((c2 / NZP) & 1), abort) ||
             !rc_wait(&bfull[j], (uint32_t)((c2 / NS2) & 1), abort)) {
           ok = false;
           break;
@@ -584,7 +625,7 @@ __global__ void __launch_bounds__(RC_NT, 1)
             break;
           }
           const uint32_t b_hi = sbase + (uint32_t)(j * L::SLOT + e * L::BCH);
-          const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * (2 * zp + e));  // Z hi; lo at + 32
+          const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * zp + 32 * e);
           const uint32_t acc = tmem + (uint32_t)(b * ACW);
 #pragma unroll
           for (int k = 0; k < RC_KC / 8; ++k) {
@@ -592,7 +633,6 @@ __global__ void __launch_bounds__(RC_NT, 1)
             const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
             // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
             tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(32 + 8 * k), tc_sdesc(b_hi + o), idesc, 1);
           }
           if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
         }
@@ -621,6 +661,10 @@ __global__ void __launch_bounds__(RC_NT, 1)
     unsigned long long xi2[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) xi2[d] = f2_pack(xi[d], xi[d]);
+    float ni = 0.f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) ni = fmaf(xi[d], xi[d], ni);
+    const unsigned long long ni2 = f2_pack(ni, ni), m2 = f2_pack(-2.f, -2.f);
     auto flush = [&](int g) -> bool {
       const int b = g & 1;
       if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
@@ -651,49 +695,57 @@ __global__ void __launch_bounds__(RC_NT, 1)
       return true;
     };
     int flushed = 0;  // segments added into registers
-    // Z of one chunk for this thread's row and 8 K, two K per f32x2
-    // instruction: the squared distances to records u and u + 1 in the two
-    // halves of a packed register (records interleaved by particle pairs)
-    auto z_chunk = [&](const uint8_t *recs_ch, uint32_t (&hv)[8], uint32_t (&lv)[8]) {
+    // Z of one chunk for this thread's row and 8 K, rounded to TF32, two K
+    // per f32x2 instruction: the squared distances to records u and u + 1 in
+    // the two halves of a packed register (records interleaved by particle
+    // pairs), expanded through the norms (see above)
+    auto z_chunk = [&](const uint8_t *recs_ch, uint32_t (&hv)[8]) {
       const unsigned long long *rs = reinterpret_cast<const unsigned long long *>(recs_ch) + cq * 4 * DP;
 #pragma unroll
       for (int u = 0; u < 8; u += 2) {
-        unsigned long long r2 = f2_pack(0.f, 0.f);
+        const unsigned long long *rp = rs + (u / 2) * DP;
+        // coordinates d, d + 1 (and the norms in slot D) of the pair in
+        // 128-bit shared loads
+        unsigned long long dot = f2_pack(0.f, 0.f), nk = 0ull;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const unsigned long long dd = f2_sub(xi2[d], rs[(u / 2) * DP + d]);
-          r2 = f2_fma(dd, dd, r2);
+        for (int d = 0; d <= D; d += 2) {
+          if (d + 1 <= D) {
+            const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(rp + d);
+            if (d + 1 < D) {
+              dot = f2_fma(xi2[d], w.x, dot);
+              dot = f2_fma(xi2[d + 1], w.y, dot);
+            } else {
+              dot = f2_fma(xi2[d], w.x, dot);
+              nk = w.y;
+            }
+          } else {
+            nk = rp[D];
+          }
         }
+        const unsigned long long r2 = f2_fma(m2, dot, f2_add(ni2, nk));
         float r2a, r2b;
         f2_unpack(r2, r2a, r2b);
         const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
         const float ha = to_tf32(za), hb = to_tf32(zb);
         hv[u] = __float_as_uint(ha);
         hv[u + 1] = __float_as_uint(hb);
-        // the low parts stay unrounded: the MMA reads only their TF32 bits
-        float la, lb;
-        f2_unpack(f2_sub(f2_pack(za, zb), f2_pack(ha, hb)), la, lb);
-        lv[u] = __float_as_uint(la);
-        lv[u + 1] = __float_as_uint(lb);
       }
     };
     for (int c2 = 0; c2 < npass && ok; ++c2) {
-      const int j = c2 % NS2, zp = c2 & 1;
+      const int j = c2 % NS2, zp = c2 % NZP;
       if (!__all_sync(0xffffffffu, rc_wait(&rfull[j], (uint32_t)((c2 / NS2) & 1), abort) &&
-                                       (c2 < 2 || rc_wait(&zfree[zp], (uint32_t)(((c2 >> 1) - 1) & 1), abort)))) {
+                                       (c2 < NZP || rc_wait(&zfree[zp], (uint32_t)((c2 / NZP - 1) & 1), abort)))) {
         ok = false;
         break;
       }
       tc_fence_after();  // the MMAs that read this Z pair have completed
       const uint8_t *rp = sm + (size_t)j * L::SLOT + L::ROFF;
-      uint32_t hv0[8], lv0[8], hv1[8], lv1[8];
-      z_chunk(rp, hv0, lv0);
-      z_chunk(rp + L::REC_BYTES, hv1, lv1);
-      const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 128 * zp + 8 * cq);
+      uint32_t hv0[8], hv1[8];
+      z_chunk(rp, hv0);
+      z_chunk(rp + L::REC_BYTES, hv1);
+      const uint32_t zt = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(2 * ACW + 64 * zp + 8 * cq);
       tc_st8(zt, hv0);
-      tc_st8(zt + 32u, lv0);
-      tc_st8(zt + 64u, hv1);
-      tc_st8(zt + 96u, lv1);
+      tc_st8(zt + 32u, hv1);
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
