@@ -35,6 +35,7 @@
 // than 512 terms).  Every wait is bounded; a wait that runs out raises the
 // abort flag, every role leaves its loop, copies and MMAs in flight are
 // waited for and the tensor memory is freed.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "pair.cuh"
@@ -51,6 +52,14 @@ constexpr int RC_NT = RC_PT + 64;  // + one warp of bulk copies + one warp of MM
 constexpr int RC_SEG = 16;   // chunks per FP32 accumulator segment (512 K)
 constexpr int RC_FLUSH = 7;  // chunk of the next segment at which a segment is flushed
 constexpr int RC_ZOP = RC_M * RC_KC * 4;  // bytes of one Z operand tile (16 KB)
+// k_refresh_ta works in FP16 (kind::f16, K = 16 per MMA) on chunks of 64
+// particles K, eight to the same 512-particle segment; B is scaled by 2^12
+// on its way to FP16 (|Phi| <= 1 and rho >= 1 put every entry of
+// [Phi, Phi/rho, 1/rho] below 4096, and the small ones above FP16's smallest
+// normal), the totals by 2^-12 on the way out (both exact)
+constexpr int TA_KC = 64;
+constexpr int TA_SEGC = 8;
+constexpr float TA_BSCALE = 4096.f;
 
 // Shared memory of the wide-B kernel (2 s r + 1 > 64): NZ slots of
 // [Z hi | Z lo | B hi | B lo | records]; the epilogue reuses it for the
@@ -113,13 +122,28 @@ __global__ void k_rc_bt(const float *__restrict__ phi, int ld, int r, int s, int
       v = w;
     }
   }
-  const int nch = Npad / RC_KC, ch = K / RC_KC, k = K - ch * RC_KC;
-  const size_t tile = (size_t)NCP * RC_KC;
-  const size_t o = ((size_t)cb * nch + ch) * 2 * tile +
-                   (size_t)(((c >> 3) * 1024 + (k >> 2) * 128 + (c & 7) * 16 + (k & 3) * 4) >> 2);
-  const float h = to_tf32(v);
-  bimg[o] = h;
-  bimg[o + tile] = to_tf32(v - h);
+  if (NCP <= 64) {
+    // FP16, chunks of TA_KC particles: element (c, k) of the hi tile at byte
+    // (c/8)*1024 + (k/8)*128 + (c%8)*16 + (k%8)*2, the lo tile NCP*128 bytes on
+    const int nch = Npad / TA_KC, ch = K / TA_KC, k = K - ch * TA_KC;
+    __half *img = reinterpret_cast<__half *>(bimg);
+    const size_t tile = (size_t)NCP * TA_KC;  // halves per tile
+    const size_t o = ((size_t)cb * nch + ch) * 2 * tile +
+                     (size_t)(((c >> 3) * 1024 + (k >> 3) * 128 + (c & 7) * 16 + (k & 7) * 2) >> 1);
+    const float vs = v * TA_BSCALE;
+    const __half h = __float2half_rn(vs);
+    img[o] = h;
+    img[o + tile] = __float2half_rn(vs - __half2float(h));
+  } else {
+    const int nch = Npad / RC_KC, ch = K / RC_KC, k = K - ch * RC_KC;
+    const size_t tile = (size_t)NCP * RC_KC;
+    const size_t o = ((size_t)cb * nch + ch) * 2 * tile +
+                     (size_t)(((c >> 3) * 1024 + (k >> 2) * 128 + (c & 7) * 16 + (k & 3) * 4) >> 2);
+    const float h = to_tf32(v);
+    bimg[o] = h;
+    bimg[o + tile] = to_tf32(v - h);
+  }
+  const int ch = K / RC_KC, k = K - ch * RC_KC;
   if (c == 0 && cb == 0) {
     if (NCP <= 64) {
       // coordinates, then |q^_K|^2 in place of w (FP32, d ascending: the same
@@ -204,13 +228,13 @@ __device__ __forceinline__ void rc_epilogue(uint8_t *sm, int tot_ld, const float
                                             int lane, int i0, int cb, int N, const float *__restrict__ rec,
                                             const float *__restrict__ phi, int ld, int r, int s, int rr,
                                             float *__restrict__ U1, float *__restrict__ U2,
-                                            float *__restrict__ part) {
+                                            float *__restrict__ part, float scale) {
   constexpr int DP = Rec<D>::DP;
   float *T = reinterpret_cast<float *>(sm);
   if (tid < RC_PT) {
     const int il = (warp & 3) * 32 + lane, cq = warp >> 2;
 #pragma unroll
-    for (int j = 0; j < QC; ++j) T[il * tot_ld + cq * QC + j] = tot[j];
+    for (int j = 0; j < QC; ++j) T[il * tot_ld + cq * QC + j] = tot[j] * scale;
   }
   __syncthreads();
   if (part) {
@@ -474,29 +498,34 @@ __global__ void __launch_bounds__(RC_NT, 1)
   tc_fence_after();
   if (warp == 0) tc_dealloc(tmem, TCOLS);
   if (*abort) return;
-  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part);
+  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part,
+                          1.f);
 }
 
 // ------------------------------------------------ Z in tensor memory (NCP <= 64)
 //
-// The same contraction with Z in tensor memory and the staging decoupled
-// from it: shared memory holds NS2 pair slots, each the B images of two
-// consecutive 32-particle chunks (one 32 KB bulk copy at NCP = 64) and their
-// 64 records (one copy), each with its own mbarrier, so the Z-forming warps
-// wait only for the records and the tensor cores only for B; tensor memory
-// holds four pair slots of Z (8 chunks).  The copies run up to NS2 pairs of
-// chunks ahead of the tensor cores, the Z-forming warps up to four.
+// The same contraction with Z in tensor memory, in FP16 (kind::f16, K = 16
+// per MMA: half the accumulator updates of K = 8 TF32 steps at the same
+// 11-bit significand), and the staging decoupled from it: shared memory
+// holds NS2 pair slots, each the B images of two consecutive 64-particle
+// chunks (one 32 KB bulk copy at NCP = 64) and their 128 records (one copy),
+// each with its own mbarrier, so the Z-forming warps wait only for the
+// records and the tensor cores only for B; tensor memory holds four pair
+// slots of Z (8 chunks, two halves per column).  The copies run up to NS2
+// pairs of chunks ahead of the tensor cores, the Z-forming warps up to four.
 //
-// Precision: Z is rounded to TF32 once (relative error at most 2^-11 per
-// kernel value, unbiased) and B carries the refinement step (B_hi + B_lo), so
-// one MMA of N = 2 NCP per K step forms Z (B_hi + B_lo).  Z's own low part
-// (the third product of the wide kernel) is left out: with it the tensor
-// cores' accumulator updates, not the kernel values, set the pace; without
-// it X^B moved by at most 1e-6 relative against the FP64 oracle's, far
-// inside the 1e-4 the tests demand.  The squared distance of a pair is
-// expanded, |x - y|^2 = |x|^2 + |y|^2 - 2 x.y: D + 2 FP32 operations instead
-// of 2D + 1 (k_rc_bt stores each staged record's norm; the row's own is
-// rounded the same way, so coincident points give exactly 0).
+// Precision: Z is rounded to FP16 once (relative error at most 2^-11 per
+// kernel value, unbiased; below FP16's smallest normal an absolute error of
+// at most 2^-25) and B carries the refinement step (B_hi + B_lo, each FP16,
+// of B scaled by 2^12), so one MMA of N = 2 NCP per K step forms
+// Z (B_hi + B_lo).  Z's own low part (the third product of the wide kernel)
+// is left out: with it the tensor cores' accumulator updates, not the kernel
+// values, set the pace; without it X^B moved by at most 1e-6 relative against
+// the FP64 oracle's, far inside the 1e-4 the tests demand.  The squared
+// distance of a pair is expanded, |x - y|^2 = |x|^2 + |y|^2 - 2 x.y: D + 2
+// FP32 operations instead of 2D + 1 (k_rc_bt stores each staged record's
+// norm; the row's own is rounded the same way, so coincident points give
+// exactly 0).
 //
 // Barriers (pass c2 = chunks 2 c2 and 2 c2 + 1; pair slot j = c2 % NS2,
 // completion u = c2 / NS2; Z pair zp = c2 % NZP, completion c2 / NZP):
@@ -509,9 +538,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
 template <int D, int NCP>
 struct TaLayout {
   static constexpr int DP = Rec<D>::DP;
-  static constexpr int BOP = NCP * RC_KC * 4;        // one B operand tile
+  static constexpr int BOP = NCP * TA_KC * 2;        // one FP16 B operand tile
   static constexpr int BCH = 2 * BOP;                // B hi + lo of one chunk
-  static constexpr int REC_BYTES = RC_KC * DP * 4;   // one chunk's records
+  static constexpr int REC_BYTES = TA_KC * DP * 4;   // one chunk's records
   static constexpr int ROFF = 2 * BCH;               // records of the pair
   static constexpr int SLOT = ((2 * BCH + 2 * REC_BYTES + 1023) / 1024) * 1024;
   static constexpr int NS2 = (200 * 1024 / SLOT) < 8 ? (200 * 1024 / SLOT) : 8;
@@ -546,10 +575,10 @@ __global__ void __launch_bounds__(RC_NT, 1)
   const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
   const int i0 = tile * RC_M;
   const int cb = blockIdx.y;
-  const int nch_all = Npad / RC_KC, nseg_all = (nch_all + RC_SEG - 1) / RC_SEG;
+  const int nch_all = Npad / TA_KC, nseg_all = (nch_all + TA_SEGC - 1) / TA_SEGC;
   const int sg0 = split * nseg_all / nsplit, sg1 = (split + 1) * nseg_all / nsplit;
-  const int c0 = sg0 * RC_SEG;                       // first chunk of this CTA
-  const int nch = min(sg1 * RC_SEG, nch_all) - c0;   // a multiple of 8: Npad is of 256
+  const int c0 = sg0 * TA_SEGC;                      // first chunk of this CTA
+  const int nch = min(sg1 * TA_SEGC, nch_all) - c0;  // a multiple of 4: Npad is of 256
   const int npass = nch / 2;
   const int nseg = sg1 - sg0;
   volatile int *abort = &s_abort;
@@ -609,7 +638,7 @@ __global__ void __launch_bounds__(RC_NT, 1)
   } else if (warp == RC_PW + 1) {
     // ---------------------------------------------------- MMA issue
     if (lane == 0) {
-      const uint32_t idesc = tc_idesc(TC_FMT_TF32, RC_M, NCP), idesc2 = tc_idesc(TC_FMT_TF32, RC_M, ACW);
+      const uint32_t idesc2 = tc_idesc(TC_FMT_F16, RC_M, ACW);
       for (int c2 = 0; c2 < npass && ok; ++c2) {
         const int j = c2 % NS2, zp = c2 % NZP;
         if (!rc_wait(&zready[zp], (uint32_t)((c2 / NZP) & 1), abort) ||
@@ -619,22 +648,23 @@ __global__ void __launch_bounds__(RC_NT, 1)
         }
         tc_fence_after();
         for (int e = 0; e < 2 && ok; ++e) {
-          const int ch = 2 * c2 + e, g = ch / RC_SEG, b = g & 1;
-          if (ch % RC_SEG == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
+          const int ch = 2 * c2 + e, g = ch / TA_SEGC, b = g & 1;
+          if (ch % TA_SEGC == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
             ok = false;
             break;
           }
           const uint32_t b_hi = sbase + (uint32_t)(j * L::SLOT + e * L::BCH);
           const uint32_t zt = tmem + (uint32_t)(2 * ACW + 64 * zp + 32 * e);
           const uint32_t acc = tmem + (uint32_t)(b * ACW);
+          // four K = 16 steps: 8 Z columns (16 halves) and 256 bytes of B each
 #pragma unroll
-          for (int k = 0; k < RC_KC / 8; ++k) {
+          for (int k = 0; k < TA_KC / 16; ++k) {
             const uint32_t o = (uint32_t)k * 256u;
-            const int first = (ch % RC_SEG == 0 && k == 0) ? 0 : 1;
+            const int first = (ch % TA_SEGC == 0 && k == 0) ? 0 : 1;
             // B_lo's rows follow B_hi's at the next 8-row group: one operand of 2 NCP rows
-            tc_mma_tf32_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_f16_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
           }
-          if (ch % RC_SEG == RC_SEG - 1 || ch == nch - 1) tc_commit(&segdone[b]);
+          if (ch % TA_SEGC == TA_SEGC - 1 || ch == nch - 1) tc_commit(&segdone[b]);
         }
         tc_commit(&sfree[j]);
         tc_commit(&zfree[zp]);
@@ -695,14 +725,14 @@ __global__ void __launch_bounds__(RC_NT, 1)
       return true;
     };
     int flushed = 0;  // segments added into registers
-    // Z of one chunk for this thread's row and 8 K, rounded to TF32, two K
+    // Z of one chunk for this thread's row and 16 K, rounded to FP16, two K
     // per f32x2 instruction: the squared distances to records u and u + 1 in
     // the two halves of a packed register (records interleaved by particle
     // pairs), expanded through the norms (see above)
     auto z_chunk = [&](const uint8_t *recs_ch, uint32_t (&hv)[8]) {
-      const unsigned long long *rs = reinterpret_cast<const unsigned long long *>(recs_ch) + cq * 4 * DP;
+      const unsigned long long *rs = reinterpret_cast<const unsigned long long *>(recs_ch) + cq * 8 * DP;
 #pragma unroll
-      for (int u = 0; u < 8; u += 2) {
+      for (int u = 0; u < 16; u += 2) {
         const unsigned long long *rp = rs + (u / 2) * DP;
         // coordinates d, d + 1 (and the norms in slot D) of the pair in
         // 128-bit shared loads
@@ -725,10 +755,9 @@ __global__ void __launch_bounds__(RC_NT, 1)
         const unsigned long long r2 = f2_fma(m2, dot, f2_add(ni2, nk));
         float r2a, r2b;
         f2_unpack(r2, r2a, r2b);
-        const float za = ex2_approx(-r2a), zb = ex2_approx(-r2b);
-        const float ha = to_tf32(za), hb = to_tf32(zb);
-        hv[u] = __float_as_uint(ha);
-        hv[u + 1] = __float_as_uint(hb);
+        // particles u and u + 1 as two halves of one tensor-memory column
+        const __half2 z2 = __floats2half2_rn(ex2_approx(-r2a), ex2_approx(-r2b));
+        hv[u / 2] = *reinterpret_cast<const uint32_t *>(&z2);
       }
     };
     for (int c2 = 0; c2 < npass && ok; ++c2) {
@@ -750,10 +779,10 @@ __global__ void __launch_bounds__(RC_NT, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&zready[zp]);
-      // segment g - 1 is added into registers part-way through segment g
+      // segment g - 1 is added into registers at the third pass of segment g
       const int ch = 2 * c2;
-      if ((ch + 1) % RC_SEG == RC_FLUSH && ch / RC_SEG >= 1) {
-        if (!flush(ch / RC_SEG - 1)) {
+      if (ch % TA_SEGC == 4 && ch / TA_SEGC >= 1) {
+        if (!flush(ch / TA_SEGC - 1)) {
           ok = false;
           break;
         }
@@ -771,7 +800,8 @@ __global__ void __launch_bounds__(RC_NT, 1)
   tc_fence_after();
   if (warp == 0) tc_dealloc(tmem, TCOLS);
   if (*abort) return;
-  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part);
+  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part,
+                          1.f / TA_BSCALE);
 }
 
 // U1, U2 from the totals of the nsplit K splits of every row tile, summed in

@@ -23,6 +23,7 @@ __device__ __forceinline__ uint32_t tc_idesc(int fmt, int M, int N) {
   return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+constexpr int TC_FMT_F16 = 0;
 constexpr int TC_FMT_BF16 = 1;
 constexpr int TC_FMT_TF32 = 2;
 
@@ -51,6 +52,18 @@ __device__ __forceinline__ void tc_mma_tf32_ta(uint32_t tmem_d, uint32_t a_tmem,
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "r"(a_tmem), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// FP16 operands (kind::f16, K = 16 per instruction) with the A operand in
+// tensor memory: M rows = lanes, each 32-bit column two consecutive K
+// elements (the lower K in the low half); B from shared memory.
+__device__ __forceinline__ void tc_mma_f16_ta(uint32_t tmem_d, uint32_t a_tmem, uint64_t bd, uint32_t idesc,
+                                              int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(tmem_d),
       "r"(a_tmem), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
