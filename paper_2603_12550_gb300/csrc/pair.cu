@@ -33,67 +33,67 @@ __global__ void k_axpy(int n, const float *__restrict__ a, const float *__restri
   }
 
 int vds_prep_2(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_2(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_2(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_2(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_2(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_2(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_2(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_3(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_3(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_3(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_3(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_3(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_3(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_3(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_4(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_4(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_4(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_4(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_4(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_4(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_4(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_6(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_6(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_6(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_6(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_6(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_6(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_6(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_8(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_8(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_8(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_8(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_8(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_8(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_8(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_9(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_9(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_9(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_9(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_9(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_9(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_9(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_10(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_10(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_10(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_10(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_10(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_10(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_10(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_12(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_12(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_12(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_12(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_12(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_12(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_12(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_14(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_14(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_14(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_14(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_14(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_14(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_14(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_15(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_15(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_15(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_15(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_15(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_15(vds_ctx *, const KParams &, const float *, float *);
 int vds_query_15(vds_ctx *, const KParams &, const float *, const float *, int, float *);
 int vds_prep_16(vds_ctx *, const KParams &, const float *, const float *, const float *, float, float *);
-int vds_density_16(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *);
+int vds_density_16(vds_ctx *, const KParams &, float *, bool, const float *, const float *, const float *, const float *, bool);
 int vds_grad_16(vds_ctx *, const KParams &, int, float *, const float *, const float *, const float *, const float *, float *);
 int vds_stress_16(vds_ctx *, const KParams &, const float *, double *, double *);
 int vds_flow_16(vds_ctx *, const KParams &, const float *, float *);
@@ -153,8 +153,8 @@ int pass_prep(vds_ctx *c, const KParams &kp, const float *base, const float *del
 }
 
 int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
-                 const float *ybase, const float *ydelta, const float *qa, const float *qb) {
-#define CALL(DD) vds_density_##DD(c, kp, rho_out, want_energy, ybase, ydelta, qa, qb)
+                 const float *ybase, const float *ydelta, const float *qa, const float *qb, bool expand) {
+#define CALL(DD) vds_density_##DD(c, kp, rho_out, want_energy, ybase, ydelta, qa, qb, expand)
   VDS_DISPATCH_D(kp.D, CALL)
 #undef CALL
 }

@@ -53,10 +53,13 @@ int pass_prep(vds_ctx *c, const KParams &kp, const float *base, const float *del
 //   (1/N) sum_I [kBT (ln rho_I + lnorm) + Psi(y_I)]
 //   + (zeta/2dt)(1/N) sum_I dI^T (A^-1 (x) I) dI,   dI = qa_I - qb_I
 // (the quadratic term only when qa != NULL; qb may be NULL) into scal[SC_E].
-// y_I = ybase_I + ydelta_I (ydelta may be NULL).
+// y_I = ybase_I + ydelta_I (ydelta may be NULL).  expand: large clouds take
+// the squared distances through the records' norms (D + 2 instead of 2D + 1
+// FP32 operations per pair; 1e-6 relative in the kernel values), for the
+// reduced model's refresh cycle; the records must come from pass_prep.
 int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
                  const float *ybase, const float *ydelta, const float *qa,
-                 const float *qb);
+                 const float *qb, bool expand = false);
 
 // Gradient pass (records must hold w from pass_density) and its epilogues.
 enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2, GM_VEL = 3 };

@@ -53,10 +53,22 @@ constexpr int NT_SMALL = 128, RI_SMALL = 1, TJ_SMALL = 64;
 
 // ------------------------------------------------------------- pair kernel
 
-template <int D, int RI, int NT, bool GRAD, int TJK = TJ>
+// EXP (density pass only, records with their squared norm in slot D + 1):
+// the squared distance through the norms, |x|^2 + |y|^2 - 2 x.y, D + 2 FP32
+// operations per pair instead of 2D + 1, with an absolute error of a few
+// units of FP32 rounding of |x|^2 + |y|^2 (1e-6 relative in the kernel value
+// for the bulk of a cloud).  Only the reduced model's refresh cycle takes
+// it; the full-order path keeps the differences its 1e-5 bar needs.
+template <int D>
+struct HasNorm {
+  static constexpr bool value = Rec<D>::DP >= D + 2;
+};
+
+template <int D, int RI, int NT, bool GRAD, int TJK = TJ, bool EXP = false>
 __global__ void __launch_bounds__(NT)
     k_pair(const float *__restrict__ rec, const float *__restrict__ reci, Sched sc,
            double *__restrict__ part, int *__restrict__ err) {
+  static_assert(!EXP || (!GRAD && HasNorm<D>::value), "expanded distances: density pass, norm slot");
   static_assert(TJ % TJK == 0, "j-tiles divide the record padding");
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
@@ -86,6 +98,7 @@ __global__ void __launch_bounds__(NT)
 
   float xi[RI][D];
   float wi[RI];
+  float ni[RI];
   float sum[RI][ACC], cmp[RI][ACC];
   int cur = -1, seg = 0;
   long long it_fail = -1;
@@ -114,6 +127,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
         for (int d = 0; d < D; ++d) xi[k][d] = r[d];
         wi[k] = GRAD ? r[D] : 0.f;
+        ni[k] = EXP ? r[D + 1] : 0.f;
 #pragma unroll
         for (int a = 0; a < ACC; ++a) sum[k][a] = cmp[k][a] = 0.f;
       }
@@ -148,12 +162,20 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
       for (int k = 0; k < RI; ++k) {
         float dd[D];
-        dd[0] = xi[k][0] - xj[0];
-        float r2 = dd[0] * dd[0];
+        float r2;
+        if constexpr (EXP) {
+          float dot = xi[k][0] * xj[0];
 #pragma unroll
-        for (int d = 1; d < D; ++d) {
-          dd[d] = xi[k][d] - xj[d];
-          r2 = fmaf(dd[d], dd[d], r2);
+          for (int d = 1; d < D; ++d) dot = fmaf(xi[k][d], xj[d], dot);
+          r2 = fmaf(-2.f, dot, ni[k] + xj[(D + 1) % DP]);
+        } else {
+          dd[0] = xi[k][0] - xj[0];
+          r2 = dd[0] * dd[0];
+#pragma unroll
+          for (int d = 1; d < D; ++d) {
+            dd[d] = xi[k][d] - xj[d];
+            r2 = fmaf(dd[d], dd[d], r2);
+          }
         }
         const float e = ex2_approx(-r2);
         if constexpr (!GRAD) {
@@ -265,6 +287,13 @@ __global__ void k_prep(int N, int Npad, float c, const float *__restrict__ base,
   }
 #pragma unroll
   for (int d = D; d < DP; ++d) o[d] = 0.f;
+  if constexpr (HasNorm<D>::value) {
+    // the squared norm, rounded as the expanded density pass forms x.x
+    float nrm = o[0] * o[0];
+#pragma unroll
+    for (int d = 1; d < D; ++d) nrm = fmaf(o[d], o[d], nrm);
+    o[D + 1] = nrm;
+  }
   float4 *dst = reinterpret_cast<float4 *>(rec + (size_t)i * DP);
 #pragma unroll
   for (int v = 0; v < DP / 4; ++v) dst[v] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
@@ -611,7 +640,7 @@ __global__ void k_flow(KParams kp, const float *__restrict__ q, float *__restric
 
 // i points: the Ni records at reci (the particles themselves unless a query
 // pass); j points: the N particle records in c->rec.
-template <int D, int RI, int NT, bool GRAD, int TJK = TJ>
+template <int D, int RI, int NT, bool GRAD, int TJK = TJ, bool EXP = false>
 int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   constexpr int DP = Rec<D>::DP;
   constexpr int ACC = GRAD ? D : 1;
@@ -622,10 +651,10 @@ int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   int &occ = occ_dev[c->device < VDS_MAX_DEVICES ? c->device : 0];
   if (occ <= 0 || c->device >= VDS_MAX_DEVICES) {
     // large D needs more than the default 48 KB of dynamic shared memory
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD, TJK>,
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_pair<D, RI, NT, GRAD, TJK, EXP>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int o = 0;
-    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, NT, GRAD, TJK>, NT, smem));
+    VDS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pair<D, RI, NT, GRAD, TJK, EXP>, NT, smem));
     occ = o > 0 ? o : 1;
   }
   sc.TI = TI;
@@ -646,8 +675,8 @@ int launch_pair(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   VDS_TRY(vds_ensure(c, c->part, (size_t)sc.n_itiles * maxseg * TI * ACC * sizeof(double)));
   const int pk = GRAD ? PK_GRADIENT : PK_DENSITY;
   VDS_TRY(vds_time_begin(c, pk));
-  k_pair<D, RI, NT, GRAD, TJK><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, reci, sc,
-                                                                (double *)c->part.ptr, c->err);
+  k_pair<D, RI, NT, GRAD, TJK, EXP><<<sc.G, NT, smem, c->stream>>>((const float *)c->rec.ptr, reci, sc,
+                                                                     (double *)c->part.ptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   VDS_TRY(vds_time_end(c, pk));
   ++c->launches;
@@ -672,21 +701,27 @@ int prep_impl(vds_ctx *c, const KParams &kp, const float *base, const float *del
 // four times the items, so that the last round of the stream-K split is
 // not a large fraction of the pass (N = 10000 at D = 9: 200 and 360 items
 // per pass at 256 records).
-template <int D, bool GRAD>
+// EXP: the expanded distances of the density pass, for large clouds only
+// (small clouds keep the direct form: their passes are latency bound).
+template <int D, bool GRAD, bool EXP = false>
 int launch_pass(vds_ctx *c, int N, Sched &sc, int Ni, const float *reci) {
   constexpr int RI = GRAD ? PairCfg<D>::RI_GRAD : PairCfg<D>::RI_DENS;
   constexpr int NT = GRAD ? PairCfg<D>::NT_GRAD : PairCfg<D>::NT_DENS;
   const long long items = (long long)((Ni + NT * RI - 1) / (NT * RI)) * ((N + TJ - 1) / TJ);
   if (2 * items < c->num_sms) return launch_pair<D, RI_SMALL, NT_SMALL, GRAD, TJ_SMALL>(c, N, sc, Ni, reci);
   if (items < 8LL * c->num_sms) return launch_pair<D, RI, NT, GRAD, TJ_SMALL>(c, N, sc, Ni, reci);
-  return launch_pair<D, RI, NT, GRAD>(c, N, sc, Ni, reci);
+  if constexpr (EXP && !GRAD && HasNorm<D>::value) return launch_pair<D, RI, NT, GRAD, TJ, true>(c, N, sc, Ni, reci);
+  else return launch_pair<D, RI, NT, GRAD>(c, N, sc, Ni, reci);
 }
 
 template <int D>
 int density_impl(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,
-                 const float *ybase, const float *ydelta, const float *qa, const float *qb) {
+                 const float *ybase, const float *ydelta, const float *qa, const float *qb, bool expand) {
   Sched sc;
-  VDS_TRY((launch_pass<D, false>(c, kp.N, sc, kp.N, (const float *)c->rec.ptr)));
+  if (expand)
+    VDS_TRY((launch_pass<D, false, true>(c, kp.N, sc, kp.N, (const float *)c->rec.ptr)));
+  else
+    VDS_TRY((launch_pass<D, false>(c, kp.N, sc, kp.N, (const float *)c->rec.ptr)));
   const int nb = (kp.N + NT_FIN - 1) / NT_FIN;
   VDS_TRY(vds_ensure(c, c->red, (size_t)nb * 4 * sizeof(double)));
   k_dens_finish<D><<<nb, NT_FIN, 0, c->stream>>>(sc, (const double *)c->part.ptr, (float *)c->rec.ptr,
@@ -897,8 +932,9 @@ int flow_impl(vds_ctx *c, const KParams &kp, const float *q, float *qs) {
   }                                                                                           \
   int vds_density_##DD(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy,       \
                        const float *ybase, const float *ydelta, const float *qa,              \
-                       const float *qb) {                                                     \
-    return vds_pair::density_impl<DD>(c, kp, rho_out, want_energy, ybase, ydelta, qa, qb);    \
+                       const float *qb, bool expand) {                                        \
+    return vds_pair::density_impl<DD>(c, kp, rho_out, want_energy, ybase, ydelta, qa, qb,     \
+                                      expand);                                                \
   }                                                                                           \
   int vds_grad_##DD(vds_ctx *c, const KParams &kp, int mode, float *out, const float *ybase,  \
                     const float *ydelta, const float *qa, const float *qb, float *q_io) {     \

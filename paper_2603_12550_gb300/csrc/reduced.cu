@@ -356,7 +356,9 @@ int brownian_dev(vds_ctx *c, const pod_basis *b, const float *P, int N, int D, c
                  float *qt, float *U1, float *U2, double *G1, double *G2) {
   VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
   VDS_TRY(pass_prep(c, kp, qt, nullptr, nullptr, 0.f, nullptr));
-  VDS_TRY(pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr));
+  // the density at the lifted state feeds only the frozen terms (X^B within
+  // 1e-4 of the FP64 oracle): the expanded distances suffice
+  VDS_TRY(pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr, true));
   VDS_TRY(pod_refresh_dev(c, b, N, D, U1, U2));
   VDS_TRY(pod_tsgram(c, b->phi, U1, b->Ns, b->ld, b->r, G1));
   VDS_TRY(pod_tsgram(c, b->phi, U2, b->Ns, b->ld, b->r, G2));
@@ -559,9 +561,11 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     c->launches += 2;
     bool exact = false;
     {
-      // full density (every 1/rho_J enters S_I), gradient of the checked rows
+      // full density (every 1/rho_J enters S_I), gradient of the checked rows;
+      // the density through the expanded distances (1e-6 relative, against a
+      // check threshold of order 0.1 and a fallback step judged at 1e-3)
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
-      VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr));
+      VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr, true));
       // compact exact S of the checked rows (after the FP64 segment partials)
       // in the shared scratch, taken afresh at every check
       const size_t rows_bytes = ((size_t)nrows * D * sizeof(float) + 255) / 256 * 256;
