@@ -52,7 +52,8 @@ def _args():
                     help="take the row-split path also with one rank (a one-GPU check of that path)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary measurements (implicit step, POD, batched, surrogate)")
-    ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,surrogate,paper_tables,surrogate_n262144",
+    ap.add_argument("--extras", default="implicit,dumbbell2d,pod,batched,convect,surrogate,paper_tables,"
+                                        "surrogate_n262144",
                     help="comma-separated subset of the secondary measurements to run")
     return ap.parse_args()
 
@@ -255,7 +256,39 @@ def _extras(ctx, vds, inputs, torch, wl, h, stream, which):
         out["dumbbell2d"] = _extra_dumbbell2d(ctx, vds, inputs, torch, timed)
     if "paper_tables" in which:
         out["paper_tables"] = _extra_paper_tables(ctx, vds, inputs, torch, timed)
+    if "convect" in which:
+        out["convect"] = _extra_convect(ctx, vds, torch)
     return out
+
+
+def _extra_convect(ctx, vds, torch):
+    """vds_convect on a grid of 8 x 8 x 8 ensembles of 16384 three-bead chains
+    (D = 6): 201 MB of field, more than L2, so every step reads it from HBM and
+    writes it back; the HBM roofline is one read and one write of the field."""
+    nx = ny = nz = 8
+    G, M = nx * ny * nz, 16384 * 6
+    q = torch.randn((G, M), device="cuda")
+    out = torch.empty_like(q)
+    u = torch.randn((G, 3), device="cuda") * 0.5
+    dx, dt = (0.5, 0.5, 0.5), 0.01
+    for _ in range(3):
+        ctx.vds_convect(q, out, (nx, ny, nz), u, dx, dt, 0)
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(reps):
+        a, b = (q, out) if k % 2 == 0 else (out, q)
+        ctx.vds_convect(a, b, (nx, ny, nz), u, dx, dt, 0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 2.0 * G * M * 4
+    peaks, src = _peaks()
+    return {"nodes": G, "values_per_node": M, "ms": ms, "algorithmic_bytes": nbytes,
+            "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": nbytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "peak_source": src}}
 
 
 # The paper's Sec. 3 tables at P = 1000, delta t = 1e-3, t in [0, 6] (its

@@ -463,6 +463,7 @@ __device__ __forceinline__ float tanh_approx(float x) {
   return y;
 }
 
+
 // Wait that also gives up as soon as another role has aborted.
 __device__ __forceinline__ bool fwait(uint64_t *bar, uint32_t parity, volatile int *abort) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -540,9 +541,11 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_init(&empty[k], 1);
     }
     mbar_init(&afull, 1);
-    for (int k = 0; k < 2; ++k) mbar_init(&accfree[k], F_ET);
-    for (int k = 0; k < 4; ++k) mbar_init(&hb[k], F_ET);
-    mbar_init(&a0r, F_ET);
+    // one arrival per epilogue warp (its lanes synchronised first): 16
+    // arrivals per barrier phase instead of 512 atomics on one word
+    for (int k = 0; k < 2; ++k) mbar_init(&accfree[k], F_EW);
+    for (int k = 0; k < 4; ++k) mbar_init(&hb[k], F_EW);
+    mbar_init(&a0r, F_EW);
     mbar_init(&fin, 1);
     s_abort = 0;
     fence_mbar_init();
@@ -664,11 +667,15 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       *reinterpret_cast<uint4 *>(h + ag * 128) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
       *reinterpret_cast<uint4 *>(h + (ag + 4) * 128) = make_uint4(0, 0, 0, 0);
     };
+    auto warp_arrive = [&](uint64_t *bar) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar);
+    };
     if (nk > 0) {
       fetch_x(tile_of(0));
       put_a0();
       fence_proxy_async_smem();
-      mbar_arrive(&a0r);
+      warp_arrive(&a0r);
     }
     bool ok = true;
     for (int i = 0; i < nk && ok; ++i)
@@ -709,14 +716,14 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             *reinterpret_cast<uint4 *>(hk + 128) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             // this K-chunk is the next layer's operand as soon as every thread wrote it
             fence_proxy_async_smem();
-            mbar_arrive(&hb[kc]);
+            warp_arrive(&hb[kc]);
           }
         } else {
           // the output layer's MMAs have read the activations: the next tile's input may go in
           if (next) {
             put_a0();
             fence_proxy_async_smem();
-            mbar_arrive(&a0r);
+            warp_arrive(&a0r);
           }
           if (cp == 0) {
             uint32_t v[16];
@@ -731,7 +738,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
           }
         }
         tc_fence_before();
-        mbar_arrive(&accfree[b]);
+        warp_arrive(&accfree[b]);
       }
     if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
   }

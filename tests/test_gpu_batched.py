@@ -221,3 +221,30 @@ def test_batched_implicit_fene_matches_oracle(orc, vds, ctx):
         q_o, _, _ = orc.implicit_steps(q.astype(np.float64), po, 3)
         assert np.max(np.abs(q_all[off:off + n] - q_o)) <= 1e-5 * np.max(np.abs(q_o)), e
         off += n
+
+
+def test_batched_workload_200_implicit_steps(orc, vds, ctx):
+    # the batched workload itself: 512 three-bead Hookean chains (D = 6),
+    # N_e = round(2^U(10,14)) and shear rates 10^U(-1,1) from seed 0, median-rule
+    # h per ensemble, dt = 0.005, 200 implicit steps of the whole batch in one
+    # call; the four smallest ensembles against the FP64 oracle's 200 implicit
+    # steps on each alone (stress within 1e-3, connectors within 1e-4 of their
+    # scale: the GPU minimiser stops at tol 1e-6, the oracle's at 1e-10)
+    sizes, rates = inputs.ensemble_sizes(512, seed=0)
+    qs = [inputs.equilibrium_cloud(int(n), NB, S, seed=1000 + e) for e, n in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    q_all = torch.from_numpy(np.concatenate(qs)).cuda()
+    hs = np.array([ctx.vds_bandwidth(q_all[off[e]:off[e + 1]], 0) for e in range(len(sizes))])
+    kaps = np.stack([inputs.shear_kappa(S, r) for r in rates])
+    b = _batch(vds, ctx, sizes, hs, kaps, kBT=1.0, zeta=4.0, dt=0.005, scheme=1, tol=1e-6, jfloor=1e-9)
+    b.step(q_all, 200)
+    q_all = q_all.cpu().numpy()
+    for e in np.argsort(sizes, kind="stable")[:4]:
+        po = orc.params(NB, S, h=hs[e], dt=0.005, kappa=kaps[e])
+        q_o, _, _ = orc.implicit_steps(qs[e].astype(np.float64), po, 200)
+        got = q_all[off[e]:off[e + 1]].astype(np.float64)
+        assert np.max(np.abs(got - q_o)) <= 1e-4 * np.max(np.abs(q_o)), e
+        tau_o, _ = orc.stress(q_o, po)
+        tau, _ = orc.stress(got, po)
+        assert np.linalg.norm(tau - tau_o) <= 1e-3 * np.linalg.norm(tau_o), e
+    b.free()

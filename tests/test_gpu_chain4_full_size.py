@@ -5,9 +5,11 @@ configurations the benchmark times:
 - final-time stress: explicit runs compared, at every stored checkpoint, with
   the oracle's trajectories written by tests/golden/make_chain4_trajectories.py
   (N = 16384 over t in [0, 5], i.e. 1000 steps, and N = 65536 over 100 steps,
-  Hookean and FENE b = 50): the paper's stress tau and the second moments
+  Hookean and FENE b = 50; and the 3D dumbbell, N = 16384, shear rates 0.1, 1
+  and 10 over t in [0, 5]): the paper's stress tau and the second moments
   within 1e-3 relative (Frobenius), and every 256th particle's connectors;
-  the bandwidth of the median rule (Eq. model_bandwidth) against the oracle's;
+  the bandwidth (median rule of Eq. model_bandwidth, or Silverman for the
+  dumbbell) against the oracle's;
 - the reduced path (Sec. 2.4) at N = 65536, r = 10: X^B1 and X^B2 at a lifted
   state within 1e-4 relative, and 61 frozen-term steps refreshed every 60
   (so the run crosses one refresh) within 1e-4 relative on P;
@@ -62,7 +64,8 @@ def _rel(a, b):
 # ------------------------------------------------------- final-time stress
 
 @pytest.mark.parametrize("name", ["chain4_n16384_hookean_T5", "chain4_n65536_hookean_s100",
-                                  "chain4_n65536_fene50_s100"])
+                                  "chain4_n65536_fene50_s100", "dumbbell3d_n16384_rate0.1_T5",
+                                  "dumbbell3d_n16384_rate1_T5", "dumbbell3d_n16384_rate10_T5"])
 def test_final_time_stress_matches_oracle_trajectory(vds, ctx, name):
     with open(os.path.join(GOLDEN, name + ".json")) as f:
         gold = json.load(f)
@@ -70,8 +73,10 @@ def test_final_time_stress_matches_oracle_trajectory(vds, ctx, name):
     fene = gold["spring"] == 1
     q32 = inputs.equilibrium_cloud(N, nb, s, seed=gold["seed"], fene_b=gold["b"] if fene else None)
     q = _dev(q32)
-    # the GPU's median over FP32 pair distances against the oracle's FP64 one
-    assert ctx.vds_bandwidth(q, rule=0) == pytest.approx(gold["h"], rel=1e-6)
+    # the GPU's bandwidth rule (median over FP32 pair distances, or Silverman)
+    # against the oracle's FP64 one
+    rule = 1 if gold.get("bandwidth") == "silverman" else 0
+    assert ctx.vds_bandwidth(q, rule=rule) == pytest.approx(gold["h"], rel=1e-6)
     p = vds.params(nb, s, H=gold["H"], kBT=gold["kBT"], zeta=gold["zeta"], h=gold["h"], dt=gold["dt"],
                    kappa=inputs.shear_kappa(s, gold["rate"]), spring=gold["spring"], b=gold["b"],
                    scheme=0)
