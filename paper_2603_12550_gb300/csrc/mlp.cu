@@ -3,17 +3,16 @@
 // activations, FP32 accumulation, trained by denoising score matching with
 // Adam; forward and backward GEMMs on the 5th-generation tensor cores.
 //
-// GEMM (k_gemm_tn): C[M x N] = A[M x K] . B[N x K]^T, A and B row-major BF16
-// (K contiguous).  One CTA per 128-row tile (and per K split), 4 warps.  K is
-// consumed in chunks of 64: all threads copy the A (128 x 64) and B (N x 64)
-// chunks into shared memory in the canonical K-major layout without swizzle
-// (8-row x 16-byte core matrices; 128 B between core matrices along K, 1024 B
-// between 8-row groups), one thread issues four tcgen05.mma (M=128, N, K=16,
-// kind::f16 with BF16 inputs) accumulating in tensor memory and commits them
-// to an mbarrier; two chunk buffers alternate.  The epilogue reads the
-// accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31 = rows) and
-// applies the layer's bias/activation, writing row-major and, where the
-// backward pass needs it, transposed copies.
+// GEMM (k_gemm_tma): C[M x N] = A[M x K] . B[N x K]^T, A and B row-major
+// BF16 (K contiguous).  One CTA per 128-row tile (and per K split), 8 warps.
+// K is consumed in chunks of 64: one thread loads the A (128 x 64) and B
+// (N x 64) chunks with tensor-map TMA copies (128-byte swizzle) into a ring of
+// stages, one thread issues four tcgen05.mma (M=128, N, K=16, kind::f16 with
+// BF16 inputs) per chunk accumulating in tensor memory and frees the stage
+// with a commit.  The epilogue reads the accumulator with tcgen05.ld (warp w
+// owns lanes 32 (w % 4).. = rows) and applies the layer's bias/activation,
+// writing row-major and, where the backward pass needs it, transposed copies.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -64,91 +63,83 @@ constexpr int GBN = 128;   // columns of C per CTA
 constexpr int GNT = 256;   // threads: warps w and w + 4 share TMEM lanes 32 (w % 4), split the columns
 constexpr int GSTAGE = GM * KC * 2 + GBN * KC * 2;  // bytes per stage (A 16 KB + B <= 16 KB)
 
-// Asynchronous copy of a rows_tile x 64 chunk (rows beyond nvalid zero-filled)
-// into the K-major canonical layout: byte offset of element (r, k) is
-// (r/8)*1024 + (k/8)*128 + (r%8)*16 + (k%8)*2.  Consecutive lanes take
-// consecutive rows inside an 8-row group, so one warp writes 512 contiguous
-// bytes (no bank conflicts).
-__device__ __forceinline__ void load_chunk_async(uint32_t dst, const bf16 *__restrict__ src, int ld, int row0,
-                                                 int nvalid, int rows_tile, int k0) {
-  for (int idx = threadIdx.x; idx < rows_tile * 8; idx += blockDim.x) {
-    const int r8 = idx & 7, c = (idx >> 3) & 7, g = idx >> 6;
-    const int r = g * 8 + r8;
-    const bool ok = r < nvalid;
-    const bf16 *p = src + (size_t)(row0 + (ok ? r : 0)) * ld + k0 + c * 8;
-    cp_async16(dst + g * 1024 + c * 128 + r8 * 16, p, ok);
-  }
-}
-
-// C tile [128 rows x BN cols] = A[m0:, K-split] . B[n0:n0+BN, K-split]^T,
-// GS chunks of K in flight (2 when K is short: three CTAs fit on an SM).
+// C tile [128 rows x BN cols] = A[m0:, K-split] . B[n0:n0+BN, K-split]^T.
+// A and B come in by tensor-map TMA loads (2-D boxes of 64 K x 128 (or BN)
+// rows, 128-byte swizzled, rows past the tensor zero-filled) issued by one
+// thread into a GS-stage ring; one thread issues four tcgen05.mma per chunk
+// (M=128, N=BN, K=16, kind::f16 with BF16 inputs) and frees each stage with a
+// commit; all 8 warps then run the epilogue (warps w and w + 4 share tensor
+// memory lanes 32 (w % 4).., splitting the columns).
 template <int GS>
 __global__ void __launch_bounds__(GNT)
-    k_gemm_tn(const bf16 *__restrict__ A, int lda, const bf16 *__restrict__ B, int ldb, int N, int Ksplit,
-              Epi ep, int *err) {
+    k_gemm_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int N,
+               int Ksplit, int boxB, Epi ep, int *err) {
   extern __shared__ __align__(1024) uint8_t gsm[];
-  __shared__ __align__(8) uint64_t bars[GS];
+  __shared__ __align__(8) uint64_t full[GS], empty[GS], done;
   __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * GM;
   const int kbase = blockIdx.y * Ksplit;
   const int n0 = blockIdx.z * GBN;
   const int BN = min(GBN, N - n0);
-  if (warp == 0) {
-    tc_alloc(&s_tmem, TMEM_COLS);
-  }
+  if (warp == 0) tc_alloc(&s_tmem, TMEM_COLS);
   if (tid == 0) {
-    for (int k = 0; k < GS; ++k) mbar_init(&bars[k], 1);
+    for (int k = 0; k < GS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1);
+    }
+    mbar_init(&done, 1);
+    s_abort = 0;
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = tc_idesc(TC_FMT_BF16, GM, BN);
   const int nch = Ksplit / KC;
-  const int avalid = min(GM, ep.rows - m0);
   const uint32_t sbase = smem_u32(gsm);
-  auto issue_loads = [&](int ch) {
-    if (ch < nch) {
-      const uint32_t st = sbase + (ch % GS) * GSTAGE;
-      load_chunk_async(st, A, lda, m0, avalid, GM, kbase + ch * KC);
-      load_chunk_async(st + GM * KC * 2, B, ldb, n0, BN, BN, kbase + ch * KC);
-    }
-    cp_async_commit();
-  };
-  for (int ch = 0; ch < GS - 1; ++ch) issue_loads(ch);
-  bool ok = true;
-  for (int ch = 0; ch < nch; ++ch) {
-    cp_async_wait<GS - 2>();
-    fence_proxy_async_smem();
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t a0 = sbase + (ch % GS) * GSTAGE, b0 = a0 + GM * KC * 2;
-#pragma unroll
-      for (int k = 0; k < KC / 16; ++k)
-        tc_mma_bf16(tmem, tc_sdesc(a0 + k * 256), tc_sdesc(b0 + k * 256), idesc, (ch > 0 || k > 0) ? 1 : 0);
-      tc_commit(&bars[ch % GS]);
-    }
-    // the stage refilled next was read by the MMAs of chunk ch-1
-    if (ch >= 1 && ch + GS - 1 < nch) {
-      const int pc = ch - 1;
-      const bool got = mbar_wait_bounded(&bars[pc % GS], (uint32_t)((pc / GS) & 1), VDS_WAIT_LIMIT_NS);
-      if (__syncthreads_or(!got)) {
-        ok = false;
+  const uint32_t txbytes = (uint32_t)(GM * KC * 2 + boxB * KC * 2);
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------ TMA producer
+    int ch = 0;
+    for (; ch < nch; ++ch) {
+      const int st = ch % GS;
+      if (ch >= GS && !mbar_wait_bounded(&empty[st], (uint32_t)((ch / GS - 1) & 1), VDS_WAIT_LIMIT_NS)) {
+        s_abort = 1;
         break;
       }
+      const uint32_t a0 = sbase + st * GSTAGE, b0 = a0 + GM * KC * 2;
+      mbar_arrive_expect_tx(&full[st], txbytes);
+      tma_load_2d(a0, &tmA, kbase + ch * KC, m0, &full[st]);
+      tma_load_2d(b0, &tmB, kbase + ch * KC, n0, &full[st]);
     }
-    issue_loads(ch + GS - 1);
+    // the loads still in flight land before the CTA may exit
+    for (int k = ch > GS ? ch - GS : 0; k < ch; ++k)
+      mbar_wait_bounded(&full[k % GS], (uint32_t)((k / GS) & 1), VDS_WAIT_LIMIT_NS);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------------------------ MMA issue
+    const uint32_t idesc = tc_idesc(TC_FMT_BF16, GM, BN);
+    for (int ch = 0; ch < nch; ++ch) {
+      const int st = ch % GS;
+      if (!mbar_wait_bounded(&full[st], (uint32_t)((ch / GS) & 1), VDS_WAIT_LIMIT_NS)) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = sbase + st * GSTAGE, b0 = a0 + GM * KC * 2;
+#pragma unroll
+      for (int k = 0; k < KC / 16; ++k)
+        tc_mma_bf16(tmem, tc_sdesc_sw128(a0 + k * 32), tc_sdesc_sw128(b0 + k * 32), idesc,
+                    (ch > 0 || k > 0) ? 1 : 0);
+      tc_commit(&empty[st]);
+    }
+    // every MMA issued is complete before the epilogue reads the accumulator
+    tc_commit(&done);
   }
-  cp_async_wait<0>();
-  if (ok && nch > 0) {
-    const int last = nch - 1;
-    const bool got = mbar_wait_bounded(&bars[last % GS], (uint32_t)((last / GS) & 1), VDS_WAIT_LIMIT_NS);
-    if (__syncthreads_or(!got)) ok = false;
-  }
+  __syncwarp();
+  const bool got = mbar_wait_bounded(&done, 0, VDS_WAIT_LIMIT_NS);
+  const bool ok = !__syncthreads_or(!got || s_abort);
   tc_fence_after();
   if (!ok) {
     if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
@@ -791,22 +782,62 @@ struct Dev {
   }
 };
 
+// Tensor map of a row-major BF16 matrix (rows x K used, row stride ld
+// elements) in boxes of 64 K x box_rows rows, 128-byte swizzled, rows and K
+// past the matrix read as zeros.
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library does not link the driver library itself, so it loads without one)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int make_tmap(CUtensorMap *m, const bf16 *base, int rows, int K, int ld, int box_rows) {
+  if (((uintptr_t)base & 15) != 0 || (ld * 2) % 16 != 0) return VDS_EARG;
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) return VDS_ECUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(base), dims,
+                                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? VDS_OK : VDS_ECUDA;
+}
+
 int gemm(vds_ctx *c, const bf16 *A, int lda, const bf16 *B, int ldb, int rows, int N, int K, int splits,
          const Epi &ep) {
   if (N % 16 != 0 || N < 16 || N > 256 || K % (KC * splits) != 0) return VDS_EARG;
   // per device: the shared-memory attribute is a property of the function on that device
   static bool attr[VDS_MAX_DEVICES] = {};
   if (c->device >= VDS_MAX_DEVICES || !attr[c->device]) {
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * GSTAGE));
-    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * GSTAGE));
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * GSTAGE));
+    VDS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tma<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * GSTAGE));
     if (c->device < VDS_MAX_DEVICES) attr[c->device] = true;
   }
+  const int boxB = N < GBN ? N : GBN;
+  CUtensorMap tA, tB;
+  VDS_TRY(make_tmap(&tA, A, rows, K, lda, GM));
+  VDS_TRY(make_tmap(&tB, B, N, K, ldb, boxB));
   dim3 grid((rows + GM - 1) / GM, splits, (N + GBN - 1) / GBN);
   const int nch = K / splits / KC;
   if (nch <= 4)
-    k_gemm_tn<2><<<grid, GNT, 2 * GSTAGE, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
+    k_gemm_tma<2><<<grid, GNT, 2 * GSTAGE, c->stream>>>(tA, tB, N, K / splits, boxB, ep, c->err);
   else
-    k_gemm_tn<4><<<grid, GNT, 4 * GSTAGE, c->stream>>>(A, lda, B, ldb, N, K / splits, ep, c->err);
+    k_gemm_tma<4><<<grid, GNT, 4 * GSTAGE, c->stream>>>(tA, tB, N, K / splits, boxB, ep, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;

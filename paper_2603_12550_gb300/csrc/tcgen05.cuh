@@ -16,6 +16,28 @@ __device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr) {
          (1ull << 46);
 }
 
+// Shared-memory matrix descriptor of a K-major operand tile written by a
+// tensor-map TMA load with 128-byte swizzling: rows of 128 bytes (64 BF16
+// along K), 8-row groups 1024 bytes apart (SBO), the tile 1024-byte aligned;
+// layout type SWIZZLE_128B (2) in bits 61-63.  Within the swizzle atom a K
+// offset is a plain byte offset of the start address (16 BF16 = 32 bytes).
+__device__ __forceinline__ uint64_t tc_sdesc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46) | (2ull << 61);
+}
+
+// 2-D tiled bulk tensor load (TMA engine) global -> shared with 128-byte
+// swizzling as the tensor map states; completion as transaction bytes on
+// bar.  x (innermost, elements) must be 16-byte aligned: a multiple of 8 for
+// 16-bit types; coordinates past the tensor fill with zeros.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Instruction descriptor: D = F32 (bits 4-5 = 1), A and B format at bits 7-9
 // and 10-12 (kind::f16: BF16 = 1; kind::tf32: TF32 = 2), both K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
