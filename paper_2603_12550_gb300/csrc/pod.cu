@@ -6,9 +6,12 @@
 //                        (3xTF32 split of every snapshot value) and FP64
 //                        sums across 512-row segments (gram_tc.cu)
 //   C = V Lambda V^T     two-sided cyclic Jacobi in FP64 with the round-robin
-//                        ordering: each round computes its M/2 disjoint
-//                        rotations once, then applies them in one launch
-//                        (block (a,b) of A' = R_a^T A_ab R_b)
+//                        ordering, one launch per round: each CTA computes
+//                        the few of the round's M/2 disjoint rotations its
+//                        tile needs (angles to FP32 accuracy, orthogonal to
+//                        FP64 rounding), then applies them (blocks (a,b) of
+//                        A' = R_a^T A_ab R_b, a <= b, with their mirror
+//                        images; columns of V' = V R)
 //   r                    energy rule on the sorted eigenvalues (FP64 prefix
 //                        sums in descending order), or r_fixed
 //   Phi = X V_r Lambda_r^(-1/2)   FP64 accumulation, stored FP32
@@ -46,81 +49,155 @@ __device__ __forceinline__ void jac_pair(int a, int rnd, int Mp, int &p, int &q)
   }
 }
 
-// Rotation R = [[c, s], [-s, c]] on (p, q) with R^T A R zeroing the (p, q)
-// entry (classical Jacobi with the smaller rotation angle).
-__device__ __forceinline__ void jac_rot(const double *A, int M, int p, int q, double &c, double &s) {
-  c = 1.0;
-  s = 0.0;
-  if (q >= M) return;
+// Rotation R = [[c, s], [-s, c]] on (p, q), the classical Jacobi rotation
+// (the smaller angle, R^T A R zeroing the (p, q) entry) with its angle taken
+// to FP32 accuracy: tan(theta) comes from the FP64 entries scaled by a power
+// of two and rounded to FP32 (the FP64 divide and square root of this GPU are
+// slow and on the critical path of every round); c and s are then promoted
+// and normalised in FP64 by the series (c^2 + s^2)^(-1/2) = 1 - d/2 + 3d^2/8,
+// d = c^2 + s^2 - 1 (|d| ~ 1e-7, the truncation ~ d^3 is below FP64
+// rounding), so R is orthogonal to FP64 rounding and R^T A R a similarity.
+// The (p, q) entry drops to ~1e-7 of itself instead of to zero; the next
+// sweeps take it further, at the pace of the exact rotation's convergence.
+__device__ __forceinline__ double2 jac_rot(const double *A, int M, int p, int q) {
+  if (q >= M) return make_double2(1.0, 0.0);
   const double apq = A[(size_t)p * M + q];
-  if (apq == 0.0) return;
-  const double app = A[(size_t)p * M + p], aqq = A[(size_t)q * M + q];
-  if (fabs(apq) <= 1e-300 * (fabs(app) + fabs(aqq))) return;
-  const double theta = (aqq - app) / (2.0 * apq);
-  double t;
-  if (fabs(theta) > 1e150) t = 0.5 / theta;
-  else t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-  c = 1.0 / sqrt(t * t + 1.0);
-  s = t * c;
+  if (apq == 0.0) return make_double2(1.0, 0.0);
+  const double dqp = A[(size_t)q * M + q] - A[(size_t)p * M + p];
+  // scale both by 2^-e, e the exponent of apq (|apq 2^-e| in [1, 2)); the
+  // scale is built from its bits (e in [-1022, 1022]; outside, apq is
+  // subnormal or within a factor 2 of overflow, and the pair is left alone)
+  const int e = ((__double2hiint(apq) >> 20) & 0x7ff) - 1023;
+  if (e < -1022 || e > 1022) return make_double2(1.0, 0.0);
+  const double sc = __hiloint2double((1023 - e) << 20, 0);
+  const float a32 = (float)(apq * sc), d32 = (float)(dqp * sc);
+  const float theta = d32 / (2.f * a32);
+  float t;
+  if (fabsf(theta) > 1e18f) t = 0.5f / theta;  // also theta = +-inf: t = 0
+  else t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+  const float cf = 1.f / sqrtf(t * t + 1.f), sf = t * cf;
+  const double c = cf, s = sf;
+  const double d = (c * c + s * s) - 1.0;
+  const double f = 1.0 + d * (-0.5 + 0.375 * d);
+  return make_double2(c * f, s * f);
 }
 
-// The M/2 disjoint rotations of round `rnd`, computed once from the current A
-// (rot[a] = (c, s) for pair a of the round-robin ordering).
-__global__ void __launch_bounds__(256)
-    k_jacobi_rots(const double *__restrict__ A, int M, int Mp, int rnd, double2 *__restrict__ rot) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= Mp / 2) return;
-  int p, q;
-  jac_pair(a, rnd, Mp, p, q);
-  double c, s;
-  jac_rot(A, M, p, q, c, s);
-  rot[a] = make_double2(c, s);
-}
+constexpr int JR_NT = 256;  // threads per CTA
+constexpr int JT = 16;       // pairs per tile side
+constexpr int JV_ROWS = 32;  // rows of V per tile (two per thread)
 
-// A2 = R^T A R on every 2x2 block (rows of pair a, columns of pair b) and
-// V2 = V R, with the rotations of the round from k_jacobi_rots.
-__global__ void __launch_bounds__(256)
+// One round of the cyclic Jacobi sweep in one launch.  The work is cut into
+// tiles that need few rotations, so each CTA computes only those (into
+// shared memory, one per thread, every CTA the same values for a pair):
+//   CTAs [0, nAt): the JT x JT tiles (ta, tb), ta <= tb, of 2x2 blocks (a, b)
+//     of A2 = R^T A R (rows of pair a, columns of pair b); a thread takes one
+//     block with a <= b and writes it with its mirror image (A2 exactly
+//     symmetric; a diagonal block writes its (p, q) value to (q, p));
+//   CTAs [nAt, nAt + nVt): the JV_ROWS x JT tiles (rows i, pairs b) of
+//     V2 = V R, two rows per thread.
+__global__ void __launch_bounds__(JR_NT)
     k_jacobi_round(const double *__restrict__ A, double *__restrict__ A2, const double *__restrict__ V,
-                   double *__restrict__ V2, int M, int Mp, int rnd, const double2 *__restrict__ rot) {
-  const int H = Mp / 2;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long nA = (long)H * H;
-  if (idx < nA) {
-    const int a = (int)(idx / H), b = (int)(idx - (long)(idx / H) * H);
-    int p, q, p2, q2;
-    jac_pair(a, rnd, Mp, p, q);
-    jac_pair(b, rnd, Mp, p2, q2);
-    const double2 ra = rot[a], rb = rot[b];
-    const double ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
+                   double *__restrict__ V2, int M, int Mp, int rnd, int nT, int nAt) {
+  __shared__ double2 rot[2 * JT];
+  constexpr int VR = JV_ROWS / (JR_NT / JT);  // rows of V per thread
+  const int H = Mp / 2, tid = threadIdx.x;
+  int bt = blockIdx.x;
+  // Each thread loads its entries first; the rotations are computed while
+  // those loads are in flight (the round's critical path is one L2 round
+  // trip plus the rotation arithmetic, not their sum).
+  if (bt < nAt) {
+    int ta = 0;
+    while (bt >= nT - ta) {  // upper-triangle tile index -> (ta, tb)
+      bt -= nT - ta;
+      ++ta;
+    }
+    const int tb = ta + bt;
+    const int a = ta * JT + tid / JT, b = tb * JT + tid % JT;
+    const bool act = a < H && b < H && a <= b;
+    int p = 0, q = 0, p2 = 0, q2 = 0;
+    double x00 = 0.0, x01 = 0.0, x10 = 0.0, x11 = 0.0;
     auto get = [&](int i, int j) -> double { return (i < M && j < M) ? A[(size_t)i * M + j] : 0.0; };
-    const double x00 = get(p, p2), x01 = get(p, q2), x10 = get(q, p2), x11 = get(q, q2);
+    if (act) {
+      jac_pair(a, rnd, Mp, p, q);
+      jac_pair(b, rnd, Mp, p2, q2);
+      x00 = get(p, p2);
+      x01 = get(p, q2);
+      x10 = get(q, p2);
+      x11 = get(q, q2);
+    }
+    if (tid < 2 * JT) {
+      const int ar = (tid < JT ? ta : tb) * JT + (tid % JT);
+      double2 r = make_double2(1.0, 0.0);
+      if (ar < H) {
+        int pr, qr;
+        jac_pair(ar, rnd, Mp, pr, qr);
+        r = jac_rot(A, M, pr, qr);
+      }
+      rot[tid] = r;
+    }
+    __syncthreads();
+    if (!act) return;
+    const double2 ra = rot[tid / JT], rb = rot[JT + tid % JT];
+    const double ca = ra.x, sa = ra.y, cb = rb.x, sb = rb.y;
     const double t00 = ca * x00 - sa * x10, t01 = ca * x01 - sa * x11;
     const double t10 = sa * x00 + ca * x10, t11 = sa * x01 + ca * x11;
-    double y00 = t00 * cb - t01 * sb, y01 = t00 * sb + t01 * cb;
-    double y10 = t10 * cb - t11 * sb, y11 = t10 * sb + t11 * cb;
+    const double y00 = t00 * cb - t01 * sb, y01 = t00 * sb + t01 * cb;
+    const double y10 = t10 * cb - t11 * sb, y11 = t10 * sb + t11 * cb;
+    auto put = [&](int i, int j, double v) {
+      if (i < M && j < M) {
+        A2[(size_t)i * M + j] = v;
+        A2[(size_t)j * M + i] = v;
+      }
+    };
     if (a == b) {
-      y01 = 0.0;
-      y10 = 0.0;
+      put(p, p, y00);
+      put(p, q, y01);
+      put(q, q, y11);
+    } else {
+      put(p, p2, y00);
+      put(p, q2, y01);
+      put(q, p2, y10);
+      put(q, q2, y11);
     }
-    if (p < M && p2 < M) A2[(size_t)p * M + p2] = y00;
-    if (p < M && q2 < M) A2[(size_t)p * M + q2] = y01;
-    if (q < M && p2 < M) A2[(size_t)q * M + p2] = y10;
-    if (q < M && q2 < M) A2[(size_t)q * M + q2] = y11;
   } else {
-    const long v = idx - nA;
-    if (v >= (long)M * H) return;
-    const int i = (int)(v / H), b = (int)(v - (long)(v / H) * H);
-    int p2, q2;
-    jac_pair(b, rnd, Mp, p2, q2);
-    const double2 rb = rot[b];
-    const double cb = rb.x, sb = rb.y;
-    if (q2 >= M) {
-      if (p2 < M) V2[(size_t)i * M + p2] = V[(size_t)i * M + p2];
-      return;
+    bt -= nAt;
+    const int tb = bt % nT, ti = bt / nT;
+    const int b = tb * JT + tid % JT;
+    int p2 = 0, q2 = 0;
+    double vp[VR], vq[VR];
+    if (b < H) jac_pair(b, rnd, Mp, p2, q2);
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      const int i = ti * JV_ROWS + tid / JT + k * (JR_NT / JT);
+      const bool ok = b < H && i < M;
+      vp[k] = (ok && p2 < M) ? V[(size_t)i * M + p2] : 0.0;
+      vq[k] = (ok && q2 < M) ? V[(size_t)i * M + q2] : 0.0;
     }
-    const double vp = V[(size_t)i * M + p2], vq = V[(size_t)i * M + q2];
-    V2[(size_t)i * M + p2] = vp * cb - vq * sb;
-    V2[(size_t)i * M + q2] = vp * sb + vq * cb;
+    if (tid < JT) {
+      const int br = tb * JT + tid;
+      double2 r = make_double2(1.0, 0.0);
+      if (br < H) {
+        int pr, qr;
+        jac_pair(br, rnd, Mp, pr, qr);
+        r = jac_rot(A, M, pr, qr);
+      }
+      rot[tid] = r;
+    }
+    __syncthreads();
+    if (b >= H) return;
+    const double2 rb = rot[tid % JT];
+    const double cb = rb.x, sb = rb.y;
+#pragma unroll
+    for (int k = 0; k < VR; ++k) {
+      const int i = ti * JV_ROWS + tid / JT + k * (JR_NT / JT);
+      if (i >= M) break;
+      if (q2 >= M) {  // the dummy index of odd M: column p2 is carried over
+        if (p2 < M) V2[(size_t)i * M + p2] = vp[k];
+        continue;
+      }
+      V2[(size_t)i * M + p2] = vp[k] * cb - vq[k] * sb;
+      V2[(size_t)i * M + q2] = vp[k] * sb + vq[k] * cb;
+    }
   }
 }
 
@@ -130,16 +207,19 @@ __global__ void k_identity(double *V, int M) {
 }
 
 // off-diagonal and total squared Frobenius norms -> scal[SC_AUX], scal[SC_AUX+1]
+// (M <= 2048: int indices; the last CTA sums the per-CTA partials in a fixed
+// order, one warp, lanes striding over the CTAs, then a fixed shuffle tree)
 __global__ void __launch_bounds__(256)
     k_offnorm(const double *__restrict__ A, int M, double *red, unsigned *ticket, double *scal) {
   __shared__ double sh[8][2];
   __shared__ bool last;
   double off = 0.0, tot = 0.0;
-  for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long)M * M;
-       idx += (long)gridDim.x * blockDim.x) {
+  const int MM = M * M;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < MM; idx += gridDim.x * blockDim.x) {
     const double v = A[idx];
+    const int i = idx / M;
     tot += v * v;
-    if (idx / M != idx % M) off += v * v;
+    if (idx != i * M + i) off += v * v;
   }
   for (int o = 16; o > 0; o >>= 1) {
     off += __shfl_xor_sync(0xffffffffu, off, o);
@@ -162,16 +242,22 @@ __global__ void __launch_bounds__(256)
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
+  if (!last || threadIdx.x >= 32) return;
   __threadfence();
   double o = 0.0, t = 0.0;
-  for (unsigned b = 0; b < gridDim.x; ++b) {
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
     o += __ldcg(red + 2 * b);
     t += __ldcg(red + 2 * b + 1);
   }
-  scal[SC_AUX] = o;
-  scal[SC_AUX + 1] = t;
-  *ticket = 0u;
+  for (int k = 16; k > 0; k >>= 1) {
+    o += __shfl_xor_sync(0xffffffffu, o, k);
+    t += __shfl_xor_sync(0xffffffffu, t, k);
+  }
+  if (threadIdx.x == 0) {
+    scal[SC_AUX] = o;
+    scal[SC_AUX + 1] = t;
+    *ticket = 0u;
+  }
 }
 
 // ------------------------------------------------------- sort and rank rule
@@ -632,8 +718,6 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   Linv = G + 64 * 64;
   VDS_CUDA_TRY(cudaMalloc(&tb.p[3], (size_t)M * sizeof(int)));
   order = (int *)tb.p[3];
-  VDS_CUDA_TRY(cudaMalloc(&tb.p[7], (size_t)(M / 2 + 1) * sizeof(double2)));
-  double2 *rot = (double2 *)tb.p[7];
 
   // 1. Gram
   VDS_TRY(vds_time_begin(c, PK_GRAM));
@@ -648,11 +732,12 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   VDS_TRY(vds_ensure(c, c->red, 2 * 1024 * sizeof(double)));
   const int Mpe = (M % 2 == 0) ? M : M + 1;  // odd M: one dummy index
   const int H = Mpe / 2;
-  const long nthreads = (long)H * H + (long)M * H;
-  const unsigned nblk_round = (unsigned)((nthreads + 255) / 256);
+  const int nT = (H + JT - 1) / JT;                                // <= 64 (M <= 2048)
+  const int nAt = nT * (nT + 1) / 2, nVt = ((M + JV_ROWS - 1) / JV_ROWS) * nT;
+  const unsigned nblk_round = (unsigned)(nAt + nVt);
   int offblk = (int)((MM + 255) / 256);
-  if (offblk > 1024) offblk = 1024;
-  // One sweep (Mpe - 1 rounds, two launches each) is captured as a CUDA graph
+  if (offblk > 256) offblk = 256;
+  // One sweep (Mpe - 1 rounds, one launch each) is captured as a CUDA graph
   // per starting buffer pair (the buffers swap once per round).
   struct SweepGraphs {
     cudaGraphExec_t g[2] = {nullptr, nullptr};
@@ -668,8 +753,8 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     int cur = par;
     for (int rnd = 0; rnd < Mpe - 1 && e == cudaSuccess; ++rnd) {
-      k_jacobi_rots<<<(H + 255) / 256, 256, 0, cap>>>(Ab[cur], M, Mpe, rnd, rot);
-      k_jacobi_round<<<nblk_round, 256, 0, cap>>>(Ab[cur], Ab[cur ^ 1], Vb[cur], Vb[cur ^ 1], M, Mpe, rnd, rot);
+      k_jacobi_round<<<nblk_round, JR_NT, 0, cap>>>(Ab[cur], Ab[cur ^ 1], Vb[cur], Vb[cur ^ 1], M, Mpe, rnd,
+                                                    nT, nAt);
       e = cudaGetLastError();
       cur ^= 1;
     }
@@ -690,7 +775,7 @@ int pod_build(vds_ctx *c, const float *X, long Ns, int M, int s, double energy, 
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (!sg.g[par]) VDS_TRY(capture(par));
     VDS_CUDA_TRY(cudaGraphLaunch(sg.g[par], c->stream));
-    c->launches += 2 * (Mpe - 1);
+    c->launches += Mpe - 1;
     if ((Mpe - 1) % 2 == 1) par ^= 1;
     k_offnorm<<<offblk, 256, 0, c->stream>>>(Ab[par], M, (double *)c->red.ptr, c->ticket + TK_MISC, c->scal);
     VDS_CUDA_TRY(cudaGetLastError());
