@@ -190,8 +190,10 @@ VDS_API int vds_grad_rows(vds_ctx *ctx, const float *q, int N, int D, const vds_
  *    uses (its partial sums must fit the fixed array), so it is slower there;
  *    results agree within the library's FP32 tolerance.
  *  - The first call on each device looks up the array's device address with
- *    that device current (the call's one-time set-up); make that first call
- *    before any stream capture on the device.
+ *    that device current (the call's one-time set-up).
+ *  - No call can be captured into a CUDA graph: each copies a status word to
+ *    the host and synchronises its stream.  A call on a stream that is being
+ *    captured returns VDS_EARG without enqueuing work.
  *  - Every call shares the one array: calls that overlap on the GPU (from
  *    several host threads, or on several streams) race and give wrong results.
  *    Calls made one after another do not overlap, because each synchronises

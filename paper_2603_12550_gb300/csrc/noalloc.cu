@@ -202,10 +202,18 @@ extern "C" int vds_energy_grad_noalloc(const float *q, int N, int D, const vds_p
     vds_last_cuda_error(e);
     return VDS_ECUDA;
   }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the call copies a status word to the host and synchronises its stream,
+  // neither of which a stream capture allows: refuse before touching it
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return VDS_EARG;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return VDS_EARG;
   DevState *s = nullptr;
   VDS_TRY(setup_device(dev, &s));
   const KParams kp = make_kparams(p, N, D);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   int r = VDS_EARG;
   switch (D) {
     case 2: r = na_energy_grad<2>(*s, q, kp, E, g, rho, st); break;

@@ -4,7 +4,8 @@ cannot allocate device memory when they evaluate the density and gradient
 the same energy, gradient and density as vds_energy_grad and as the FP64
 oracle, on two calls in a row through the C ABI, also at its largest size
 (where its gradient pass runs on a cut-down grid so that the partial sums fit
-the fixed scratch), and rejects sizes beyond its fixed scratch.
+the fixed scratch), rejects sizes beyond its fixed scratch, and refuses a
+stream that is being captured.
 
 Kept in a file that pytest collects last, so that a run stopping at its first
 failure has already run every other test.
@@ -105,3 +106,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(vds):
     st, _ = _call_noalloc(vds, q, vds.params(3, 3, h=0.9), g, rho)
     assert st == vds.VDS_ESIZE
     assert "fixed-size" in vds.strerror(st)
+
+
+def test_noalloc_refuses_stream_capture(vds):
+    # a call on a stream being captured returns VDS_EARG before it enqueues
+    # anything (it would copy to the host and synchronise), the capture stays
+    # valid, and the entry point works again afterwards
+    N = 256
+    q = torch.from_numpy(inputs.equilibrium_cloud(N, 3, 3, seed=3)).cuda()
+    g, rho = torch.empty_like(q), torch.empty(N, device="cuda")
+    p = vds.params(3, 3, h=0.8)
+    st, _ = _call_noalloc(vds, q, p, g, rho)  # the device's one-time set-up, outside any capture
+    assert st == vds.VDS_OK
+    g_ref = g.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st_cap, _ = _call_noalloc(vds, q, p, g, rho)
+        g.mul_(2.0)
+    assert st_cap == vds.VDS_EARG
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(g, 2.0 * g_ref)
+    st, _ = _call_noalloc(vds, q, p, g, rho)
+    assert st == vds.VDS_OK
+    assert torch.equal(g, g_ref)
