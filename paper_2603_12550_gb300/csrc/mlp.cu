@@ -100,6 +100,35 @@ __global__ void __launch_bounds__(GNT)
   const int nch = Ksplit / KC;
   const uint32_t sbase = smem_u32(gsm);
   const uint32_t txbytes = (uint32_t)(GM * KC * 2 + boxB * KC * 2);
+  // this thread's epilogue share: row `row`, columns [cb, ce) of the tile
+  const int row = m0 + (warp & 3) * 32 + lane;
+  const bool vrow = row < ep.rows;
+  const int half = ((BN + 31) / 32) * 16;
+  const int cb = (warp >> 2) * half, ce = min(BN, cb + half);
+  // the pre-activations the derivative epilogue multiplies by are loaded
+  // before the main loop, so their latency hides behind it
+  constexpr int HMAX = GBN / 2;
+  float zpre[HMAX];
+  if (ep.mode == EPI_DSILU) {
+    const bool vec = (ep.ldc & 3) == 0 && ((uintptr_t)ep.zin & 15) == 0;
+#pragma unroll
+    for (int c4 = 0; c4 < HMAX; c4 += 4) {
+      const int colb = n0 + cb + c4;
+      const bool in = vrow && cb + c4 < ce;
+      if (in && vec && colb + 4 <= ep.ncols) {
+        const float4 z4 = *reinterpret_cast<const float4 *>(ep.zin + (size_t)row * ep.ldc + colb);
+        zpre[c4] = z4.x;
+        zpre[c4 + 1] = z4.y;
+        zpre[c4 + 2] = z4.z;
+        zpre[c4 + 3] = z4.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          zpre[c4 + u] = (in && cb + c4 + u < ce && colb + u < ep.ncols) ? ep.zin[(size_t)row * ep.ldc + colb + u]
+                                                                        : 0.f;
+      }
+    }
+  }
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------ TMA producer
     int ch = 0;
@@ -145,11 +174,10 @@ __global__ void __launch_bounds__(GNT)
     if (tid == 0) vds_flag(err, VDS_ETIMEOUT);
   } else {
     // warp w: rows 32 (w % 4) + lane, columns [cb, ce) of the tile
-    const int row = m0 + (warp & 3) * 32 + lane;
-    const bool vrow = row < ep.rows;
-    const int half = ((BN + 31) / 32) * 16;
-    const int cb = (warp >> 2) * half, ce = min(BN, cb + half);
-    for (int c0 = cb; c0 < ce; c0 += 16) {
+#pragma unroll
+    for (int cc = 0; cc < HMAX; cc += 16) {
+      const int c0 = cb + cc;
+      if (c0 >= ce) break;
       uint32_t v[16];
       tc_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
       if (!vrow) continue;
@@ -184,8 +212,7 @@ __global__ void __launch_bounds__(GNT)
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const float zin = (full || colb + j < ep.ncols) ? ep.zin[(size_t)row * ep.ldc + colb + j] : 0.f;
-          y[j] = a[j] * dsilu_f(zin);
+          y[j] = a[j] * dsilu_f(zpre[cc + j]);
           a[j] = y[j];
         }
       }
@@ -978,8 +1005,9 @@ int loss_grad(vds_ctx *c, vds_score *s, const float *x, const int *rows, const f
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   // split-K over the batch for the weight gradients
+  // (at most 16 splits: more write more FP32 partials than their MMAs save)
   int splits = M / KC;
-  while (splits > 64 || (M % (KC * splits)) != 0) --splits;
+  while (splits > 16 || (M % (KC * splits)) != 0) --splits;
   if (splits < 1) splits = 1;
   auto wgrad = [&](const bf16 *At, int rows, const bf16 *Bt, int N, float *dst) -> int {
     const long long stride = (long long)rows * N;

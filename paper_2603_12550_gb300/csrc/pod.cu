@@ -559,27 +559,64 @@ __global__ void k_kappa_phi(const float *__restrict__ phi, long Ns, int ld, int 
 
 // ------------------------------------------------------- project and lift
 
-constexpr int PJ_PART = 32;  // particles per CTA
+constexpr int PJ_NT = 256;   // threads per CTA
+constexpr int PJ_TT = 8;     // basis columns per pass
 
 // partial[blk][t*nb + k] = sum over the block's particles of
 //   sum_a Phi[(I s + a), t] q[I D + s k + a]
-__global__ void __launch_bounds__(256)
-    k_project(const float *__restrict__ phi, int ld, int r, const float *__restrict__ q, int N, int D,
-              int s, int nb, double *__restrict__ part) {
-  extern __shared__ float psm[];
-  float *ph = psm;                    // PJ_PART * s * ld
-  float *qs = psm + PJ_PART * s * ld; // PJ_PART * D
-  const int I0 = blockIdx.x * PJ_PART;
-  const int np = min(PJ_PART, N - I0);
-  for (int e = threadIdx.x; e < np * s * ld; e += 256) ph[e] = phi[(size_t)I0 * s * ld + e];
-  for (int e = threadIdx.x; e < np * D; e += 256) qs[e] = q[(size_t)I0 * D + e];
-  __syncthreads();
-  for (int o = threadIdx.x; o < r * nb; o += 256) {
-    const int t = o / nb, k = o - (o / nb) * nb;
-    float acc = 0.f;
-    for (int p = 0; p < np; ++p)
-      for (int a = 0; a < s; ++a) acc = fmaf(ph[(p * s + a) * ld + t], qs[p * D + s * k + a], acc);
-    part[(size_t)blockIdx.x * (r * nb) + o] = (double)acc;
+// (PJ_NB >= nb bonds, a compile-time bound).
+// Each thread takes particles I = I0 + tid, I0 + tid + 256, ... of the
+// block's contiguous range and keeps PJ_TT x nb FP32 sums per pass over the
+// basis columns; the block combines them in a fixed order (warp shuffle tree,
+// then the warps in order, in FP64), so the result does not depend on the
+// schedule.  Phi rows and q rows are read once per pass.
+template <int S, int PJ_NB>
+__global__ void __launch_bounds__(PJ_NT)
+    k_project(const float *__restrict__ phi, int ld, int r, const float *__restrict__ q, int N, int nb,
+              long per_cta, double *__restrict__ part) {
+  __shared__ double red[PJ_NT / 32][PJ_TT * PJ_NB];
+  const int D = nb * S, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long I0 = (long)blockIdx.x * per_cta, I1 = min((long)N, I0 + per_cta);
+  for (int t0 = 0; t0 < r; t0 += PJ_TT) {
+    float acc[PJ_TT][PJ_NB];
+#pragma unroll
+    for (int tt = 0; tt < PJ_TT; ++tt)
+#pragma unroll
+      for (int k = 0; k < PJ_NB; ++k) acc[tt][k] = 0.f;
+    for (long I = I0 + threadIdx.x; I < I1; I += PJ_NT) {
+      float qv[PJ_NB * S];
+#pragma unroll
+      for (int e = 0; e < PJ_NB * S; ++e) qv[e] = e < D ? q[(size_t)I * D + e] : 0.f;
+#pragma unroll
+      for (int a = 0; a < S; ++a) {
+        const float *row = phi + ((size_t)I * S + a) * ld + t0;
+        float ph[PJ_TT];
+#pragma unroll
+        for (int tt = 0; tt < PJ_TT; ++tt) ph[tt] = t0 + tt < r ? row[tt] : 0.f;
+#pragma unroll
+        for (int tt = 0; tt < PJ_TT; ++tt)
+#pragma unroll
+          for (int k = 0; k < PJ_NB; ++k) acc[tt][k] = fmaf(ph[tt], qv[k * S + a], acc[tt][k]);
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < PJ_TT; ++tt)
+#pragma unroll
+      for (int k = 0; k < PJ_NB; ++k) {
+        float v = acc[tt][k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][tt * PJ_NB + k] = (double)v;
+      }
+    __syncthreads();
+    if (threadIdx.x < PJ_TT * PJ_NB) {
+      const int tt = threadIdx.x / PJ_NB, k = threadIdx.x % PJ_NB;
+      if (t0 + tt < r && k < nb) {
+        double v = 0.0;
+        for (int w = 0; w < PJ_NT / 32; ++w) v += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * (r * nb) + (t0 + tt) * nb + k] = v;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -616,9 +653,17 @@ __global__ void __launch_bounds__(256)
   const int a = (int)(row - I * s);
   float acc[8];
   for (int k = 0; k < nb; ++k) acc[k] = 0.f;
-  for (int t = 0; t < r; ++t) {
-    const float f = phi[row * ld + t];
-    for (int k = 0; k < nb; ++k) acc[k] = fmaf(f, ps[t * nb + k], acc[k]);
+  // ld is a multiple of 4 (columns r..ld-1 hold zeros): the row in float4s
+  const float4 *row4 = reinterpret_cast<const float4 *>(phi + row * ld);
+  for (int t4 = 0; t4 < (r + 3) / 4; ++t4) {
+    const float4 f4 = row4[t4];
+    const float f[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int t = 4 * t4 + u;
+      if (t >= r) break;
+      for (int k = 0; k < nb; ++k) acc[k] = fmaf(f[u], ps[t * nb + k], acc[k]);
+    }
   }
   for (int k = 0; k < nb; ++k) q[I * D + s * k + a] = acc[k];
 }
@@ -659,13 +704,32 @@ int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int 
 
 int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf) {
   const int nb = D / b->s;
-  const int nblk = (N + PJ_PART - 1) / PJ_PART;
+  if (nb > 8) return VDS_EARG;
+  // about two CTAs per SM, each a contiguous range of particles
+  long nblk = (N + PJ_NT - 1) / PJ_NT;
+  if (nblk > 2L * c->num_sms) nblk = 2L * c->num_sms;
+  const long per_cta = (N + nblk - 1) / nblk;
+  nblk = (N + per_cta - 1) / per_cta;
   const int n = b->r * nb;
   VDS_TRY(vds_ensure(c, c->gbuf, (size_t)nblk * n * sizeof(double)));
-  const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
-  k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->gbuf.ptr);
+  auto launch = [&](auto kern) {
+    kern<<<(unsigned)nblk, PJ_NT, 0, c->stream>>>(b->phi, b->ld, b->r, q, N, nb, per_cta, (double *)c->gbuf.ptr);
+  };
+  if (b->s == 3) {
+    if (nb <= 1) launch(k_project<3, 1>);
+    else if (nb <= 2) launch(k_project<3, 2>);
+    else if (nb <= 3) launch(k_project<3, 3>);
+    else if (nb <= 4) launch(k_project<3, 4>);
+    else launch(k_project<3, 8>);
+  } else {
+    if (nb <= 1) launch(k_project<2, 1>);
+    else if (nb <= 2) launch(k_project<2, 2>);
+    else if (nb <= 3) launch(k_project<2, 3>);
+    else if (nb <= 4) launch(k_project<2, 4>);
+    else launch(k_project<2, 8>);
+  }
   VDS_CUDA_TRY(cudaGetLastError());
-  k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, nblk, n, pd, pf);
+  k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, (int)nblk, n, pd, pf);
   VDS_CUDA_TRY(cudaGetLastError());
   c->launches += 2;
   return VDS_OK;
@@ -1015,16 +1079,7 @@ int pod_project(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, fl
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != c->device) cudaSetDevice(c->device);
-  const int nblk = (N + PJ_PART - 1) / PJ_PART;
-  const int n = b->r * nb;
-  int st = vds_ensure(c, c->red, (size_t)nblk * n * sizeof(double));
-  if (st == VDS_OK) {
-    const size_t smem = ((size_t)PJ_PART * b->s * b->ld + (size_t)PJ_PART * D) * sizeof(float);
-    k_project<<<nblk, 256, smem, c->stream>>>(b->phi, b->ld, b->r, q, N, D, b->s, nb, (double *)c->red.ptr);
-    k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->red.ptr, nblk, n, nullptr, p);
-    c->launches += 2;
-    if (cudaGetLastError() != cudaSuccess) st = VDS_ECUDA;
-  }
+  const int st = pod_project_dev(c, b, q, N, D, nullptr, p);
   if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
   return st;
 }

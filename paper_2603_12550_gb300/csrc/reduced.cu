@@ -89,59 +89,99 @@ __global__ void k_combine_xb(const double *__restrict__ G1, const double *__rest
   if (o < n) XB[o] = scale * (G1[o] + G2[o]);
 }
 
-// column means of an N x D matrix: CM_BLK blocks of partial sums per column,
-// then one block per column combining them in a fixed order
-constexpr int CM_BLK = 64;
-__global__ void k_colmean_part(const float *__restrict__ s, int N, int D, double *__restrict__ part) {
-  __shared__ double sh[256];
-  const int col = blockIdx.x, b = blockIdx.y;
-  double a = 0.0;
-  for (int i = b * 256 + threadIdx.x; i < N; i += 256 * CM_BLK) a += (double)s[(size_t)i * D + col];
-  sh[threadIdx.x] = a;
-  __syncthreads();
-  for (int o = 128; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
+// column means of an N x D matrix (D <= 16): up to CM_BLK CTAs, each over a
+// contiguous range of rows; a thread sums the rows I0 + tid, I0 + tid + 256,
+// ... in FP32 (a handful per thread), the CTA combines them in a fixed order
+// (warp shuffle tree in FP32, then the warps in order in FP64), and one warp
+// adds the CTA sums in order: the result does not depend on the schedule.
+constexpr int CM_NT = 256;
+constexpr int CM_BLK = 256;
+__global__ void __launch_bounds__(CM_NT)
+    k_colmean_part(const float *__restrict__ s, int N, int D, long per_cta, double *__restrict__ part) {
+  __shared__ double red[CM_NT / 32][16];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long I0 = (long)blockIdx.x * per_cta, I1 = min((long)N, I0 + per_cta);
+  float acc[16];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) acc[a] = 0.f;
+  for (long I = I0 + threadIdx.x; I < I1; I += CM_NT) {
+#pragma unroll
+    for (int a = 0; a < 16; ++a)
+      if (a < D) acc[a] += s[(size_t)I * D + a];
   }
-  if (threadIdx.x == 0) part[col * CM_BLK + b] = sh[0];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    float v = acc[a];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][a] = (double)v;
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    double v = 0.0;
+    for (int w = 0; w < CM_NT / 32; ++w) v += red[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 16 + threadIdx.x] = v;
+  }
 }
-__global__ void k_colmean(const double *__restrict__ part, int N, double *__restrict__ mean) {
-  if (threadIdx.x != 0) return;
-  double a = 0.0;
-  for (int b = 0; b < CM_BLK; ++b) a += part[blockIdx.x * CM_BLK + b];
-  mean[blockIdx.x] = a / (double)N;
+// one warp per column: lanes take every 32nd CTA sum, then a fixed shuffle tree
+__global__ void k_colmean(const double *__restrict__ part, int nblk, int N, int D, double *__restrict__ mean,
+                          float *__restrict__ meanf) {
+  const int a = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (a >= D) return;
+  double v = 0.0;
+  for (int b = lane; b < nblk; b += 32) v += part[(size_t)b * 16 + a];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) {
+    mean[a] = v / (double)N;
+    meanf[a] = (float)(v / (double)N);
+  }
+}
+// the grid of k_colmean_part for N rows
+inline void colmean_grid(const vds_ctx *c, int N, int &nblk, long &per_cta) {
+  long nb = (N + CM_NT - 1) / CM_NT;
+  const long cap = 2L * c->num_sms < CM_BLK ? 2L * c->num_sms : CM_BLK;
+  if (nb > cap) nb = cap;
+  per_cta = (N + nb - 1) / nb;
+  nblk = (int)((N + per_cta - 1) / per_cta);
 }
 
 // particle velocity with the entropy gradient replaced by the surrogate
 // (mean-centred): v = kappa q - (1/zeta)(A (x) I)(kBT (s - mean s) + grad Psi),
 // in FP32 (the inputs and the output are FP32); A is the Rouse matrix, so
 // (A g)_k = 2 g_k - g_(k-1) - g_(k+1) per bond k.
+// the step's constants in FP32, converted once on the host (a conversion
+// from FP64 per particle would run on this GPU's narrow FP64 pipe)
+struct VelF {
+  float kappa[9];
+  float H[8];
+  float kBT, izeta, b;
+  int spring, N;
+};
+
 template <int D, int S>
-__global__ void k_score_vel(KParams kp, const float *__restrict__ q, const float *__restrict__ sc,
-                            const double *__restrict__ smean, float *__restrict__ v, int *err) {
+__global__ void k_score_vel(VelF vf, const float *__restrict__ q, const float *__restrict__ sc,
+                            const float *__restrict__ smean, float *__restrict__ v, int *err) {
   constexpr int NB = D / S;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= kp.N) return;
+  if (i >= vf.N) return;
   float y[D], g[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) y[a] = q[(size_t)i * D + a];
-  const float kBT = (float)kp.kBT, izeta = (float)(1.0 / kp.zeta);
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
-    float f = (float)kp.H[k];
-    if (kp.spring != 0) {
+    float f = vf.H[k];
+    if (vf.spring != 0) {
       float n2 = 0.f;
 #pragma unroll
       for (int al = 0; al < S; ++al) n2 = fmaf(y[k * S + al], y[k * S + al], n2);
-      const float x = 1.f - n2 / (float)kp.b;
+      const float x = 1.f - n2 / vf.b;
       if (!(x > 0.f)) vds_flag(err, VDS_EDOMAIN);
       f = x > 0.f ? f / x : 0.f;
     }
 #pragma unroll
     for (int al = 0; al < S; ++al) {
       const int a = k * S + al;
-      const float sm = smean ? (float)smean[a] : 0.f;
-      g[a] = fmaf(kBT, sc[(size_t)i * D + a] - sm, f * y[a]);
+      const float sm = smean ? smean[a] : 0.f;
+      g[a] = fmaf(vf.kBT, sc[(size_t)i * D + a] - sm, f * y[a]);
     }
   }
 #pragma unroll
@@ -151,11 +191,11 @@ __global__ void k_score_vel(KParams kp, const float *__restrict__ q, const float
       const int a = k * S + al;
       float vv = 0.f;
 #pragma unroll
-      for (int be = 0; be < S; ++be) vv = fmaf((float)kp.kappa[al * S + be], y[k * S + be], vv);
+      for (int be = 0; be < S; ++be) vv = fmaf(vf.kappa[al * S + be], y[k * S + be], vv);
       float m = 2.f * g[a];
       if (k > 0) m -= g[a - S];
       if (k < NB - 1) m -= g[a + S];
-      v[(size_t)i * D + a] = fmaf(-izeta, m, vv);
+      v[(size_t)i * D + a] = fmaf(-vf.izeta, m, vv);
     }
 }
 
@@ -306,15 +346,23 @@ int grad_rows(vds_ctx *c, const KParams &kS, int stride, int nrows, double *part
 }
 
 template <int D, int S>
-int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean,
+int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const float *smean,
                    float *v) {
-  k_score_vel<D, S><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(kp, q, sc, smean, v, c->err);
+  VelF vf;
+  for (int k = 0; k < 9; ++k) vf.kappa[k] = (float)kp.kappa[k];
+  for (int k = 0; k < 8; ++k) vf.H[k] = (float)kp.H[k];
+  vf.kBT = (float)kp.kBT;
+  vf.izeta = (float)(1.0 / kp.zeta);
+  vf.b = (float)kp.b;
+  vf.spring = kp.spring;
+  vf.N = kp.N;
+  k_score_vel<D, S><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(vf, q, sc, smean, v, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   return VDS_OK;
 }
 
-int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const double *smean, float *v) {
+int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const float *smean, float *v) {
   const int key = kp.D * 4 + kp.s;
   switch (key) {
     case 2 * 4 + 2: return score_vel_impl<2, 2>(c, kp, q, sc, smean, v);
@@ -470,11 +518,15 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   VDS_TRY(vds_ensure(c, c->ubuf, (2 * 512 + 64 + 16 * CM_BLK) * sizeof(double)));
   double *Pd = (double *)c->ubuf.ptr, *Pdot = Pd + 512, *smean = Pdot + 512, *errs = smean + 32,
          *cpart = errs + 32;
+  float *smeanf = (float *)(smean + 16);  // FP32 copy of the means (D <= 16)
   k_f2d<<<(n + 255) / 256, 256, 0, c->stream>>>(P, Pd, n);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
   const int stride = check_n >= N ? 1 : N / check_n;
   const int nrows = (N + stride - 1) / stride;
+  int cm_nblk;
+  long cm_per;
+  colmean_grid(c, N, cm_nblk, cm_per);
   double worst = 0.0;
   int nfall = 0;
   // one surrogate step without a check: lift, network, mean, velocity,
@@ -482,11 +534,11 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   auto plain_step = [&]() -> int {
     VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
     VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
-    k_colmean_part<<<dim3(D, CM_BLK), 256, 0, c->stream>>>(sbuf, N, D, cpart);
-    k_colmean<<<D, 32, 0, c->stream>>>(cpart, N, smean);
+    k_colmean_part<<<cm_nblk, CM_NT, 0, c->stream>>>(sbuf, N, D, cm_per, cpart);
+    k_colmean<<<1, 32 * D, 0, c->stream>>>(cpart, cm_nblk, N, D, smean, smeanf);
     VDS_CUDA_TRY(cudaGetLastError());
     c->launches += 2;
-    VDS_TRY(score_vel(c, kp, qt, sbuf, smean, vel));
+    VDS_TRY(score_vel(c, kp, qt, sbuf, smeanf, vel));
     VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
     k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
     VDS_CUDA_TRY(cudaGetLastError());
@@ -555,8 +607,8 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     }
     VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
     VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
-    k_colmean_part<<<dim3(D, CM_BLK), 256, 0, c->stream>>>(sbuf, N, D, cpart);
-    k_colmean<<<D, 32, 0, c->stream>>>(cpart, N, smean);
+    k_colmean_part<<<cm_nblk, CM_NT, 0, c->stream>>>(sbuf, N, D, cm_per, cpart);
+    k_colmean<<<1, 32 * D, 0, c->stream>>>(cpart, cm_nblk, N, D, smean, smeanf);
     VDS_CUDA_TRY(cudaGetLastError());
     c->launches += 2;
     bool exact = false;
@@ -588,7 +640,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
         ++nfall;
       }
     }
-    VDS_TRY(score_vel(c, kp, qt, exact ? Sx : sbuf, exact ? nullptr : smean, vel));
+    VDS_TRY(score_vel(c, kp, qt, exact ? Sx : sbuf, exact ? nullptr : smeanf, vel));
     VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
     k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
     VDS_CUDA_TRY(cudaGetLastError());
