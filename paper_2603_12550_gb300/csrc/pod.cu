@@ -702,14 +702,26 @@ int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int 
   return tsgram(c, A, B, Ns, ld, r, (double *)c->gbuf.ptr, nblk, rchunk, G);
 }
 
+void pod_project_grid(const vds_ctx *c, int N, long &nblk, long &per_cta) {
+  // about two CTAs per SM, each a contiguous range of particles
+  nblk = (N + PJ_NT - 1) / PJ_NT;
+  if (nblk > 2L * c->num_sms) nblk = 2L * c->num_sms;
+  per_cta = (N + nblk - 1) / nblk;
+  nblk = (N + per_cta - 1) / per_cta;
+}
+
+int pod_project_finish(vds_ctx *c, int n, long nblk, double *pd, float *pf) {
+  k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, (int)nblk, n, pd, pf);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
 int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf) {
   const int nb = D / b->s;
   if (nb > 8) return VDS_EARG;
-  // about two CTAs per SM, each a contiguous range of particles
-  long nblk = (N + PJ_NT - 1) / PJ_NT;
-  if (nblk > 2L * c->num_sms) nblk = 2L * c->num_sms;
-  const long per_cta = (N + nblk - 1) / nblk;
-  nblk = (N + per_cta - 1) / per_cta;
+  long nblk, per_cta;
+  pod_project_grid(c, N, nblk, per_cta);
   const int n = b->r * nb;
   VDS_TRY(vds_ensure(c, c->gbuf, (size_t)nblk * n * sizeof(double)));
   auto launch = [&](auto kern) {
@@ -729,10 +741,8 @@ int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D
     else launch(k_project<2, 8>);
   }
   VDS_CUDA_TRY(cudaGetLastError());
-  k_project_reduce2<<<n, 256, 0, c->stream>>>((const double *)c->gbuf.ptr, (int)nblk, n, pd, pf);
-  VDS_CUDA_TRY(cudaGetLastError());
-  c->launches += 2;
-  return VDS_OK;
+  ++c->launches;
+  return pod_project_finish(c, n, nblk, pd, pf);
 }
 
 int pod_lift_dev(vds_ctx *c, const pod_basis *b, const float *p, int N, int D, float *q) {

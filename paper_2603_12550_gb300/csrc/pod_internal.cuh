@@ -23,6 +23,12 @@ int pod_gram_tc(vds_ctx *c, const float *X, long Ns, int M, double *part, double
 int pod_tsgram(vds_ctx *c, const float *A, const float *B, long Ns, int ld, int r, double *G);
 // P = Phi^T q (r x nb) into pd (FP64, may be NULL) and/or pf (FP32, may be NULL).
 int pod_project_dev(vds_ctx *c, const pod_basis *b, const float *q, int N, int D, double *pd, float *pf);
+// The projection's split over CTAs (nblk CTAs of per_cta contiguous
+// particles) and its final step: per-CTA FP64 partials [nblk][n] in
+// ctx->gbuf summed in a fixed order into pd and/or pf (n = r nb values), for
+// kernels that compute the projected field themselves (reduced.cu).
+void pod_project_grid(const vds_ctx *c, int N, long &nblk, long &per_cta);
+int pod_project_finish(vds_ctx *c, int n, long nblk, double *pd, float *pf);
 // U1, U2 (Ns x ld, FP32) of the X^B refresh at the records in ctx->rec
 // (refresh.cu); time kind PK_REFRESH.
 int pod_refresh_dev(vds_ctx *c, const pod_basis *b, int N, int D, float *U1, float *U2);

@@ -157,15 +157,12 @@ struct VelF {
   int spring, N;
 };
 
+// v of one particle from its connectors y and its score (FP32)
 template <int D, int S>
-__global__ void k_score_vel(VelF vf, const float *__restrict__ q, const float *__restrict__ sc,
-                            const float *__restrict__ smean, float *__restrict__ v, int *err) {
+__device__ __forceinline__ void score_velocity(const VelF &vf, const float (&y)[D], const float *__restrict__ si,
+                                               const float *__restrict__ smean, float (&v)[D], int *err) {
   constexpr int NB = D / S;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= vf.N) return;
-  float y[D], g[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) y[a] = q[(size_t)i * D + a];
+  float g[D];
 #pragma unroll
   for (int k = 0; k < NB; ++k) {
     float f = vf.H[k];
@@ -181,7 +178,7 @@ __global__ void k_score_vel(VelF vf, const float *__restrict__ q, const float *_
     for (int al = 0; al < S; ++al) {
       const int a = k * S + al;
       const float sm = smean ? smean[a] : 0.f;
-      g[a] = fmaf(vf.kBT, sc[(size_t)i * D + a] - sm, f * y[a]);
+      g[a] = fmaf(vf.kBT, si[a] - sm, f * y[a]);
     }
   }
 #pragma unroll
@@ -195,8 +192,71 @@ __global__ void k_score_vel(VelF vf, const float *__restrict__ q, const float *_
       float m = 2.f * g[a];
       if (k > 0) m -= g[a - S];
       if (k < NB - 1) m -= g[a + S];
-      v[(size_t)i * D + a] = fmaf(-vf.izeta, m, vv);
+      v[a] = fmaf(-vf.izeta, m, vv);
     }
+}
+
+constexpr int VP_NT = 256;  // threads per CTA
+constexpr int VP_TT = 8;    // basis columns per pass
+
+// The surrogate step's velocity and its projection in one pass: per-CTA
+// partials part[blk][t nb + k] = sum over the CTA's particles I (a
+// contiguous range of per_cta) of sum_a Phi[(I s + a), t] v_I[s k + a], with
+// v_I the velocity above; the velocity is never written to memory.  Each
+// thread keeps VP_TT x nb FP32 sums per pass over the basis columns; the CTA
+// combines them in a fixed order (warp shuffle tree, then the warps in order
+// in FP64), so the result does not depend on the schedule.
+template <int D, int S>
+__global__ void __launch_bounds__(VP_NT)
+    k_vel_project(VelF vf, const float *__restrict__ q, const float *__restrict__ sc,
+                  const float *__restrict__ smean, const float *__restrict__ phi, int ld, int r, long per_cta,
+                  double *__restrict__ part, int *err) {
+  constexpr int NB = D / S;
+  __shared__ double red[VP_NT / 32][VP_TT * NB];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long I0 = (long)blockIdx.x * per_cta, I1 = min((long)vf.N, I0 + per_cta);
+  for (int t0 = 0; t0 < r; t0 += VP_TT) {
+    float acc[VP_TT][NB];
+#pragma unroll
+    for (int tt = 0; tt < VP_TT; ++tt)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) acc[tt][k] = 0.f;
+    for (long I = I0 + threadIdx.x; I < I1; I += VP_NT) {
+      float y[D], v[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) y[a] = q[(size_t)I * D + a];
+      score_velocity<D, S>(vf, y, sc + (size_t)I * D, smean, v, err);
+#pragma unroll
+      for (int a = 0; a < S; ++a) {
+        const float *row = phi + ((size_t)I * S + a) * ld + t0;
+        float ph[VP_TT];
+#pragma unroll
+        for (int tt = 0; tt < VP_TT; ++tt) ph[tt] = t0 + tt < r ? row[tt] : 0.f;
+#pragma unroll
+        for (int tt = 0; tt < VP_TT; ++tt)
+#pragma unroll
+          for (int k = 0; k < NB; ++k) acc[tt][k] = fmaf(ph[tt], v[k * S + a], acc[tt][k]);
+      }
+    }
+#pragma unroll
+    for (int tt = 0; tt < VP_TT; ++tt)
+#pragma unroll
+      for (int k = 0; k < NB; ++k) {
+        float x = acc[tt][k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[warp][tt * NB + k] = (double)x;
+      }
+    __syncthreads();
+    if (threadIdx.x < VP_TT * NB) {
+      const int tt = threadIdx.x / NB, k = threadIdx.x % NB;
+      if (t0 + tt < r) {
+        double x = 0.0;
+        for (int w = 0; w < VP_NT / 32; ++w) x += red[w][threadIdx.x];
+        part[(size_t)blockIdx.x * (r * NB) + (t0 + tt) * NB + k] = x;
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // The exact entropy gradient S of the checked particles only (every
@@ -345,9 +405,11 @@ int grad_rows(vds_ctx *c, const KParams &kS, int stride, int nrows, double *part
   }
 }
 
+// Pdot (FP64 and/or FP32, r x nb) = Phi^T v, v the surrogate velocity of
+// every particle (scores sc, mean-centred by smean when given)
 template <int D, int S>
-int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const float *smean,
-                   float *v) {
+int vel_project_impl(vds_ctx *c, const KParams &kp, const pod_basis *b, const float *q, const float *sc,
+                     const float *smean, double *pd) {
   VelF vf;
   for (int k = 0; k < 9; ++k) vf.kappa[k] = (float)kp.kappa[k];
   for (int k = 0; k < 8; ++k) vf.H[k] = (float)kp.H[k];
@@ -356,24 +418,30 @@ int score_vel_impl(vds_ctx *c, const KParams &kp, const float *q, const float *s
   vf.b = (float)kp.b;
   vf.spring = kp.spring;
   vf.N = kp.N;
-  k_score_vel<D, S><<<(kp.N + 255) / 256, 256, 0, c->stream>>>(vf, q, sc, smean, v, c->err);
+  long nblk, per_cta;
+  pod_project_grid(c, kp.N, nblk, per_cta);
+  const int n = b->r * (D / S);
+  VDS_TRY(vds_ensure(c, c->gbuf, (size_t)nblk * n * sizeof(double)));
+  k_vel_project<D, S><<<(unsigned)nblk, VP_NT, 0, c->stream>>>(vf, q, sc, smean, b->phi, b->ld, b->r, per_cta,
+                                                               (double *)c->gbuf.ptr, c->err);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
-  return VDS_OK;
+  return pod_project_finish(c, n, nblk, pd, nullptr);
 }
 
-int score_vel(vds_ctx *c, const KParams &kp, const float *q, const float *sc, const float *smean, float *v) {
+int vel_project(vds_ctx *c, const KParams &kp, const pod_basis *b, const float *q, const float *sc,
+                const float *smean, double *pd) {
   const int key = kp.D * 4 + kp.s;
   switch (key) {
-    case 2 * 4 + 2: return score_vel_impl<2, 2>(c, kp, q, sc, smean, v);
-    case 3 * 4 + 3: return score_vel_impl<3, 3>(c, kp, q, sc, smean, v);
-    case 4 * 4 + 2: return score_vel_impl<4, 2>(c, kp, q, sc, smean, v);
-    case 6 * 4 + 2: return score_vel_impl<6, 2>(c, kp, q, sc, smean, v);
-    case 6 * 4 + 3: return score_vel_impl<6, 3>(c, kp, q, sc, smean, v);
-    case 8 * 4 + 2: return score_vel_impl<8, 2>(c, kp, q, sc, smean, v);
-    case 9 * 4 + 3: return score_vel_impl<9, 3>(c, kp, q, sc, smean, v);
-    case 12 * 4 + 2: return score_vel_impl<12, 2>(c, kp, q, sc, smean, v);
-    case 12 * 4 + 3: return score_vel_impl<12, 3>(c, kp, q, sc, smean, v);
+    case 2 * 4 + 2: return vel_project_impl<2, 2>(c, kp, b, q, sc, smean, pd);
+    case 3 * 4 + 3: return vel_project_impl<3, 3>(c, kp, b, q, sc, smean, pd);
+    case 4 * 4 + 2: return vel_project_impl<4, 2>(c, kp, b, q, sc, smean, pd);
+    case 6 * 4 + 2: return vel_project_impl<6, 2>(c, kp, b, q, sc, smean, pd);
+    case 6 * 4 + 3: return vel_project_impl<6, 3>(c, kp, b, q, sc, smean, pd);
+    case 8 * 4 + 2: return vel_project_impl<8, 2>(c, kp, b, q, sc, smean, pd);
+    case 9 * 4 + 3: return vel_project_impl<9, 3>(c, kp, b, q, sc, smean, pd);
+    case 12 * 4 + 2: return vel_project_impl<12, 2>(c, kp, b, q, sc, smean, pd);
+    case 12 * 4 + 3: return vel_project_impl<12, 3>(c, kp, b, q, sc, smean, pd);
     default: return VDS_EARG;
   }
 }
@@ -513,8 +581,8 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   const KParams kS = make_kparams(&pS, N, D);
   const int r = b->r, nb = p->nb, n = r * nb;
   const size_t nd = (size_t)N * D;
-  VDS_TRY(vds_ensure(c, c->vecs, 4 * nd * sizeof(float)));
-  float *qt = (float *)c->vecs.ptr, *sbuf = qt + nd, *Sx = sbuf + nd, *vel = Sx + nd;
+  VDS_TRY(vds_ensure(c, c->vecs, 3 * nd * sizeof(float)));
+  float *qt = (float *)c->vecs.ptr, *sbuf = qt + nd, *Sx = sbuf + nd;
   VDS_TRY(vds_ensure(c, c->ubuf, (2 * 512 + 64 + 16 * CM_BLK) * sizeof(double)));
   double *Pd = (double *)c->ubuf.ptr, *Pdot = Pd + 512, *smean = Pdot + 512, *errs = smean + 32,
          *cpart = errs + 32;
@@ -529,8 +597,8 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
   colmean_grid(c, N, cm_nblk, cm_per);
   double worst = 0.0;
   int nfall = 0;
-  // one surrogate step without a check: lift, network, mean, velocity,
-  // projection, Euler update of P
+  // one surrogate step without a check: lift, network, mean, velocity and
+  // projection (one pass), Euler update of P
   auto plain_step = [&]() -> int {
     VDS_TRY(pod_lift_dev(c, b, P, N, D, qt));
     VDS_TRY(vds_score_eval(c, sc, qt, N, sbuf));
@@ -538,8 +606,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     k_colmean<<<1, 32 * D, 0, c->stream>>>(cpart, cm_nblk, N, D, smean, smeanf);
     VDS_CUDA_TRY(cudaGetLastError());
     c->launches += 2;
-    VDS_TRY(score_vel(c, kp, qt, sbuf, smeanf, vel));
-    VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
+    VDS_TRY(vel_project(c, kp, b, qt, sbuf, smeanf, Pdot));
     k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
@@ -640,8 +707,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
         ++nfall;
       }
     }
-    VDS_TRY(score_vel(c, kp, qt, exact ? Sx : sbuf, exact ? nullptr : smeanf, vel));
-    VDS_TRY(pod_project_dev(c, b, vel, N, D, Pdot, nullptr));
+    VDS_TRY(vel_project(c, kp, b, qt, exact ? Sx : sbuf, exact ? nullptr : smeanf, Pdot));
     k_euler_p<<<(n + 255) / 256, 256, 0, c->stream>>>(Pd, P, Pdot, p->dt, n);
     VDS_CUDA_TRY(cudaGetLastError());
     ++c->launches;
