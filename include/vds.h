@@ -142,6 +142,24 @@ VDS_API int vds_stress(vds_ctx *ctx, const float *q, int N, int D, const vds_par
 VDS_API int vds_density_at(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p,
                            const float *y, int M, float *f);
 
+/* Density of every particle, rho[I] = sum_J exp(-|q_I - q_J|^2 / 2h^2)
+ * (Sec. 2.2, self term included), with the pair dot products on the tensor
+ * cores: -|qh_I - qh_J|^2 = 2 qh_I . qh_J - |qh_I|^2 - |qh_J|^2 as MMAs of
+ * TF32 operands split into two TF32 parts each (three products per pair), the
+ * exponentials on the CUDA cores.  For passes that tolerate about 1e-4 (the
+ * library uses it for the density of the surrogate's subset check): within
+ * 1e-5 relative of the exact kernel sum for the median particle of an
+ * equilibrium cloud and 1e-4 at its outermost particles; the error grows with
+ * |q|^2 / h^2 (3.4e-4 at the worst particle of a cloud stretched five-fold
+ * along one axis at h = 0.7), faster than for the expanded form on the CUDA
+ * cores, because the tensor cores accumulate the large |q|^2 terms in FP32
+ * with rounding toward zero.
+ * q: device N x D FP32; rho: device N FP32.  D = 6 or 9 (records with a norm
+ * slot and D + 1 <= 16); VDS_EARG otherwise, for NULL pointers or invalid
+ * parameters; VDS_ENAN (at the next synchronising call) for a non-finite
+ * density.  Asynchronous on the context stream. */
+VDS_API int vds_density_tc(vds_ctx *ctx, const float *q, int N, int D, const vds_params *p, float *rho);
+
 /* Row-range evaluation: the pieces of one evaluation split over ranks by
  * particle rows.  The paper's cost is the O(P^2) pair sums (Sec. 1.2, The
  * VDS Scheme and its Limitation); each of G ranks takes a contiguous range

@@ -61,6 +61,13 @@ int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy
                  const float *ybase, const float *ydelta, const float *qa,
                  const float *qb, bool expand = false);
 
+// The same density without the energy, with the pair dot products on the
+// tensor cores (dens_tc.cu: 3xTF32; 1e-5 relative for the median particle of
+// an equilibrium cloud, 1e-4 at its outermost, more on stretched clouds): w_I = 1/rho_I
+// into the records (which must come from pass_prep), optional rho output.
+// D = 6 and 9 only; VDS_EARG otherwise, and the caller takes pass_density.
+int pass_density_tc(vds_ctx *c, const KParams &kp, float *rho_out);
+
 // Gradient pass (records must hold w from pass_density) and its epilogues.
 enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2, GM_VEL = 3 };
 // GM_OUT: g = kBT S + grad Psi(y) (+ (zeta/dt)(A^-1 (x) I)(qa - qb) if qa).

@@ -466,6 +466,18 @@ struct Dev {
   }
 };
 
+// The density of every particle of the records in ctx->rec for the
+// surrogate's subset check (judged against a threshold of order 0.1): the
+// pair dot products on the tensor cores where the records allow it (D = 6,
+// 9), else the expanded distances on the CUDA cores.  The tensor-core sums
+// lose more to the |q|^2 terms (3e-4 relative on a cloud stretched five-fold
+// against 1e-5 for the expanded FP32 form), so the refresh keeps the latter.
+int density_check(vds_ctx *c, const KParams &kp, const float *qt) {
+  const int st = pass_density_tc(c, kp, nullptr);
+  if (st != VDS_EARG) return st;
+  return pass_density(c, kp, nullptr, false, qt, nullptr, nullptr, nullptr, true);
+}
+
 // Lift P, evaluate the density at the lifted state, run the refresh pass and
 // the two contractions: G1 = Phi^T U1, G2 = Phi^T U2 (device FP64 r x r).
 int brownian_dev(vds_ctx *c, const pod_basis *b, const float *P, int N, int D, const KParams &kp,
@@ -681,10 +693,10 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     bool exact = false;
     {
       // full density (every 1/rho_J enters S_I), gradient of the checked rows;
-      // the density through the expanded distances (1e-6 relative, against a
-      // check threshold of order 0.1 and a fallback step judged at 1e-3)
+      // the density within about 1e-4 (against a check threshold of order 0.1
+      // and a fallback step judged at 1e-3)
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
-      VDS_TRY(pass_density(c, kS, nullptr, false, qt, nullptr, nullptr, nullptr, true));
+      VDS_TRY(density_check(c, kS, qt));
       // compact exact S of the checked rows (after the FP64 segment partials)
       // in the shared scratch, taken afresh at every check
       const size_t rows_bytes = ((size_t)nrows * D * sizeof(float) + 255) / 256 * 256;

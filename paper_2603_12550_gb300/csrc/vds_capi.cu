@@ -209,7 +209,7 @@ void vds_destroy(vds_ctx *c) {
   DeviceGuard g(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
-  DevBuf *bufs[] = {&c->rec, &c->recq, &c->part, &c->red, &c->vecs, &c->gbuf, &c->ubuf};
+  DevBuf *bufs[] = {&c->rec, &c->recq, &c->part, &c->red, &c->vecs, &c->gbuf, &c->ubuf, &c->dtbuf};
   for (DevBuf *b : bufs)
     if (b->ptr) cudaFree(b->ptr);
   if (c->err) cudaFree(c->err);
@@ -301,6 +301,16 @@ int vds_grad_rows(vds_ctx *c, const float *q, int N, int D, const vds_params *p,
   const KParams kp = make_kparams(p, N, D);
   VDS_TRY(pass_grad_rows(c, kp, q, rho, row0, nrows, mode, out));
   return VDS_OK;
+}
+
+int vds_density_tc(vds_ctx *c, const float *q, int N, int D, const vds_params *p, float *rho) {
+  if (!c || !q || !rho) return VDS_EARG;
+  VDS_TRY(check_params(p, N, D));
+  if (D != 6 && D != 9) return VDS_EARG;
+  DeviceGuard dg(c->device);
+  const KParams kp = make_kparams(p, N, D);
+  VDS_TRY(pass_prep(c, kp, q, nullptr, nullptr, 0.f, nullptr));
+  return pass_density_tc(c, kp, rho);
 }
 
 int vds_density_at(vds_ctx *c, const float *q, int N, int D, const vds_params *p, const float *y, int M,

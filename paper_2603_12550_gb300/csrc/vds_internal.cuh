@@ -196,6 +196,7 @@ struct vds_ctx {
   DevBuf vecs;     // minimiser vectors / scratch (FP32)
   DevBuf gbuf;     // Gram / projection partials (FP64)
   DevBuf ubuf;     // reduced-order scratch (refresh outputs, reduced state)
+  DevBuf dtbuf;    // tensor-core density: operand images and split partials
   int *err = nullptr;          // device error flag
   unsigned *ticket = nullptr;  // last-block tickets (zeroed, self-resetting)
   double *scal = nullptr;      // device scalars

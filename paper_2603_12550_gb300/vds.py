@@ -79,6 +79,7 @@ _SIGS = {
     "vds_step": ([_vp, _vp, _i, _i, _pp, _i, _ip], _i),
     "vds_stress": ([_vp, _vp, _i, _i, _pp, _dp, _dp], _i),
     "vds_density_at": ([_vp, _vp, _i, _i, _pp, _vp, _i, _vp], _i),
+    "vds_density_tc": ([_vp, _vp, _i, _i, _pp, _vp], _i),
     "vds_density_rows": ([_vp, _vp, _i, _i, _pp, _i, _i, _vp], _i),
     "vds_grad_rows": ([_vp, _vp, _i, _i, _pp, _vp, _i, _i, _i, _vp], _i),
     "vds_timing": ([_vp, _i], _i),
@@ -235,6 +236,10 @@ class Context:
         N, D = q.shape
         M = int(y.shape[0])
         _check(lib.vds_density_at(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(y), M, _ptr(f)))
+
+    def vds_density_tc(self, q, p: VdsParams, rho):
+        N, D = q.shape
+        _check(lib.vds_density_tc(self.h, _ptr(q), N, D, ctypes.byref(p), _ptr(rho)))
 
     def vds_density_rows(self, q, p: VdsParams, row0, nrows, rho_rows):
         N, D = q.shape
