@@ -30,8 +30,8 @@
 //
 // Roles per CTA (one 128-row tile of I, a range of 256-column tiles of J):
 // one thread bulk-copies the A image once and the B images through a
-// DT_NS-stage ring; one thread issues the MMAs; 8 warps read the
-// accumulators (warp w: rows 32 (w % 4) + lane, columns 128 (w / 4) ..),
+// DT_NS-stage ring; one thread issues the MMAs; 16 warps read the
+// accumulators (warp w: rows 32 (w % 4) + lane, columns 64 (w / 4) ..),
 // keep FP32 sums per tile and Kahan-compensated FP32 totals across tiles.
 // Every wait is bounded; a wait that runs out sets the abort flag and the
 // error status, and every role leaves its loop.  Partial sums per column
@@ -46,7 +46,8 @@ constexpr int DT_M = 128;                  // rows I per CTA (tensor-memory lane
 constexpr int DT_N = 256;                  // columns J per MMA tile
 constexpr int DT_K = 16;                   // padded dot-product length
 constexpr int DT_NS = 4;                   // B ring stages
-constexpr int DT_EW = 8;                   // epilogue warps
+constexpr int DT_EW = 16;                  // epilogue warps (4 per tensor-memory lane quarter)
+constexpr int DT_CW = DT_N / (DT_EW / 4);   // accumulator columns per epilogue warp
 constexpr int DT_NT = (DT_EW + 2) * 32;    // + copy warp + MMA warp
 constexpr int DT_RB = 128;                 // image bytes per row (hi 64 + lo 64, interleaved by row group)
 constexpr int DT_AB = DT_M * DT_RB;        // 16 KB
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(DT_NT, 1)
   __shared__ __align__(8) uint64_t abar, full[DT_NS], empty[DT_NS], accfull[2], accfree[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ float s_tot[DT_M], s_cmp[DT_M];
+  __shared__ float s_tot[DT_EW / 4][DT_M], s_cmp[DT_EW / 4][DT_M];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tr = blockIdx.x, split = blockIdx.y;
   const int c0 = split * tpc, c1 = min(ntc, c0 + tpc);
@@ -220,10 +221,10 @@ __global__ void __launch_bounds__(DT_NT, 1)
       ok = __all_sync(0xffffffffu, dt_wait(&accfull[b], (uint32_t)((g >> 1) & 1), abort));
       if (!ok) break;
       tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * DT_N + hc * 128);
+      const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * DT_N + hc * DT_CW);
       float s0 = 0.f, s1 = 0.f;
 #pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < DT_CW / 32; ++c) {
         uint32_t v[32];
         tc_ld32(ta + (uint32_t)(c * 32), v);
 #pragma unroll
@@ -241,13 +242,14 @@ __global__ void __launch_bounds__(DT_NT, 1)
       tot = t;
     }
     // the two column halves of a row: warp pairs (w, w + 4) through shared memory
-    if (hc == 1) {
-      s_tot[rl] = tot;
-      s_cmp[rl] = cmp;
-    }
+    s_tot[hc][rl] = tot;
+    s_cmp[hc][rl] = cmp;
     asm volatile("bar.sync 1, %0;" ::"r"(DT_EW * 32) : "memory");
-    if (hc == 0 && row < N)
-      part[(size_t)split * N + row] = ((double)tot - (double)cmp) + ((double)s_tot[rl] - (double)s_cmp[rl]);
+    if (hc == 0 && row < N) {
+      double v = 0.0;
+      for (int k = 0; k < DT_EW / 4; ++k) v += (double)s_tot[k][rl] - (double)s_cmp[k][rl];
+      part[(size_t)split * N + row] = v;
+    }
     if (!ok && lane == 0) vds_flag(err, VDS_ETIMEOUT);
   }
   // every role has left its loop; the MMAs issued are complete before the
