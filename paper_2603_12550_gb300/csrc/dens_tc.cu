@@ -1,8 +1,9 @@
 // dens_tc.cu -- the density pass rho_I = sum_J exp2(-|qh_I - qh_J|^2)
 // (Sec. 2.2's kernel density, qh the connectors scaled by sqrt(log2 e / 2h^2))
 // with the pair dot products on the 5th-generation tensor cores, for passes
-// that tolerate about 1e-4 rather than the full-order path's 1e-5: the
-// density of all particles that the surrogate's subset check needs.
+// judged at 1e-4 rather than the full-order path's 1e-5: the density at the
+// lifted state of the frozen reduced step's refresh, and the density of all
+// particles that the surrogate's subset check needs.
 //
 // -|qh_I - qh_J|^2 = a_I . b_J - |qh_I|^2 with a_I = (qh_I, 1, 0...) and
 // b_J = (2 qh_J, -|qh_J|^2, 0...), K = 16 columns.  One tcgen05.mma of kind

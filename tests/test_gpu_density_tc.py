@@ -5,8 +5,10 @@ equilibrium clouds of 1 to 20001 particles (one to many 128-row and
 256-column tiles, ragged last tiles, several column splits), D = 6 and 9, and
 at the full size N = 65536 against the library's exact FP32 pass; within
 1e-3 (1e-4 median) on a cloud stretched five-fold, where the error of the
-expanded form grows with |q|^2 / h^2.  The library uses it for the density of
-the surrogate's subset check, judged against a threshold of order 0.1.
+expanded form grows with |q|^2 / h^2.  The library uses it for the density at
+the lifted state of the refresh (X^B, a sum over all particles, is tested
+against the oracle at 1e-4 in test_gpu_reduced.py and at full size) and for
+the density of the surrogate's subset check.
 """
 import numpy as np
 import pytest
