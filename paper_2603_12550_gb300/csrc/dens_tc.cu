@@ -333,3 +333,21 @@ int pass_density_tc(vds_ctx *c, const KParams &kp, float *rho_out) {
     default: return VDS_EARG;  // no norm slot in the records, or D + 1 > 16
   }
 }
+
+int pass_density_tc_images(vds_ctx *c, int N, int D, const uint8_t **aimg, const uint8_t **bimg) {
+  if (N < 1 || (D != 6 && D != 9)) return VDS_EARG;
+  const int Npad = (N + DT_N - 1) / DT_N * DT_N;
+  const size_t img = (size_t)Npad * DT_RB;
+  VDS_TRY(vds_ensure(c, c->dtbuf, 2 * img));
+  uint8_t *a = (uint8_t *)c->dtbuf.ptr, *b = a + img;
+  const long ne = (long)Npad * DT_K;
+  if (D == 6)
+    k_dt_prep<6><<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>((const float *)c->rec.ptr, N, Npad, a, b);
+  else
+    k_dt_prep<9><<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>((const float *)c->rec.ptr, N, Npad, a, b);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  *aimg = a;
+  *bimg = b;
+  return VDS_OK;
+}

@@ -67,6 +67,12 @@ int pass_density(vds_ctx *c, const KParams &kp, float *rho_out, bool want_energy
 // into the records (which must come from pass_prep), optional rho output.
 // D = 6 and 9 only; VDS_EARG otherwise, and the caller takes pass_density.
 int pass_density_tc(vds_ctx *c, const KParams &kp, float *rho_out);
+// The operand images of that density (a_I rows and b_J rows, TF32 hi/lo
+// split, 128 bytes per row, rows [0, pass_npad(N)) in 8-row groups of 1024
+// bytes) from the records in ctx->rec, into the context's workspace: for the
+// refresh, which forms its kernel values from the same dot products.  D = 6
+// and 9 only (VDS_EARG otherwise).
+int pass_density_tc_images(vds_ctx *c, int N, int D, const uint8_t **aimg, const uint8_t **bimg);
 
 // Gradient pass (records must hold w from pass_density) and its epilogues.
 enum GradMode { GM_OUT = 0, GM_EXPLICIT = 1, GM_IMPLICIT_DIR = 2, GM_VEL = 3 };

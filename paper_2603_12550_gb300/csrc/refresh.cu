@@ -804,6 +804,273 @@ __global__ void __launch_bounds__(RC_NT, 1)
                           1.f / TA_BSCALE);
 }
 
+// ---------------------------------------------------------------------------
+// The refresh with the kernel values' dot products on the tensor cores as
+// well (D = 6, 9; 2 s r + 1 <= 64): per pass of two 64-particle chunks K, one
+// group of tcgen05.mma kind::tf32 forms a_I . b_K = 2 qh_I . qh_K - |qh_K|^2
+// (the density pass's operand images: TF32 hi/lo split, three products per
+// K = 8 step) into a 128-column tensor-memory buffer; the 16 warps that formed
+// Z from the records on the CUDA cores now read those sums (tcgen05.ld),
+// subtract |qh_I|^2, take ex2 and round to FP16 (one ex2, one FP32 operation
+// and a half conversion per pair instead of D + 2 operations), and the MMA
+// warp runs Z against [B_hi; B_lo] as in k_refresh_ta.  The dot products of
+// pass c + 1 are issued as soon as the warps have read those of pass c, so
+// they run under the exponentials and the Z.B MMAs of pass c.
+// Tensor memory: the two segment accumulators (2 x 2 NCP columns), two Z
+// pair slots (2 x 64) and the dot buffer (128).
+template <int NCP>
+struct DtLayout {
+  static constexpr int BOP = NCP * TA_KC * 2;       // one FP16 B operand tile
+  static constexpr int BCH = 2 * BOP;               // B hi + lo of one chunk
+  static constexpr int DOT = 2 * TA_KC * 128;       // dot-product B image of a pass (128 rows)
+  static constexpr int AIMG = RC_M * 128;           // dot-product A image of the row tile
+  static constexpr int SLOT = ((2 * BCH + DOT + 1023) / 1024) * 1024;
+  static constexpr int NS2 = ((200 * 1024 - AIMG) / SLOT) < 8 ? ((200 * 1024 - AIMG) / SLOT) : 8;
+  static constexpr int TOT_LD = NCP + 1;
+  static constexpr size_t RING = (size_t)AIMG + (size_t)NS2 * SLOT;
+  static constexpr size_t SMEM = RING > (size_t)RC_M * TOT_LD * 4 ? RING : (size_t)RC_M * TOT_LD * 4;
+  static_assert(NCP <= 64, "Z in tensor memory needs 2 s r + 1 <= 64");
+  static_assert(NS2 >= 2, "refresh ring depth");
+  static_assert(SMEM <= 227 * 1024 - 1024, "refresh shared memory");
+};
+
+template <int D, int NCP>
+__global__ void __launch_bounds__(RC_NT, 1)
+    k_refresh_dt(const float *__restrict__ rec, int N, int Npad, const float *__restrict__ bimg,
+                 const uint8_t *__restrict__ daimg, const uint8_t *__restrict__ dbimg,
+                 const float *__restrict__ phi, int ld, int r, int s, int rr, float *__restrict__ U1,
+                 float *__restrict__ U2, int nsplit, float *__restrict__ part, int *err) {
+  using L = DtLayout<NCP>;
+  constexpr int DP = Rec<D>::DP;
+  constexpr int NS2 = L::NS2;
+  constexpr int QC = NCP / 4;   // accumulator columns per thread in a flush
+  constexpr int ACW = 2 * NCP;  // Z against [B_hi; B_lo]: N = 2 NCP
+  constexpr int NZP = 2;        // Z pair slots: 2 chunks x 32 columns each
+  constexpr int ZCOL = 2 * ACW, DCOL = ZCOL + NZP * 64;
+  constexpr int TCOLS = 512;
+  static_assert(DCOL + 128 <= TCOLS, "tensor memory columns");
+  extern __shared__ __align__(1024) uint8_t sm[];
+  __shared__ __align__(8) uint64_t afull, sfull[NS2], sfree[NS2], dotready, dotfree, zready[NZP], zfree[NZP],
+      segdone[2], accfree[2], fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x / nsplit, split = blockIdx.x - tile * nsplit;
+  const int i0 = tile * RC_M;
+  const int cb = blockIdx.y;
+  const int nch_all = Npad / TA_KC, nseg_all = (nch_all + TA_SEGC - 1) / TA_SEGC;
+  const int sg0 = split * nseg_all / nsplit, sg1 = (split + 1) * nseg_all / nsplit;
+  const int c0 = sg0 * TA_SEGC;                      // first chunk of this CTA
+  const int nch = min(sg1 * TA_SEGC, nch_all) - c0;  // a multiple of 4: Npad is of 256
+  const int npass = nch / 2;
+  const int nseg = sg1 - sg0;
+  volatile int *abort = &s_abort;
+  if (warp == 0) tc_alloc(&s_tmem, TCOLS);
+  if (tid == 0) {
+    mbar_init(&afull, 1);
+    for (int j = 0; j < NS2; ++j) {
+      mbar_init(&sfull[j], 1);
+      mbar_init(&sfree[j], 1);
+    }
+    mbar_init(&dotready, 1);
+    mbar_init(&dotfree, RC_PW);
+    for (int b = 0; b < NZP; ++b) {
+      mbar_init(&zready[b], RC_PW);
+      mbar_init(&zfree[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&segdone[b], 1);
+      mbar_init(&accfree[b], RC_PW);
+    }
+    mbar_init(&fin, 1);
+    s_abort = 0;
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = smem_u32(sm);
+  float tot[QC];
+  bool ok = true;
+
+  if (warp == RC_PW) {
+    // ---------------------------------------------------- bulk copies
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&afull, (uint32_t)L::AIMG);
+      bulk_g2s(sm, daimg + (size_t)tile * L::AIMG, L::AIMG, &afull);
+      const uint8_t *bsrc = reinterpret_cast<const uint8_t *>(bimg) + ((size_t)cb * nch_all + c0) * L::BCH;
+      const uint8_t *dsrc = dbimg + (size_t)c0 * TA_KC * 128;
+      int c2 = 0;
+      for (; c2 < npass; ++c2) {
+        const int j = c2 % NS2;
+        if (c2 >= NS2 && !rc_wait(&sfree[j], (uint32_t)((c2 / NS2 - 1) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        uint8_t *slot = sm + L::AIMG + (size_t)j * L::SLOT;
+        mbar_arrive_expect_tx(&sfull[j], (uint32_t)(2 * L::BCH + L::DOT));
+        bulk_g2s(slot + 2 * L::BCH, dsrc + (size_t)c2 * L::DOT, L::DOT, &sfull[j]);
+        bulk_g2s(slot, bsrc + (size_t)(2 * c2) * L::BCH, 2 * L::BCH, &sfull[j]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      // the copies still in flight land before the CTA may exit
+      for (int k = c2 > NS2 ? c2 - NS2 : 0; k < c2; ++k)
+        mbar_wait_bounded(&sfull[k % NS2], (uint32_t)((k / NS2) & 1), VDS_WAIT_LIMIT_NS);
+      mbar_wait_bounded(&afull, 0, VDS_WAIT_LIMIT_NS);
+    }
+  } else if (warp == RC_PW + 1) {
+    // ---------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t idesc2 = tc_idesc(TC_FMT_F16, RC_M, ACW);
+      const uint32_t idot = tc_idesc(TC_FMT_TF32, RC_M, 2 * TA_KC);
+      const uint32_t a0 = sbase;
+      // the dot products of pass c2 into the dot buffer, once the warps have
+      // read those of pass c2 - 1
+      auto issue_dot = [&](int c2) -> bool {
+        const int j = c2 % NS2;
+        if (!rc_wait(&sfull[j], (uint32_t)((c2 / NS2) & 1), abort)) return false;
+        if (c2 >= 1 && !rc_wait(&dotfree, (uint32_t)((c2 - 1) & 1), abort)) return false;
+        tc_fence_after();
+        const uint32_t b0 = sbase + (uint32_t)(L::AIMG + j * L::SLOT + 2 * L::BCH);
+        const uint32_t d = tmem + (uint32_t)DCOL;
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint32_t o = (uint32_t)(kk * 256);
+          tc_mma_tf32(d, tc_sdesc(a0 + o), tc_sdesc(b0 + o), idot, kk > 0 ? 1 : 0);
+          tc_mma_tf32(d, tc_sdesc(a0 + o), tc_sdesc(b0 + 512 + o), idot, 1);
+          tc_mma_tf32(d, tc_sdesc(a0 + 512 + o), tc_sdesc(b0 + o), idot, 1);
+        }
+        tc_commit(&dotready);
+        return true;
+      };
+      ok = rc_wait(&afull, 0, abort) && (npass == 0 || issue_dot(0));
+      for (int c2 = 0; c2 < npass && ok; ++c2) {
+        const int j = c2 % NS2, zp = c2 % NZP;
+        if (c2 + 1 < npass && !issue_dot(c2 + 1)) {
+          ok = false;
+          break;
+        }
+        if (!rc_wait(&zready[zp], (uint32_t)((c2 / NZP) & 1), abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int e = 0; e < 2 && ok; ++e) {
+          const int ch = 2 * c2 + e, g = ch / TA_SEGC, b = g & 1;
+          if (ch % TA_SEGC == 0 && g >= 2 && !rc_wait(&accfree[b], (uint32_t)(((g >> 1) - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t b_hi = sbase + (uint32_t)(L::AIMG + j * L::SLOT + e * L::BCH);
+          const uint32_t zt = tmem + (uint32_t)(ZCOL + 64 * zp + 32 * e);
+          const uint32_t acc = tmem + (uint32_t)(b * ACW);
+#pragma unroll
+          for (int k = 0; k < TA_KC / 16; ++k) {
+            const uint32_t o = (uint32_t)k * 256u;
+            const int first = (ch % TA_SEGC == 0 && k == 0) ? 0 : 1;
+            tc_mma_f16_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+          }
+          if (ch % TA_SEGC == TA_SEGC - 1 || ch == nch - 1) tc_commit(&segdone[b]);
+        }
+        tc_commit(&sfree[j]);
+        tc_commit(&zfree[zp]);
+      }
+      if (!ok) vds_flag(err, VDS_ETIMEOUT);
+      tc_commit(&fin);
+      mbar_wait_bounded(&fin, 0, VDS_WAIT_LIMIT_NS);
+    }
+  } else {
+    // ---------------------------------------------------- Z from the dot products
+    // thread = row 32 (warp % 4) + lane (its tensor-memory lane), the 16 K of
+    // quarter warp / 4 of each chunk
+    const int q4 = warp & 3, cq = warp >> 2;
+    const float ni = rec[(size_t)min(i0 + 32 * q4 + lane, Npad - 1) * DP + D + 1];
+#pragma unroll
+    for (int j = 0; j < QC; ++j) tot[j] = 0.f;
+    auto flush = [&](int g) -> bool {
+      const int b = g & 1;
+      if (!__all_sync(0xffffffffu, rc_wait(&segdone[b], (uint32_t)((g >> 1) & 1), abort))) return false;
+      tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * ACW + cq * QC);
+      if constexpr (QC == 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld16(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[j] += __uint_as_float(v[j]);
+        }
+      } else {
+        static_assert(QC == 8, "accumulator columns per thread");
+        uint32_t v[8];
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          tc_ld8(ta + (uint32_t)(hf * NCP), v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) tot[j] += __uint_as_float(v[j]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accfree[b]);
+      return true;
+    };
+    int flushed = 0;
+    const uint32_t lbase = (uint32_t)(q4 * 32) << 16;
+    for (int c2 = 0; c2 < npass && ok; ++c2) {
+      const int zp = c2 % NZP;
+      if (!__all_sync(0xffffffffu, rc_wait(&dotready, (uint32_t)(c2 & 1), abort) &&
+                                       (c2 < NZP || rc_wait(&zfree[zp], (uint32_t)((c2 / NZP - 1) & 1), abort)))) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t v0[16], v1[16];
+      tc_ld16(tmem + lbase + (uint32_t)(DCOL + 16 * cq), v0);
+      tc_ld16(tmem + lbase + (uint32_t)(DCOL + TA_KC + 16 * cq), v1);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dotfree);
+      uint32_t hv0[8], hv1[8];
+#pragma unroll
+      for (int u = 0; u < 16; u += 2) {
+        const __half2 z0 = __floats2half2_rn(ex2_approx(__uint_as_float(v0[u]) - ni),
+                                             ex2_approx(__uint_as_float(v0[u + 1]) - ni));
+        const __half2 z1 = __floats2half2_rn(ex2_approx(__uint_as_float(v1[u]) - ni),
+                                             ex2_approx(__uint_as_float(v1[u + 1]) - ni));
+        hv0[u / 2] = *reinterpret_cast<const uint32_t *>(&z0);
+        hv1[u / 2] = *reinterpret_cast<const uint32_t *>(&z1);
+      }
+      const uint32_t zt = tmem + lbase + (uint32_t)(ZCOL + 64 * zp + 8 * cq);
+      tc_st8(zt, hv0);
+      tc_st8(zt + 32u, hv1);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&zready[zp]);
+      const int ch = 2 * c2;
+      if (ch % TA_SEGC == 4 && ch / TA_SEGC >= 1) {
+        if (!flush(ch / TA_SEGC - 1)) {
+          ok = false;
+          break;
+        }
+        ++flushed;
+      }
+    }
+    for (; ok && flushed < nseg; ++flushed)
+      if (!flush(flushed)) ok = false;
+    if (!ok && tid == 0) vds_flag(err, VDS_ETIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, TCOLS);
+  if (*abort) return;
+  rc_epilogue<D, NCP, QC>(sm, L::TOT_LD, tot, tid, warp, lane, i0, cb, N, rec, phi, ld, r, s, rr, U1, U2, part,
+                          1.f / TA_BSCALE);
+}
+
 // U1, U2 from the totals of the nsplit K splits of every row tile, summed in
 // split order (FP64): one thread per (I, a, u).
 __global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, int ncta_x, const float *__restrict__ rec,
@@ -832,12 +1099,41 @@ __global__ void k_rc_fin(const float *__restrict__ part, int nsplit, int NCP, in
   U2[o] = (float)cs * f - (float)w2;
 }
 
+// the K splits' totals summed into U1, U2 (when the row tiles were split)
+template <int D, int NCP>
+int refresh_finish(vds_ctx *c, const pod_basis *b, int N, int rr, int ncb, int nsplit, float *part, float *U1,
+                   float *U2) {
+  if (nsplit <= 1) return VDS_OK;
+  const int ntiles = (N + RC_M - 1) / RC_M;
+  const int per = b->s * rr;
+  k_rc_fin<<<dim3((unsigned)(((long)N * per + 255) / 256), ncb), 256, 0, c->stream>>>(
+      part, nsplit, NCP, ntiles * nsplit, (const float *)c->rec.ptr, Rec<D>::DP, D, N, b->phi, b->ld, b->r, b->s,
+      rr, U1, U2);
+  VDS_CUDA_TRY(cudaGetLastError());
+  ++c->launches;
+  return VDS_OK;
+}
+
 template <int D, int NCP>
 int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int ncb, const float *bimg,
-                   const float *recs, int nsplit, float *part, float *U1, float *U2) {
+                   const float *recs, int nsplit, float *part, float *U1, float *U2, const uint8_t *daimg,
+                   const uint8_t *dbimg) {
   const int ntiles = (N + RC_M - 1) / RC_M;
   dim3 grid(ntiles * nsplit, ncb);
   float *pp = nsplit > 1 ? part : nullptr;
+  if constexpr (NCP <= 64 && (D == 6 || D == 9)) {
+    if (daimg && dbimg) {
+      using L = DtLayout<NCP>;
+      VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_dt<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)L::SMEM));
+      k_refresh_dt<D, NCP><<<grid, RC_NT, L::SMEM, c->stream>>>((const float *)c->rec.ptr, N, Npad, bimg, daimg,
+                                                                 dbimg, b->phi, b->ld, b->r, b->s, rr, U1, U2,
+                                                                 nsplit, pp, c->err);
+      VDS_CUDA_TRY(cudaGetLastError());
+      ++c->launches;
+      return refresh_finish<D, NCP>(c, b, N, rr, ncb, nsplit, part, U1, U2);
+    }
+  }
   if constexpr (NCP <= 64) {
     using L = TaLayout<D, NCP>;
     VDS_CUDA_TRY(cudaFuncSetAttribute(k_refresh_ta<D, NCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -855,15 +1151,7 @@ int refresh_launch(vds_ctx *c, const pod_basis *b, int N, int Npad, int rr, int 
   }
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
-  if (nsplit > 1) {
-    const int per = b->s * rr;
-    k_rc_fin<<<dim3((unsigned)(((long)N * per + 255) / 256), ncb), 256, 0, c->stream>>>(
-        part, nsplit, NCP, ntiles * nsplit, (const float *)c->rec.ptr, Rec<D>::DP, D, N, b->phi, b->ld, b->r, b->s,
-        rr, U1, U2);
-    VDS_CUDA_TRY(cudaGetLastError());
-    ++c->launches;
-  }
-  return VDS_OK;
+  return refresh_finish<D, NCP>(c, b, N, rr, ncb, nsplit, part, U1, U2);
 }
 
 // K splits per row tile: whole segments, chosen so that the CTAs (one per
@@ -908,11 +1196,18 @@ int refresh_impl(vds_ctx *c, const pod_basis *b, int N, float *U1, float *U2) {
                                                                      N, Npad, NCP, bimg, recs);
   VDS_CUDA_TRY(cudaGetLastError());
   ++c->launches;
+  // the dot products of the kernel values on the tensor cores where the
+  // density pass's operand images exist for this D (the same layout and
+  // padding as the records: Npad rows)
+  const uint8_t *daimg = nullptr, *dbimg = nullptr;
+  if (NCP <= 64 && (D == 6 || D == 9)) VDS_TRY(pass_density_tc_images(c, N, D, &daimg, &dbimg));
   switch (NCP) {
-    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
-    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
-    case 128: return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
-    default: return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2);
+    case 32: return refresh_launch<D, 32>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2, daimg, dbimg);
+    case 64: return refresh_launch<D, 64>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2, daimg, dbimg);
+    case 128:
+      return refresh_launch<D, 128>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2, nullptr, nullptr);
+    default:
+      return refresh_launch<D, 256>(c, b, N, Npad, rr, ncb, bimg, recs, nsplit, part, U1, U2, nullptr, nullptr);
   }
 }
 
