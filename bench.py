@@ -518,21 +518,31 @@ def _extra_pod(ctx, vds, inputs, torch, wl, h, kap, timed):
     ctx.vds_timing(False)
     sec3, _ = timed(lambda: ctx.pod_step(basis, P, N, D, pe, nsteps=3, mode=1))
     # the refresh pass against its CUDA-core floor: the kernel values Z_IK by
-    # their definition, 2D + 1 FP32 lane-ops per ordered pair (the kernel
-    # forms the distance through the particles' norms, D + 2 operations; the
-    # contraction Z B runs on the tensor cores), at SMs x 128 lanes x the
-    # measured maximum SM clock
+    # their definition, 2D + 1 FP32 lane-ops per ordered pair, at SMs x 128
+    # lanes x the measured maximum SM clock.  For D = 6 and 9 (2 s r + 1 <= 64)
+    # k_refresh_dt takes the pair dot products on the tensor cores (TF32 hi/lo
+    # split, K padded to 16) and leaves the CUDA cores a subtract, an ex2 and
+    # half a pack per pair; elsewhere k_refresh_ta forms the distance through
+    # the particles' norms (D + 2 lane-ops).  Both contract Z B on the tensor
+    # cores.  frac is therefore the rate of the definition's work against the
+    # CUDA cores' peak, not a pipe's utilisation.
     peaks, src = _peaks()
     nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak_tops = nsm * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     rf_t = rf_ms[3] / max(1, rf_n[3]) / 1e3
     ops = float(N) * N * (2 * D + 1)
-    refresh_roof = {"bound": "alu", "kernel": "k_refresh_ta (X^B refresh, Z on CUDA cores, Z B on tensor cores)",
+    ncp = 2 * s * basis.info()["r"] + 1
+    dt = D in (6, 9) and ncp <= 64
+    refresh_roof = {"bound": "alu",
+                    "kernel": ("k_refresh_dt (X^B refresh, pair dot products and Z B on tensor cores, ex2 on "
+                               "CUDA cores)") if dt else
+                              "k_refresh_ta (X^B refresh, Z on CUDA cores, Z B on tensor cores)",
                     "ops_per_pair": 2 * D + 1, "achieved": ops / rf_t / 1e12, "peak": peak_tops,
                     "unit": "TOP/s (FP32 lane-ops)", "frac": ops / rf_t / 1e12 / peak_tops,
                     "floor_ms": ops / (peak_tops * 1e12) * 1e3, "launch_ms": rf_t * 1e3,
-                    "kernel_ops_per_pair": D + 2,
-                    "tensor_tflops": float(N) * N * 2 * 2 * (2 * s * basis.info()["r"] + 1) / rf_t / 1e12,
+                    "kernel_ops_per_pair": 2.5 if dt else D + 2,
+                    "tensor_tflops": float(N) * N * 2 * 2 * ncp / rf_t / 1e12,
+                    "dot_tensor_tflops": float(N) * N * 2 * 16 * 3 / rf_t / 1e12 if dt else 0.0,
                     "peak_note": f"{nsm} SMs x 128 FP32 lanes x {src} sm_max_mhz; the time includes the "
                                  "B-image and split-sum kernels of a refresh"}
     out = {"snapshots": S, "snapshot_matrix": [N * s, S * nb], "build_s": sec, "rank": r,
