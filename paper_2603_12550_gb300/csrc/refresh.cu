@@ -813,11 +813,15 @@ __global__ void __launch_bounds__(RC_NT, 1)
 // Z from the records on the CUDA cores now read those sums (tcgen05.ld),
 // subtract |qh_I|^2, take ex2 and round to FP16 (one ex2, one FP32 operation
 // and a half conversion per pair instead of D + 2 operations), and the MMA
-// warp runs Z against [B_hi; B_lo] as in k_refresh_ta.  The dot products of
-// pass c + 1 are issued as soon as the warps have read those of pass c, so
-// they run under the exponentials and the Z.B MMAs of pass c.
-// Tensor memory: the two segment accumulators (2 x 2 NCP columns), two Z
-// pair slots (2 x 64) and the dot buffer (128).
+// warp runs Z against [B_hi; B_lo] as in k_refresh_ta.
+// Tensor memory: the two segment accumulators (2 x 2 NCP columns) and two
+// 128-column pass buffers X_0, X_1.  Pass c's dot products land in
+// X_(c mod 2); each thread reads its 2 x 16 sums and writes their 16 FP16
+// pairs back over the first 8 of each 16 columns it read, so Z of pass c is
+// the A operand of the Z.B MMAs in place (16 particles per 16 columns).  The
+// dot products of pass c + 2 go into the same buffer once the Z.B MMAs of
+// pass c have completed, so the tensor pipe holds the next pass's dot
+// products while the warps form Z.
 template <int NCP>
 struct DtLayout {
   static constexpr int BOP = NCP * TA_KC * 2;       // one FP16 B operand tile
@@ -845,13 +849,12 @@ __global__ void __launch_bounds__(RC_NT, 1)
   constexpr int NS2 = L::NS2;
   constexpr int QC = NCP / 4;   // accumulator columns per thread in a flush
   constexpr int ACW = 2 * NCP;  // Z against [B_hi; B_lo]: N = 2 NCP
-  constexpr int NZP = 2;        // Z pair slots: 2 chunks x 32 columns each
-  constexpr int ZCOL = 2 * ACW, DCOL = ZCOL + NZP * 64;
+  constexpr int XCOL = 2 * ACW;  // the two pass buffers
   constexpr int TCOLS = 512;
-  static_assert(DCOL + 128 <= TCOLS, "tensor memory columns");
+  static_assert(XCOL + 2 * 128 <= TCOLS, "tensor memory columns");
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t afull, sfull[NS2], sfree[NS2], dotready, dotfree, zready[NZP], zfree[NZP],
-      segdone[2], accfree[2], fin;
+  __shared__ __align__(8) uint64_t afull, sfull[NS2], sfree[NS2], dotready[2], zready[2], xfree[2], segdone[2],
+      accfree[2], fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -872,13 +875,10 @@ __global__ void __launch_bounds__(RC_NT, 1)
       mbar_init(&sfull[j], 1);
       mbar_init(&sfree[j], 1);
     }
-    mbar_init(&dotready, 1);
-    mbar_init(&dotfree, RC_PW);
-    for (int b = 0; b < NZP; ++b) {
-      mbar_init(&zready[b], RC_PW);
-      mbar_init(&zfree[b], 1);
-    }
     for (int b = 0; b < 2; ++b) {
+      mbar_init(&dotready[b], 1);
+      mbar_init(&zready[b], RC_PW);
+      mbar_init(&xfree[b], 1);
       mbar_init(&segdone[b], 1);
       mbar_init(&accfree[b], RC_PW);
     }
@@ -925,15 +925,15 @@ __global__ void __launch_bounds__(RC_NT, 1)
       const uint32_t idesc2 = tc_idesc(TC_FMT_F16, RC_M, ACW);
       const uint32_t idot = tc_idesc(TC_FMT_TF32, RC_M, 2 * TA_KC);
       const uint32_t a0 = sbase;
-      // the dot products of pass c2 into the dot buffer, once the warps have
-      // read those of pass c2 - 1
+      // the dot products of pass c2 into X_(c2 mod 2), once the Z.B MMAs of
+      // pass c2 - 2 (which read Z from that buffer) have completed
       auto issue_dot = [&](int c2) -> bool {
-        const int j = c2 % NS2;
+        const int j = c2 % NS2, x = c2 & 1;
         if (!rc_wait(&sfull[j], (uint32_t)((c2 / NS2) & 1), abort)) return false;
-        if (c2 >= 1 && !rc_wait(&dotfree, (uint32_t)((c2 - 1) & 1), abort)) return false;
+        if (c2 >= 2 && !rc_wait(&xfree[x], (uint32_t)(((c2 >> 1) - 1) & 1), abort)) return false;
         tc_fence_after();
         const uint32_t b0 = sbase + (uint32_t)(L::AIMG + j * L::SLOT + 2 * L::BCH);
-        const uint32_t d = tmem + (uint32_t)DCOL;
+        const uint32_t d = tmem + (uint32_t)(XCOL + 128 * x);
 #pragma unroll
         for (int kk = 0; kk < 2; ++kk) {
           const uint32_t o = (uint32_t)(kk * 256);
@@ -941,17 +941,13 @@ __global__ void __launch_bounds__(RC_NT, 1)
           tc_mma_tf32(d, tc_sdesc(a0 + o), tc_sdesc(b0 + 512 + o), idot, 1);
           tc_mma_tf32(d, tc_sdesc(a0 + 512 + o), tc_sdesc(b0 + o), idot, 1);
         }
-        tc_commit(&dotready);
+        tc_commit(&dotready[x]);
         return true;
       };
-      ok = rc_wait(&afull, 0, abort) && (npass == 0 || issue_dot(0));
+      ok = rc_wait(&afull, 0, abort) && (npass < 1 || issue_dot(0)) && (npass < 2 || issue_dot(1));
       for (int c2 = 0; c2 < npass && ok; ++c2) {
-        const int j = c2 % NS2, zp = c2 % NZP;
-        if (c2 + 1 < npass && !issue_dot(c2 + 1)) {
-          ok = false;
-          break;
-        }
-        if (!rc_wait(&zready[zp], (uint32_t)((c2 / NZP) & 1), abort)) {
+        const int j = c2 % NS2, x = c2 & 1;
+        if (!rc_wait(&zready[x], (uint32_t)((c2 >> 1) & 1), abort)) {
           ok = false;
           break;
         }
@@ -963,18 +959,23 @@ __global__ void __launch_bounds__(RC_NT, 1)
             break;
           }
           const uint32_t b_hi = sbase + (uint32_t)(L::AIMG + j * L::SLOT + e * L::BCH);
-          const uint32_t zt = tmem + (uint32_t)(ZCOL + 64 * zp + 32 * e);
+          const uint32_t zt = tmem + (uint32_t)(XCOL + 128 * x + 64 * e);
           const uint32_t acc = tmem + (uint32_t)(b * ACW);
 #pragma unroll
           for (int k = 0; k < TA_KC / 16; ++k) {
             const uint32_t o = (uint32_t)k * 256u;
             const int first = (ch % TA_SEGC == 0 && k == 0) ? 0 : 1;
-            tc_mma_f16_ta(acc, zt + (uint32_t)(8 * k), tc_sdesc(b_hi + o), idesc2, first);
+            tc_mma_f16_ta(acc, zt + (uint32_t)(16 * k), tc_sdesc(b_hi + o), idesc2, first);
           }
           if (ch % TA_SEGC == TA_SEGC - 1 || ch == nch - 1) tc_commit(&segdone[b]);
         }
+        if (!ok) break;
         tc_commit(&sfree[j]);
-        tc_commit(&zfree[zp]);
+        tc_commit(&xfree[x]);
+        if (c2 + 2 < npass && !issue_dot(c2 + 2)) {
+          ok = false;
+          break;
+        }
       }
       if (!ok) vds_flag(err, VDS_ETIMEOUT);
       tc_commit(&fin);
@@ -1019,19 +1020,17 @@ __global__ void __launch_bounds__(RC_NT, 1)
     int flushed = 0;
     const uint32_t lbase = (uint32_t)(q4 * 32) << 16;
     for (int c2 = 0; c2 < npass && ok; ++c2) {
-      const int zp = c2 % NZP;
-      if (!__all_sync(0xffffffffu, rc_wait(&dotready, (uint32_t)(c2 & 1), abort) &&
-                                       (c2 < NZP || rc_wait(&zfree[zp], (uint32_t)((c2 / NZP - 1) & 1), abort)))) {
+      const int x = c2 & 1;
+      if (!__all_sync(0xffffffffu, rc_wait(&dotready[x], (uint32_t)((c2 >> 1) & 1), abort))) {
         ok = false;
         break;
       }
       tc_fence_after();
+      // this thread's 16 particles of each chunk: columns 16 cq.. of the
+      // chunk's 64; Z goes back over the first 8 of them, two halves a column
+      const uint32_t xt = tmem + lbase + (uint32_t)(XCOL + 128 * x + 16 * cq);
       uint32_t v0[16], v1[16];
-      tc_ld16(tmem + lbase + (uint32_t)(DCOL + 16 * cq), v0);
-      tc_ld16(tmem + lbase + (uint32_t)(DCOL + TA_KC + 16 * cq), v1);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&dotfree);
+      tc_ld16x2(xt, xt + (uint32_t)TA_KC, v0, v1);
       uint32_t hv0[8], hv1[8];
 #pragma unroll
       for (int u = 0; u < 16; u += 2) {
@@ -1042,13 +1041,12 @@ __global__ void __launch_bounds__(RC_NT, 1)
         hv0[u / 2] = *reinterpret_cast<const uint32_t *>(&z0);
         hv1[u / 2] = *reinterpret_cast<const uint32_t *>(&z1);
       }
-      const uint32_t zt = tmem + lbase + (uint32_t)(ZCOL + 64 * zp + 8 * cq);
-      tc_st8(zt, hv0);
-      tc_st8(zt + 32u, hv1);
+      tc_st8(xt, hv0);
+      tc_st8(xt + (uint32_t)TA_KC, hv1);
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&zready[zp]);
+      if (lane == 0) mbar_arrive(&zready[x]);
       const int ch = 2 * c2;
       if (ch % TA_SEGC == 4 && ch / TA_SEGC >= 1) {
         if (!flush(ch / TA_SEGC - 1)) {

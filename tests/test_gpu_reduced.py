@@ -175,13 +175,16 @@ def test_score_check_falls_back_to_exact(vds, ctx, setup):
 
 @pytest.mark.parametrize("N,nb,s,r", [(1000, 3, 3, 5), (1000, 3, 3, 20), (777, 2, 3, 42), (1300, 3, 3, 64),
                                       (2000, 4, 2, 30), (129, 1, 3, 3), (300, 2, 3, 16), (300, 2, 3, 17),
-                                      (300, 2, 3, 32), (300, 2, 3, 33)])
+                                      (300, 2, 3, 32), (300, 2, 3, 33), (600, 2, 3, 10), (3000, 2, 3, 4),
+                                      (100, 3, 3, 3), (5000, 3, 3, 10)])
 def test_brownian_matrices_every_column_chunk_shape(orc, vds, ctx, N, nb, s, r):
     # the refresh pass for every width of its B slice (2 s r + 1 columns padded
     # to 32, 64, 128 or 256; r = 64 with s = 3 takes two column chunks), ragged
     # N, and a segment count that is not a multiple of the flush schedule;
     # r = 16/17 and 32/33 straddle the corner sizes (16, 32, 64) of the r x r
-    # contractions Phi^T U: X^B1 and X^B2 at the lifted state against the oracle
+    # contractions Phi^T U; D = 6 and 9 with 2 s r + 1 <= 64 take the kernel
+    # values' dot products on the tensor cores (one to many passes per CTA):
+    # X^B1 and X^B2 at the lifted state against the oracle
     D = nb * s
     rng = np.random.default_rng(N + r)
     Phi, _ = np.linalg.qr(rng.standard_normal((N * s, r)))
