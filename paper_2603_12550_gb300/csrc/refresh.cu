@@ -816,12 +816,14 @@ __global__ void __launch_bounds__(RC_NT, 1)
 // warp runs Z against [B_hi; B_lo] as in k_refresh_ta.
 // Tensor memory: the two segment accumulators (2 x 2 NCP columns) and two
 // 128-column pass buffers X_0, X_1.  Pass c's dot products land in
-// X_(c mod 2); each thread reads its 2 x 16 sums and writes their 16 FP16
-// pairs back over the first 8 of each 16 columns it read, so Z of pass c is
+// X_(c mod 2); each thread reads its sums 16 columns at a time and writes
+// their 8 FP16 pairs back over the first 8 of the 16 columns, so Z of pass c is
 // the A operand of the Z.B MMAs in place (16 particles per 16 columns).  The
 // dot products of pass c + 2 go into the same buffer once the Z.B MMAs of
 // pass c have completed, so the tensor pipe holds the next pass's dot
-// products while the warps form Z.
+// products while the warps form Z.  The 16 warps form Z in two groups of eight
+// on alternate passes (buffers), so one group's tensor-memory traffic and
+// waits overlap the other's exponentials.
 template <int NCP>
 struct DtLayout {
   static constexpr int BOP = NCP * TA_KC * 2;       // one FP16 B operand tile
@@ -877,7 +879,7 @@ __global__ void __launch_bounds__(RC_NT, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&dotready[b], 1);
-      mbar_init(&zready[b], RC_PW);
+      mbar_init(&zready[b], RC_PW / 2);  // the eight warps of group b
       mbar_init(&xfree[b], 1);
       mbar_init(&segdone[b], 1);
       mbar_init(&accfree[b], RC_PW);
@@ -1019,37 +1021,49 @@ __global__ void __launch_bounds__(RC_NT, 1)
     };
     int flushed = 0;
     const uint32_t lbase = (uint32_t)(q4 * 32) << 16;
-    for (int c2 = 0; c2 < npass && ok; ++c2) {
-      const int x = c2 & 1;
-      if (!__all_sync(0xffffffffu, rc_wait(&dotready[x], (uint32_t)((c2 >> 1) & 1), abort))) {
+    // two groups of eight warps take alternate passes: group gp the passes
+    // c2 = gp mod 2, so always pass buffer X_gp, and one group's
+    // tensor-memory loads and stores overlap the other's exponentials.  A
+    // warp covers its lane quarter and the 16-column blocks 2 h and 2 h + 1
+    // of each chunk, one block after the other.
+    const int gp = cq >> 1, h = cq & 1;
+    for (int c2 = gp; c2 < npass && ok; c2 += 2) {
+      if (!__all_sync(0xffffffffu, rc_wait(&dotready[gp], (uint32_t)((c2 >> 1) & 1), abort))) {
         ok = false;
         break;
       }
       tc_fence_after();
-      // this thread's 16 particles of each chunk: columns 16 cq.. of the
-      // chunk's 64; Z goes back over the first 8 of them, two halves a column
-      const uint32_t xt = tmem + lbase + (uint32_t)(XCOL + 128 * x + 16 * cq);
-      uint32_t v0[16], v1[16];
-      tc_ld16x2(xt, xt + (uint32_t)TA_KC, v0, v1);
-      uint32_t hv0[8], hv1[8];
 #pragma unroll
-      for (int u = 0; u < 16; u += 2) {
-        const __half2 z0 = __floats2half2_rn(ex2_approx(__uint_as_float(v0[u]) - ni),
-                                             ex2_approx(__uint_as_float(v0[u + 1]) - ni));
-        const __half2 z1 = __floats2half2_rn(ex2_approx(__uint_as_float(v1[u]) - ni),
-                                             ex2_approx(__uint_as_float(v1[u + 1]) - ni));
-        hv0[u / 2] = *reinterpret_cast<const uint32_t *>(&z0);
-        hv1[u / 2] = *reinterpret_cast<const uint32_t *>(&z1);
+      for (int blk = 0; blk < 2; ++blk) {
+        // the block's 16 particles of each chunk: columns 16 (2 h + blk).. of
+        // the chunk's 64; Z goes back over the first 8 of them, two halves a
+        // column, where the Z.B MMA of K block 2 h + blk takes it
+        const uint32_t xt = tmem + lbase + (uint32_t)(XCOL + 128 * gp + 16 * (2 * h + blk));
+        uint32_t v0[16], v1[16];
+        tc_ld16x2(xt, xt + (uint32_t)TA_KC, v0, v1);
+        uint32_t hv0[8], hv1[8];
+#pragma unroll
+        for (int u = 0; u < 16; u += 2) {
+          const __half2 z0 = __floats2half2_rn(ex2_approx(__uint_as_float(v0[u]) - ni),
+                                               ex2_approx(__uint_as_float(v0[u + 1]) - ni));
+          const __half2 z1 = __floats2half2_rn(ex2_approx(__uint_as_float(v1[u]) - ni),
+                                               ex2_approx(__uint_as_float(v1[u + 1]) - ni));
+          hv0[u / 2] = *reinterpret_cast<const uint32_t *>(&z0);
+          hv1[u / 2] = *reinterpret_cast<const uint32_t *>(&z1);
+        }
+        tc_st8(xt, hv0);
+        tc_st8(xt + (uint32_t)TA_KC, hv1);
       }
-      tc_st8(xt, hv0);
-      tc_st8(xt + (uint32_t)TA_KC, hv1);
       tc_wait_st();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&zready[x]);
-      const int ch = 2 * c2;
-      if (ch % TA_SEGC == 4 && ch / TA_SEGC >= 1) {
-        if (!flush(ch / TA_SEGC - 1)) {
+      if (lane == 0) mbar_arrive(&zready[gp]);
+      // segment sg - 1 is flushed after this group's pass in the middle of
+      // segment sg (pass 2 of its 4 for group 0, pass 3 for group 1)
+      constexpr int PPS = TA_SEGC / 2;  // passes per segment
+      static_assert(PPS == 4, "flush schedule: four passes per segment");
+      if (c2 % PPS == 2 + gp && c2 / PPS >= 1) {
+        if (!flush(c2 / PPS - 1)) {
           ok = false;
           break;
         }
