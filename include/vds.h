@@ -146,7 +146,7 @@ VDS_API int vds_density_at(vds_ctx *ctx, const float *q, int N, int D, const vds
  * (Sec. 2.2, self term included), with the pair dot products on the tensor
  * cores: -|qh_I - qh_J|^2 = 2 qh_I . qh_J - |qh_I|^2 - |qh_J|^2 as MMAs of
  * TF32 operands split into two TF32 parts each (three products per pair), the
- * exponentials on the CUDA cores.  For passes judged at 1e-4 (the library
+ * exponentials on the CUDA cores.  For passes held to 1e-4 (the library
  * uses it for the density at the lifted state of the frozen reduced step's
  * refresh and for the density of the surrogate's subset check): within
  * 1e-5 relative of the exact kernel sum for the median particle of an

@@ -1,7 +1,7 @@
 // dens_tc.cu -- the density pass rho_I = sum_J exp2(-|qh_I - qh_J|^2)
 // (Sec. 2.2's kernel density, qh the connectors scaled by sqrt(log2 e / 2h^2))
 // with the pair dot products on the 5th-generation tensor cores, for passes
-// judged at 1e-4 rather than the full-order path's 1e-5: the density at the
+// held to 1e-4 rather than the full-order path's 1e-5: the density at the
 // lifted state of the frozen reduced step's refresh, and the density of all
 // particles that the surrogate's subset check needs.
 //

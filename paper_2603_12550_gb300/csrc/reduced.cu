@@ -467,7 +467,7 @@ struct Dev {
 };
 
 // The density of every particle of the records in ctx->rec for the passes
-// judged at 1e-4 or looser (the refresh's lifted state, the surrogate's
+// held to 1e-4 or looser (the refresh's lifted state, the surrogate's
 // subset check): the pair dot products on the tensor cores where the records
 // allow it (D = 6, 9), else the expanded distances on the CUDA cores.  The
 // tensor-core sums lose more to the |q|^2 terms at single particles (3.4e-4
@@ -697,7 +697,7 @@ int pod_step_score(vds_ctx *c, const pod_basis *b, vds_score *sc, float *P, int 
     {
       // full density (every 1/rho_J enters S_I), gradient of the checked rows;
       // the density within about 1e-4 (against a check threshold of order 0.1
-      // and a fallback step judged at 1e-3)
+      // and a fallback step held to 1e-3)
       VDS_TRY(pass_prep(c, kS, qt, nullptr, nullptr, 0.f, nullptr));
       VDS_TRY(density_1e4(c, kS, qt));
       // compact exact S of the checked rows (after the FP64 segment partials)
