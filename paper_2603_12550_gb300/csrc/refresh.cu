@@ -1027,6 +1027,8 @@ __global__ void __launch_bounds__(RC_NT, 1)
     // warp covers its lane quarter and the 16-column blocks 2 h and 2 h + 1
     // of each chunk, one block after the other.
     const int gp = cq >> 1, h = cq & 1;
+    static_assert(RC_PW == 16 && TA_KC == 64,
+                  "two groups x 4 lane quarters x 2 column halves; 4 blocks of 16 particles per chunk");
     for (int c2 = gp; c2 < npass && ok; c2 += 2) {
       if (!__all_sync(0xffffffffu, rc_wait(&dotready[gp], (uint32_t)((c2 >> 1) & 1), abort))) {
         ok = false;
